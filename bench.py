@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark of the MAS-PNCG timestep on one B300 (or N replicas).
+
+Workload: the 64-sphere pile (46,656 vertices, 196,608 tets, seeded random
+non-overlapping centres in a 1 m box, E log-uniform in [1e4, 1e6] Pa,
+dt = 1/60 s, tol 1e-3), FP32 bulk arithmetic with FP64 for positions,
+barrier distances, CCD, the 2x2 and capacitance solves and the energy
+checks.  One bench step is one implicit-Euler timestep (Algorithm 1 to
+convergence).  Inputs are synthetic and resident in HBM when the timed region
+starts; L2 is flushed (256 MB write) before every timed step.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead,
+on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PNCG iters/s & steps/s vs plain form at fixed grad tol; p50/p99 step latency"
+WORKLOAD = ("64-sphere pile: 46,656 verts, 196,608 tets, 1 m box, E log-uniform [1e4,1e6] Pa, dt 1/60 s, "
+            "gradient-norm tol 1e-3, FP32 bulk with FP64 barrier/CCD/2x2/energy")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return pk.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def stage_bytes(nv, nt, nblocks, rsize):
+    """Algorithmic bytes per launch of the two per-iteration HBM-bound stages.
+
+    mas_blocks: every 96x96 inverse block once (all levels) + g read + z write.
+    forms: per tet the packed Hessian (45), rest inverse (9) and 4 indices;
+    per vertex z and p read once.
+    """
+    mas = nblocks * 96 * 96 * rsize + 2 * 3 * nv * rsize
+    forms = nt * (54 * rsize + 16) + 2 * 3 * nv * rsize + nv * 8
+    return {"mas_blocks": mas, "forms": forms}
+
+
+def run_cpu_baseline(sc, gpu_iters_per_step):
+    """The oracle as it stands, one PNCG iteration of timestep 0 (bounded sample)."""
+    import oracle as O
+    o = O.Scene(sc, params={"iter_max": 1})
+    t0 = time.perf_counter()
+    o.step(sc["x0"], sc["v0"])
+    dt = time.perf_counter() - t0
+    iters_per_s = 1.0 / dt
+    return {
+        "value": iters_per_s / max(gpu_iters_per_step, 1e-9),
+        "unit": "timesteps/s",
+        "cores": 1,
+        "kind": "oracle",
+        "sample": (f"1 PNCG iteration of timestep 0 of the same workload ({dt:.2f} s, single thread); "
+                   f"timesteps/s = oracle iters/s / GPU mean iters per timestep ({gpu_iters_per_step:.1f})"),
+        "iters_per_s": iters_per_s,
+    }
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle timed on host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2604_19892_b300 import scenes as S
+    import oracle as O
+    sc = S.sphere_pile()
+    # each reference step: one PNCG iteration of the timestep, iterations chained
+    o = O.Scene(sc, params={"iter_max": 1})
+    x, v = sc["x0"].copy(), sc["v0"].copy()
+    for _ in range(args.warmup):
+        o.step(x, v)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.step(x, v)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    iters_per_s = args.steps / total
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": iters_per_s,
+        "unit": "PNCG iters/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "each step = 1 PNCG iteration of timestep 0 (FP64 oracle)"},
+        "cpu_baseline": {"value": iters_per_s, "unit": "PNCG iters/s", "cores": 1, "kind": "oracle",
+                         "sample": "1 PNCG iteration of timestep 0 per step, single thread"},
+        "e2e": {"value": iters_per_s, "unit": "PNCG iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_19892_b300 import build, ipc
+    from paper_2604_19892_b300 import scenes as S
+    build.build()
+    ipc.load()
+    prec = ipc.IPC_PREC_FP32 if args.precision == "fp32" else ipc.IPC_PREC_FP64
+    rsize = 4 if prec == ipc.IPC_PREC_FP32 else 8
+    sc = S.sphere_pile()
+    scene = ipc.Scene(sc, precision=prec)
+    nv, nt = sc["x0"].shape[0], sc["tets"].shape[0]
+    nblocks = sum(int(g.max()) + 1 for g, _ in scene.levels())
+    stream = torch.cuda.current_stream()
+
+    # warm-up steps from the initial state, then reset so the timed steps are
+    # timesteps 0..K-1 of the workload
+    for _ in range(args.warmup):
+        scene.step(1)
+    scene.set_state(sc["x0"], sc["v0"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    scene.profile(True)
+    launches0 = ipc.kernel_launches()
+    iters = 0
+    status = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev0[k].record(stream)
+        st = scene.step(1)
+        ev1[k].record(stream)
+        iters += st["iters"]
+        status.append(st)
+    torch.cuda.synchronize()
+    launches = ipc.kernel_launches() - launches0
+    prof = scene.profile_read()
+    scene.profile(False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    steps_per_s = world * args.steps / (total_ms / 1e3)
+    iters_per_s = world * iters / (total_ms / 1e3)
+
+    # roofline of the dominant HBM-bound stage
+    peak, peak_kind = load_peaks()
+    by = stage_bytes(nv, nt, nblocks, rsize)
+    roof = {}
+    for stg in ("mas_blocks", "forms"):
+        n = prof[stg]["launches"]
+        if n:
+            avg_s = prof[stg]["ms"] / n / 1e3
+            ach = by[stg] / avg_s / 1e9
+            roof[stg] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "traffic": None, "bytes_per_launch": by[stg], "avg_us": avg_s * 1e6, "launches": n,
+                         "peak_source": peak_kind}
+    dominant = max(roof, key=lambda s: prof[s]["ms"]) if roof else None
+
+    # end-to-end through the C ABI with host buffers: per step the state goes
+    # host -> device, the step runs, positions come back device -> host
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(np.ascontiguousarray(sc["x0"])).pin_memory()
+        vh = torch.from_numpy(np.ascontiguousarray(sc["v0"])).pin_memory()
+        xo = torch.empty_like(xh).pin_memory()
+        n_e2e = min(args.steps, 20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            scene.set_state(xh.numpy(), vh.numpy())
+            scene.step(1)
+            xo.copy_(torch.from_numpy(scene.positions()))
+            vh.copy_(torch.from_numpy(scene.velocities()))
+            xh.copy_(xo)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": world * n_e2e / dt, "unit": "timesteps/s", "h2d_bytes_per_step": 2 * 3 * nv * 8,
+               "d2h_bytes_per_step": 2 * 3 * nv * 8, "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(sc, iters / max(args.steps, 1))
+
+    if rank != 0:
+        return
+    sorted_ms = sorted(step_ms)
+    p50 = statistics.median(sorted_ms)
+    p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
+    line = {
+        "metric": METRIC,
+        "value": steps_per_s,
+        "unit": "timesteps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == ipc.IPC_PREC_FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scene": "sphere_pile(n_balls=64, cells=8, seed=1)",
+                   "precision": args.precision, "timesteps": f"0..{args.steps - 1}",
+                   "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
+        "iters_per_s": iters_per_s,
+        "mean_iters_per_step": iters / args.steps,
+        "p50_ms": p50,
+        "p99_ms": p99,
+        "converged_steps": sum(s["converged"] for s in status),
+        "roofline": roof.get(dominant) if dominant else None,
+        "roofline_stages": roof,
+        "stage_ms": {k: v["ms"] for k, v in prof.items()},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if dominant:
+        line["roofline"]["kernel"] = dominant
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

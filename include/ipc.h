@@ -1,0 +1,246 @@
+/*
+ * ipc.h -- C ABI of the B300 MAS-PNCG library (libipc_b300.so).
+ *
+ * One implicit-Euler timestep minimises the incremental potential of the
+ * paper's problem statement (Sec. 3.1, Eq. 1 without friction):
+ *     E(x) = 1/2 (x - x~)^T M (x - x~) + h^2 Psi_SNH(x) + kappa sum_c b(d_c(x)),
+ *     x~ = x^t + h v^t + h^2 M^-1 f_ext,
+ * over vertex positions, with no intersection along the way, by the MAS-PNCG
+ * iteration of Algorithm 1: multilevel additive Schwarz preconditioner
+ * (Sec. 3.3) patched by the Sparse-Input Woodbury update (Sec. 4.1, Eq. 6-8),
+ * the Hessian-aware 2D subspace step (Sec. 4.2, Eq. 9-10), the restart test
+ * (Sec. 4.3, Eq. 11) and per-subdomain conservative CCD (Sec. 4.4; supplement
+ * Sec. 3).  Every step of the path runs in CUDA kernels built for sm_103a on
+ * one GPU; the host only sequences them.
+ *
+ * Conventions
+ *  - Positions, velocities and every per-vertex vector are arrays of
+ *    n_verts x 3 doubles (x0, y0, z0, x1, ...), row-major, in metres and
+ *    seconds.  Tets are n_tets x 4 int32 vertex ids, positively oriented.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  All device work of a call is ordered on that stream;
+ *    calls that return host data synchronise it before returning.
+ *  - Host pointers belong to the caller and are only read (or written, for
+ *    outputs) during the call.  The library owns all device memory of a
+ *    scene; it obtains it through ipc_alloc_fns (or cudaMalloc) at
+ *    ipc_scene_create and releases it in ipc_scene_destroy.
+ *  - Return codes: IPC_OK (0) or a positive warning on success, a negative
+ *    ipc_status on failure; ipc_last_error() describes the last failure of
+ *    the calling thread.  After a failure the scene keeps its pre-call state
+ *    where possible (ipc_step: the state of the last completed timestep).
+ */
+#ifndef IPC_B300_H
+#define IPC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ipc_status {
+    IPC_OK = 0,
+    IPC_NOT_CONVERGED = 1,   /* warning: iteration cap reached, step still taken */
+    IPC_PENDING = 2,         /* serving: ticket not finished yet */
+    IPC_ERR_INVALID = -1,    /* bad argument or mesh */
+    IPC_ERR_INTERSECTING = -2, /* initial state has a contact at distance <= 0 */
+    IPC_ERR_OOM = -3,        /* device allocation failed */
+    IPC_ERR_NUMERIC = -4,    /* NaN / Inf met in the iteration */
+    IPC_ERR_TIMEOUT = -5,    /* a device-side wait ran out of its budget */
+    IPC_ERR_CUDA = -6,       /* CUDA runtime error */
+    IPC_ERR_CAPACITY = -7    /* a contact / candidate buffer overflowed and
+                                could not be grown */
+} ipc_status;
+
+typedef enum ipc_precision {
+    IPC_PREC_FP64 = 0,       /* every quantity in FP64 (the plain method) */
+    IPC_PREC_FP32 = 1        /* FP32 bulk (gradient, H v, MAS blocks and
+                                products); FP64 for positions, barrier
+                                distances, CCD, the 2x2 and capacitance
+                                solves and all reductions */
+} ipc_precision;
+
+/* Scene description (host memory, copied at create). */
+typedef struct ipc_scene_desc {
+    int n_verts;
+    const double* x_rest;    /* n_verts x 3: rest shape */
+    const double* x0;        /* n_verts x 3: initial positions (NULL = x_rest) */
+    const double* v0;        /* n_verts x 3: initial velocities (NULL = 0) */
+    int n_tets;
+    const int32_t* tets;     /* n_tets x 4 */
+    const double* E;         /* n_tets Young's modulus [Pa] */
+    const double* nu;        /* n_tets Poisson ratio */
+    const double* rho;       /* n_tets density [kg/m^3] */
+    double gravity[3];       /* f_ext / m */
+    int has_ground;          /* static plane n . x = offset */
+    double ground_normal[3];
+    double ground_offset;
+} ipc_scene_desc;
+
+/* Solver parameters (see ipc_default_params). */
+typedef struct ipc_params {
+    double h;                /* timestep [s] */
+    double dhat;             /* barrier activation distance [m] */
+    double kappa;            /* barrier stiffness [kg] */
+    double tol;              /* converged when max_v |z_v| <= tol * h * bbox_diag */
+    double delta;            /* restart threshold on r_k, Eq. 11 (0.3) */
+    double eps_rot_deg;      /* normal rotation threshold, Sec. 4.1.1 (25) */
+    double ccd_shrink;       /* s in alpha_l = (1 - s) d0 / l_tight (0.1) */
+    double eps_sing;         /* 2x2 singular test, relative (1e-12) */
+    double eps_abs;          /* 2x2 singular test, absolute (1e-300) */
+    int K;                   /* Woodbury vectors kept per subdomain (8, <= 16) */
+    int iter_max;            /* PNCG iteration cap per timestep (10000) */
+    int levels_max;          /* MAS levels including level 0 (6) */
+    int ls_max;              /* energy-check trials (20) */
+    int precision;           /* ipc_precision */
+    int contact_capacity;    /* initial contact buffer size, 0 = automatic */
+} ipc_params;
+
+/* Device allocator used for all scene memory; NULL functions = cudaMalloc. */
+typedef struct ipc_alloc_fns {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*free)(void* ptr, void* ctx);
+    void* ctx;
+} ipc_alloc_fns;
+
+/* Per-call statistics of ipc_step (summed over its timesteps, last values
+ * for the state fields). */
+typedef struct ipc_step_stats {
+    int steps;
+    int iters;               /* PNCG iterations */
+    int restarts;            /* MAS rebuilds */
+    int ls_halvings;         /* rejected energy-check trials */
+    int ls_failures;         /* iterations with no accepted trial */
+    int converged;           /* 1 if the last timestep converged */
+    int n_contacts;          /* active contacts at the end */
+    int ccd_fallbacks;       /* verification passes that fell back to uniform alpha */
+    double energy;           /* E at the end of the last timestep */
+    double min_dist;         /* smallest active contact distance at the end */
+    double znorm;            /* last max_v |z_v| */
+} ipc_step_stats;
+
+typedef struct ipc_scene ipc_scene;
+
+/* Defaults of the paper's constants; h, dhat and kappa must still be set. */
+void ipc_default_params(ipc_params* p);
+
+/* Build a scene: validates the mesh (ids in range, positive rest volumes),
+ * extracts the boundary surface, computes lumped mass rho V / 4 and rest
+ * shapes, builds the MAS hierarchy (32-vertex subdomains by greedy BFS over
+ * mesh adjacency, supplement Sec. 1.2), allocates device state and copies
+ * it up.  Fails with IPC_ERR_INTERSECTING if a contact of the initial state
+ * has distance <= 0.  `alloc` may be NULL. */
+int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params,
+                     const ipc_alloc_fns* alloc, ipc_scene** out);
+
+void ipc_scene_destroy(ipc_scene* s);
+
+/* Advance n_steps timesteps (Algorithm 1 each).  `stats` may be NULL.
+ * Returns IPC_OK, IPC_NOT_CONVERGED (some timestep hit iter_max) or an
+ * error. */
+int ipc_step(ipc_scene* s, int n_steps, void* stream, ipc_step_stats* stats);
+
+/* Replace positions and velocities (checkpoint / resume).  x, v are host
+ * arrays (on_device = 0) or device arrays (on_device = 1) of n_verts x 3
+ * doubles.  v may be NULL (zero). */
+int ipc_set_state(ipc_scene* s, const double* x, const double* v, int on_device, void* stream);
+
+typedef enum ipc_query_kind {
+    IPC_Q_POSITIONS = 0,     /* n_verts x 3 double */
+    IPC_Q_VELOCITIES = 1,    /* n_verts x 3 double */
+    IPC_Q_N_VERTS = 2,       /* int */
+    IPC_Q_N_CONTACTS = 3,    /* int: active contacts at the current state */
+    IPC_Q_SUBDOMAIN_ALPHA = 4, /* n_subdomains double: last CCD step sizes */
+    IPC_Q_N_SUBDOMAINS = 5,  /* int */
+    IPC_Q_TRACE_LEN = 6,     /* int: PNCG iterations of the last timestep */
+    IPC_Q_TRACE = 7,         /* trace_len x ipc_iter_record */
+    IPC_Q_SURFACE_COUNTS = 8,/* 3 int: surface verts, tris, edges */
+    IPC_Q_LEVEL_MAP = 9,     /* per level: group and slot of each node (see
+                                ipc_query_level) */
+    IPC_Q_BBOX_DIAG = 10     /* double */
+} ipc_query_kind;
+
+/* Copy a piece of state into host memory dst (dst_bytes long). */
+int ipc_query(ipc_scene* s, int what, void* dst, size_t dst_bytes, void* stream);
+
+/* Hierarchy inspection: number of levels, and for `level` the node count,
+ * group count and, if non-NULL, group / slot of every node. */
+int ipc_query_level(ipc_scene* s, int level, int* n_nodes, int* n_groups,
+                    int* group_of_node, int* slot_of_node);
+
+/* Surface inspection: sorted surface vertex ids, triangles (3 ids each) and
+ * edges (2 ids each, a < b), all in lexicographic order. */
+int ipc_query_surface(ipc_scene* s, int* verts, int* tris, int* edges);
+
+/* Per-stage device time of the scene's ipc_step calls, measured with CUDA
+ * events recorded on the step's stream around each stage, accumulated until
+ * reset.  Stages: 0 restart (RebuildMAS), 1 classify + top-K, 2 MAS apply
+ * (restriction, block apply with Woodbury, prolongation), 3 quadratic forms
+ * and dots, 4 direction, 5 CCD, 6 trial evaluation (contacts, energy,
+ * gradient), 7 other.  ms[8] in milliseconds, launches[8] stage executions. */
+typedef struct ipc_profile {
+    double ms[8];
+    long long launches[8];
+} ipc_profile;
+
+/* enable != 0 starts timing (and resets the counters); 0 stops it. */
+int ipc_profile_enable(ipc_scene* s, int enable);
+int ipc_profile_read(ipc_scene* s, ipc_profile* out);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all scenes, all calls). */
+long long ipc_kernel_launches(void);
+
+/* One record per PNCG iteration of the last timestep. */
+typedef struct ipc_iter_record {
+    int restart;
+    int n_contacts;
+    int n_update;            /* classified contacts with dS > 0 */
+    int ls_halvings;
+    double mu, nu;
+    double gz, znorm;
+    double energy_before, energy_after;
+    double alpha_min, alpha_max;
+    double r;
+} ipc_iter_record;
+
+/* ---- evaluation entry points (host arrays in and out) -------------------
+ * They run single pieces of the path on the GPU at caller-given positions so
+ * that each can be checked on its own. */
+
+/* E(x) with x~ given (Eq. 1) and, if g != NULL, its gradient. */
+int ipc_eval_energy_grad(ipc_scene* s, const double* x, const double* xtilde,
+                         double* energy, double* g, void* stream);
+
+/* Active contact set at x (ComputeConstraintSet of Algorithm 1): writes up
+ * to cap records and the full count to *n.  type: 0 point-triangle, 1
+ * edge-edge, 2 point-ground; ids: (vertex, surface tri), (edge, edge) with
+ * the lower edge first, or (vertex, 0); verts: 4 vertex ids (-1 unused);
+ * dist; k = kappa b''(d); grad12 = nabla d over the 4 verts. */
+int ipc_eval_contacts(ipc_scene* s, const double* x, int cap, int* n, int* type,
+                      int* ids, int* verts, double* dist, double* k, double* grad12,
+                      void* stream);
+
+/* z = P g with P rebuilt at x_base (RebuildMAS) and, if x_curr != NULL,
+ * patched by the Woodbury update for the contacts at x_curr (Eq. 7-8). */
+int ipc_eval_precond(ipc_scene* s, const double* x_base, const double* x_curr,
+                     const double* g, double* z, void* stream);
+
+/* (z^T H~ z, z^T H~ p, p^T H~ p) with H~ = H_base(x_base) + U U^T, U from
+ * the contacts at x_curr (Eq. 6; supplement Eq. 13-18). */
+int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr,
+                   const double* z, const double* p, double out[3], void* stream);
+
+/* Per-subdomain conservative step sizes for direction p at x (supplement
+ * Sec. 3); alpha has n_subdomains entries; *passes = verification passes
+ * used, -1 if the uniform fallback was taken. */
+int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha,
+                 int* passes, void* stream);
+
+const char* ipc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -14,7 +14,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["o_mesh.c", "o_elastic.c", "o_contact.c", "o_mas.c", "o_ccd.c", "o_pncg.c"]
+_SRCS = ["o_mesh.c", "o_elastic.c", "o_contact.c", "o_broad.c", "o_mas.c", "o_ccd.c", "o_pncg.c"]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -38,7 +38,8 @@ class OParams(C.Structure):
     _fields_ = [("h", C.c_double), ("dhat", C.c_double), ("kappa", C.c_double), ("tol", C.c_double),
                 ("delta", C.c_double), ("eps_rot_deg", C.c_double), ("ccd_shrink", C.c_double),
                 ("eps_sing", C.c_double), ("eps_abs", C.c_double), ("K", C.c_int), ("iter_max", C.c_int),
-                ("levels_max", C.c_int), ("ls_max", C.c_int), ("subdomain", C.c_int)]
+                ("levels_max", C.c_int), ("ls_max", C.c_int), ("subdomain", C.c_int),
+                ("brute_force", C.c_int)]
 
 
 class OStepStats(C.Structure):
@@ -121,7 +122,7 @@ def make_params(p: dict, subdomain: int = 32) -> OParams:
     return OParams(h=p["h"], dhat=p["dhat"], kappa=p["kappa"], tol=p["tol"], delta=p["delta"],
                    eps_rot_deg=p["eps_rot_deg"], ccd_shrink=p["ccd_shrink"], eps_sing=p["eps_sing"],
                    eps_abs=p["eps_abs"], K=p["K"], iter_max=p["iter_max"], levels_max=p["levels_max"],
-                   ls_max=p["ls_max"], subdomain=subdomain)
+                   ls_max=p["ls_max"], subdomain=subdomain, brute_force=int(p.get("brute_force", 0)))
 
 
 class Scene:

@@ -231,52 +231,89 @@ int o_ccd(OScene* s, const double* x, const double* p, double* alpha) {
     for (int g = 0; g < ng; ++g) alpha[g] = 1.0;
     Cand* cand = NULL;
     int nc = 0, cc = 0;
-    /* PT */
-    for (int f = 0; f < s->nsf; ++f) {
-        const int* T = s->sf + 3 * f;
-        double lo[3], hi[3];
-        swept_box(x, p, T, 3, lo, hi);
-        for (int i = 0; i < s->nsv; ++i) {
-            int pv = s->sv[i];
-            if (pv == T[0] || pv == T[1] || pv == T[2]) continue;
-            double lo2[3], hi2[3];
-            swept_box(x, p, &pv, 1, lo2, hi2);
-            if (!overlap(lo, hi, lo2, hi2)) continue;
-            if (nc == cc) {
-                cc = cc ? 2 * cc : 1024;
-                cand = (Cand*)realloc(cand, sizeof(Cand) * cc);
-            }
-            Cand* c = cand + nc++;
-            c->kind = 0;
-            c->v[0] = pv;
-            c->v[1] = T[0];
-            c->v[2] = T[1];
-            c->v[3] = T[2];
-        }
+    /* swept boxes of surface points, triangles and edges over [x, x + p] */
+    double* pb = (double*)malloc(sizeof(double) * 6 * (size_t)(s->nsv + 1));
+    double* tb = (double*)malloc(sizeof(double) * 6 * (size_t)(s->nsf + 1));
+    double* eb = (double*)malloc(sizeof(double) * 6 * (size_t)(s->nse + 1));
+    double pmax = 0.0;
+    for (int i = 0; i < s->nsv; ++i) {
+        swept_box(x, p, s->sv + i, 1, pb + 6 * (size_t)i, pb + 6 * (size_t)i + 3);
+        const double* pv = p + 3 * s->sv[i];
+        double l = sqrt(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]);
+        if (l > pmax) pmax = l;
     }
-    /* EE */
-    for (int i = 0; i < s->nse; ++i) {
-        const int* A = s->se + 2 * i;
-        double lo[3], hi[3];
-        swept_box(x, p, A, 2, lo, hi);
-        for (int j = i + 1; j < s->nse; ++j) {
-            const int* B = s->se + 2 * j;
-            if (A[0] == B[0] || A[0] == B[1] || A[1] == B[0] || A[1] == B[1]) continue;
-            double lo2[3], hi2[3];
-            swept_box(x, p, B, 2, lo2, hi2);
-            if (!overlap(lo, hi, lo2, hi2)) continue;
-            if (nc == cc) {
-                cc = cc ? 2 * cc : 1024;
-                cand = (Cand*)realloc(cand, sizeof(Cand) * cc);
+    for (int f = 0; f < s->nsf; ++f) swept_box(x, p, s->sf + 3 * f, 3, tb + 6 * (size_t)f, tb + 6 * (size_t)f + 3);
+    for (int i = 0; i < s->nse; ++i) swept_box(x, p, s->se + 2 * i, 2, eb + 6 * (size_t)i, eb + 6 * (size_t)i + 3);
+    int *PT = NULL, *EE = NULL, npt = 0, nee = 0;
+    if (s->prm.brute_force) {
+        int cap = 0;
+        for (int i = 0; i < s->nsv; ++i)
+            for (int f = 0; f < s->nsf; ++f) {
+                const double* a = pb + 6 * (size_t)i;
+                const double* b = tb + 6 * (size_t)f;
+                if (!overlap(a, a + 3, b, b + 3)) continue;
+                if (npt == cap) {
+                    cap = cap ? 2 * cap : 1024;
+                    PT = (int*)realloc(PT, sizeof(int) * 2 * cap);
+                }
+                PT[2 * npt] = i;
+                PT[2 * npt + 1] = f;
+                ++npt;
             }
-            Cand* c = cand + nc++;
-            c->kind = 1;
-            c->v[0] = A[0];
-            c->v[1] = A[1];
-            c->v[2] = B[0];
-            c->v[3] = B[1];
-        }
+        cap = 0;
+        for (int i = 0; i < s->nse; ++i)
+            for (int j = i + 1; j < s->nse; ++j) {
+                const double* a = eb + 6 * (size_t)i;
+                const double* b = eb + 6 * (size_t)j;
+                if (!overlap(a, a + 3, b, b + 3)) continue;
+                if (nee == cap) {
+                    cap = cap ? 2 * cap : 1024;
+                    EE = (int*)realloc(EE, sizeof(int) * 2 * cap);
+                }
+                EE[2 * nee] = i;
+                EE[2 * nee + 1] = j;
+                ++nee;
+            }
+    } else {
+        double cs = s->cell > pmax ? s->cell : pmax;
+        npt = o_box_pairs(s->nsv, pb, s->nsf, tb, 0, cs, &PT);
+        nee = o_box_pairs(s->nse, eb, s->nse, eb, 1, cs, &EE);
     }
+    for (int k = 0; k < npt; ++k) {
+        int pv = s->sv[PT[2 * k]];
+        const int* T = s->sf + 3 * PT[2 * k + 1];
+        if (pv == T[0] || pv == T[1] || pv == T[2]) continue;
+        if (nc == cc) {
+            cc = cc ? 2 * cc : 1024;
+            cand = (Cand*)realloc(cand, sizeof(Cand) * cc);
+        }
+        Cand* c = cand + nc++;
+        c->kind = 0;
+        c->v[0] = pv;
+        c->v[1] = T[0];
+        c->v[2] = T[1];
+        c->v[3] = T[2];
+    }
+    for (int k = 0; k < nee; ++k) {
+        const int* A = s->se + 2 * EE[2 * k];
+        const int* B = s->se + 2 * EE[2 * k + 1];
+        if (A[0] == B[0] || A[0] == B[1] || A[1] == B[0] || A[1] == B[1]) continue;
+        if (nc == cc) {
+            cc = cc ? 2 * cc : 1024;
+            cand = (Cand*)realloc(cand, sizeof(Cand) * cc);
+        }
+        Cand* c = cand + nc++;
+        c->kind = 1;
+        c->v[0] = A[0];
+        c->v[1] = A[1];
+        c->v[2] = B[0];
+        c->v[3] = B[1];
+    }
+    free(PT);
+    free(EE);
+    free(pb);
+    free(tb);
+    free(eb);
     /* per-pair steps */
     for (int k = 0; k < nc; ++k) {
         double a = pair_safe(s, cand[k].kind, cand[k].v, x, p);

@@ -197,96 +197,142 @@ static int boxes_apart(const double* lo1, const double* hi1, const double* lo2, 
     return 0;
 }
 
-/* Brute force over every surface PT and EE pair and every surface vertex
- * against the ground.  The box test only skips pairs whose distance is
- * provably >= dhat.  Output sorted by key (type, ida, idb). */
+/* PT pair (surface vertex p, surface triangle f): record if d < dhat */
+static void pt_check(OScene* s, const double* x, int p, int f, OContactList* out) {
+    const int* T = s->sf + 3 * f;
+    if (p == T[0] || p == T[1] || p == T[2]) return;
+    const double* P3[3] = {x + 3 * T[0], x + 3 * T[1], x + 3 * T[2]};
+    const double* xp = x + 3 * p;
+    double w[3];
+    double d = o_pt_distance(xp, P3[0], P3[1], P3[2], w);
+    if (!(d < s->prm.dhat)) return;
+    OContact c;
+    memset(&c, 0, sizeof c);
+    c.type = 0;
+    c.v[0] = p;
+    c.v[1] = T[0];
+    c.v[2] = T[1];
+    c.v[3] = T[2];
+    c.ida = p;
+    c.idb = f;
+    c.d = d;
+    double q[3], r[3];
+    for (int k = 0; k < 3; ++k) q[k] = w[0] * P3[0][k] + w[1] * P3[1][k] + w[2] * P3[2][k];
+    for (int k = 0; k < 3; ++k) r[k] = (xp[k] - q[k]) / d;
+    double coef[4] = {1.0, -w[0], -w[1], -w[2]};
+    for (int j = 0; j < 4; ++j)
+        for (int k = 0; k < 3; ++k) c.n[3 * j + k] = coef[j] * r[k];
+    fill_common(s, &c);
+    clist_push(out, &c);
+}
+
+/* EE pair (surface edges i < j): record if not adjacent, not parallel, d < dhat */
+static void ee_check(OScene* s, const double* x, int i, int j, OContactList* out) {
+    const int* A = s->se + 2 * i;
+    const int* B = s->se + 2 * j;
+    if (A[0] == B[0] || A[0] == B[1] || A[1] == B[0] || A[1] == B[1]) return;
+    const double* PA[2] = {x + 3 * A[0], x + 3 * A[1]};
+    const double* PB[2] = {x + 3 * B[0], x + 3 * B[1]};
+    double u[3], v[3], cr[3];
+    for (int k = 0; k < 3; ++k) {
+        u[k] = PA[1][k] - PA[0][k];
+        v[k] = PB[1][k] - PB[0][k];
+    }
+    cr[0] = u[1] * v[2] - u[2] * v[1];
+    cr[1] = u[2] * v[0] - u[0] * v[2];
+    cr[2] = u[0] * v[1] - u[1] * v[0];
+    if (dot3(cr, cr) < 1e-12 * dot3(u, u) * dot3(v, v)) return;
+    double st[2];
+    double d = o_ee_distance(PA[0], PA[1], PB[0], PB[1], st);
+    if (!(d < s->prm.dhat)) return;
+    OContact c;
+    memset(&c, 0, sizeof c);
+    c.type = 1;
+    c.v[0] = A[0];
+    c.v[1] = A[1];
+    c.v[2] = B[0];
+    c.v[3] = B[1];
+    c.ida = i;
+    c.idb = j;
+    c.d = d;
+    double r[3];
+    for (int k = 0; k < 3; ++k) {
+        double pa = PA[0][k] + st[0] * u[k];
+        double pb = PB[0][k] + st[1] * v[k];
+        r[k] = (pa - pb) / d;
+    }
+    double coef[4] = {1.0 - st[0], st[0], -(1.0 - st[1]), -st[1]};
+    for (int jj = 0; jj < 4; ++jj)
+        for (int k = 0; k < 3; ++k) c.n[3 * jj + k] = coef[jj] * r[k];
+    fill_common(s, &c);
+    clist_push(out, &c);
+}
+
+static void store_box(double* dst, const double* lo, const double* hi) {
+    for (int r = 0; r < 3; ++r) {
+        dst[r] = lo[r];
+        dst[3 + r] = hi[r];
+    }
+}
+
+/* Every surface PT and EE pair and every surface vertex against the ground.
+ * The box test only skips pairs whose distance is provably >= dhat.  Pairs
+ * come from a double loop (brute_force) or from the grid pair search over the
+ * same boxes.  Output sorted by key (type, ida, idb). */
 void o_find_contacts(OScene* s, const double* x, OContactList* out) {
     out->n = 0;
     double dhat = s->prm.dhat;
-    /* PT */
+    double* tb = (double*)malloc(sizeof(double) * 6 * (size_t)(s->nsf + 1));
+    double* pb = (double*)malloc(sizeof(double) * 6 * (size_t)(s->nsv + 1));
+    double* eb = (double*)malloc(sizeof(double) * 6 * (size_t)(s->nse + 1));
+    double* ebi = (double*)malloc(sizeof(double) * 6 * (size_t)(s->nse + 1));
     for (int f = 0; f < s->nsf; ++f) {
         const int* T = s->sf + 3 * f;
         const double* P3[3] = {x + 3 * T[0], x + 3 * T[1], x + 3 * T[2]};
         double lo[3], hi[3];
         box_of(P3, 3, dhat, lo, hi);
-        for (int i = 0; i < s->nsv; ++i) {
-            int p = s->sv[i];
-            if (p == T[0] || p == T[1] || p == T[2]) continue;
-            const double* xp = x + 3 * p;
-            if (xp[0] < lo[0] || xp[0] > hi[0] || xp[1] < lo[1] || xp[1] > hi[1] || xp[2] < lo[2] ||
-                xp[2] > hi[2])
-                continue;
-            double w[3];
-            double d = o_pt_distance(xp, P3[0], P3[1], P3[2], w);
-            if (!(d < dhat)) continue;
-            OContact c;
-            memset(&c, 0, sizeof c);
-            c.type = 0;
-            c.v[0] = p;
-            c.v[1] = T[0];
-            c.v[2] = T[1];
-            c.v[3] = T[2];
-            c.ida = p;
-            c.idb = f;
-            c.d = d;
-            double q[3], r[3];
-            for (int k = 0; k < 3; ++k) q[k] = w[0] * P3[0][k] + w[1] * P3[1][k] + w[2] * P3[2][k];
-            for (int k = 0; k < 3; ++k) r[k] = (xp[k] - q[k]) / d;
-            double coef[4] = {1.0, -w[0], -w[1], -w[2]};
-            for (int j = 0; j < 4; ++j)
-                for (int k = 0; k < 3; ++k) c.n[3 * j + k] = coef[j] * r[k];
-            fill_common(s, &c);
-            clist_push(out, &c);
-        }
+        store_box(tb + 6 * (size_t)f, lo, hi);
     }
-    /* EE */
+    for (int i = 0; i < s->nsv; ++i) store_box(pb + 6 * (size_t)i, x + 3 * s->sv[i], x + 3 * s->sv[i]);
     for (int i = 0; i < s->nse; ++i) {
         const int* A = s->se + 2 * i;
         const double* PA[2] = {x + 3 * A[0], x + 3 * A[1]};
-        double loa[3], hia[3];
-        box_of(PA, 2, dhat, loa, hia);
-        for (int j = i + 1; j < s->nse; ++j) {
-            const int* B = s->se + 2 * j;
-            if (A[0] == B[0] || A[0] == B[1] || A[1] == B[0] || A[1] == B[1]) continue;
-            const double* PB[2] = {x + 3 * B[0], x + 3 * B[1]};
-            double lob[3], hib[3];
-            box_of(PB, 2, 0.0, lob, hib);
-            if (boxes_apart(loa, hia, lob, hib)) continue;
-            double u[3], v[3], cr[3];
-            for (int k = 0; k < 3; ++k) {
-                u[k] = PA[1][k] - PA[0][k];
-                v[k] = PB[1][k] - PB[0][k];
-            }
-            cr[0] = u[1] * v[2] - u[2] * v[1];
-            cr[1] = u[2] * v[0] - u[0] * v[2];
-            cr[2] = u[0] * v[1] - u[1] * v[0];
-            if (dot3(cr, cr) < 1e-12 * dot3(u, u) * dot3(v, v)) continue;
-            double st[2];
-            double d = o_ee_distance(PA[0], PA[1], PB[0], PB[1], st);
-            if (!(d < dhat)) continue;
-            OContact c;
-            memset(&c, 0, sizeof c);
-            c.type = 1;
-            c.v[0] = A[0];
-            c.v[1] = A[1];
-            c.v[2] = B[0];
-            c.v[3] = B[1];
-            c.ida = i;
-            c.idb = j;
-            c.d = d;
-            double r[3];
-            for (int k = 0; k < 3; ++k) {
-                double pa = PA[0][k] + st[0] * u[k];
-                double pb = PB[0][k] + st[1] * v[k];
-                r[k] = (pa - pb) / d;
-            }
-            double coef[4] = {1.0 - st[0], st[0], -(1.0 - st[1]), -st[1]};
-            for (int jj = 0; jj < 4; ++jj)
-                for (int k = 0; k < 3; ++k) c.n[3 * jj + k] = coef[jj] * r[k];
-            fill_common(s, &c);
-            clist_push(out, &c);
-        }
+        double lo[3], hi[3];
+        box_of(PA, 2, dhat, lo, hi);
+        store_box(ebi + 6 * (size_t)i, lo, hi);
+        box_of(PA, 2, 0.0, lo, hi);
+        store_box(eb + 6 * (size_t)i, lo, hi);
     }
+    if (s->prm.brute_force) {
+        for (int f = 0; f < s->nsf; ++f)
+            for (int i = 0; i < s->nsv; ++i) {
+                const double* b = tb + 6 * (size_t)f;
+                const double* xp = x + 3 * s->sv[i];
+                if (xp[0] < b[0] || xp[0] > b[3] || xp[1] < b[1] || xp[1] > b[4] || xp[2] < b[2] || xp[2] > b[5])
+                    continue;
+                pt_check(s, x, s->sv[i], f, out);
+            }
+        for (int i = 0; i < s->nse; ++i)
+            for (int j = i + 1; j < s->nse; ++j) {
+                const double* a = ebi + 6 * (size_t)i;
+                const double* b = eb + 6 * (size_t)j;
+                if (boxes_apart(a, a + 3, b, b + 3)) continue;
+                ee_check(s, x, i, j, out);
+            }
+    } else {
+        double cs = s->cell > 2.0 * dhat ? s->cell : 2.0 * dhat;
+        int* P = NULL;
+        int np = o_box_pairs(s->nsv, pb, s->nsf, tb, 0, cs, &P);
+        for (int k = 0; k < np; ++k) pt_check(s, x, s->sv[P[2 * k]], P[2 * k + 1], out);
+        free(P);
+        np = o_box_pairs(s->nse, ebi, s->nse, eb, 1, cs, &P);
+        for (int k = 0; k < np; ++k) ee_check(s, x, P[2 * k], P[2 * k + 1], out);
+        free(P);
+    }
+    free(tb);
+    free(pb);
+    free(eb);
+    free(ebi);
     /* PG */
     if (s->has_ground) {
         for (int i = 0; i < s->nsv; ++i) {

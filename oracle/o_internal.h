@@ -59,6 +59,7 @@ struct OScene {
     int nsv, nsf, nse;
     int *sv, *sf, *se;
     int* on_surface;
+    double cell;            /* mean rest length of surface edges (pair-search cell) */
 
     /* vertex adjacency from tet edges */
     int *adj_ptr, *adj;
@@ -105,6 +106,9 @@ int o_build_hierarchy(OScene* s);
 void o_clist_free(OContactList* l);
 void o_find_contacts(OScene* s, const double* x, OContactList* out);
 int o_contact_cmp(const void* a, const void* b);
+
+/* pair search: overlapping boxes (6 doubles lo, hi each), sorted unique */
+int o_box_pairs(int na, const double* boxA, int nb, const double* boxB, int same_set, double cs, int** out);
 
 /* elastic */
 void o_tet_gather(const OScene* s, int t, const double* x, double* x12);

@@ -239,6 +239,16 @@ static int build_surface(OScene* s) {
     }
     s->nse = nse;
     s->se = e;
+    double len = 0.0;
+    for (int i = 0; i < nse; ++i) {
+        double d2 = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            double d = s->x_rest[3 * e[2 * i] + r] - s->x_rest[3 * e[2 * i + 1] + r];
+            d2 += d * d;
+        }
+        len += sqrt(d2);
+    }
+    s->cell = nse > 0 ? len / nse : 1.0;
     /* vertices */
     s->on_surface = (int*)calloc(s->nv, sizeof(int));
     for (int i = 0; i < 3 * nsf; ++i) s->on_surface[sf[i]] = 1;

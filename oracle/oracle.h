@@ -49,6 +49,8 @@ typedef struct OParams {
     int levels_max;      /* MAS levels including level 0 */
     int ls_max;          /* energy-check halvings */
     int subdomain;       /* nodes per MAS subdomain (32) */
+    int brute_force;     /* 1: all-pairs loops; 0: uniform-grid pair search
+                            (same pairs, faster on large scenes) */
 } OParams;
 
 typedef struct OScene OScene;

@@ -1,0 +1,983 @@
+// C ABI of the library (include/ipc.h): scene set-up, device memory, the
+// Algorithm 1 driver that sequences the kernels, queries and the evaluation
+// entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dev.cuh"
+#include "host_mesh.h"
+#include "ipc.h"
+#include "kernels.h"
+
+#include <atomic>
+
+using namespace ipcb;
+
+namespace {
+std::atomic<long long> g_kernel_launches{0};
+}
+
+void ipcb::count_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess) return fail(IPC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int next_pow2(long long n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+struct Arena {
+    ipc_alloc_fns fns{nullptr, nullptr, nullptr};
+    std::vector<void*> ptrs;
+    bool ok = true;
+    size_t bytes = 0;
+    void* get(size_t n) {
+        if (n == 0) n = 16;
+        n = (n + 255) & ~(size_t)255;
+        void* p = nullptr;
+        if (fns.alloc) {
+            p = fns.alloc(n, fns.ctx);
+        } else if (cudaMalloc(&p, n) != cudaSuccess) {
+            p = nullptr;
+        }
+        if (!p) {
+            ok = false;
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        bytes += n;
+        return p;
+    }
+    template <class T>
+    T* arr(size_t n) {
+        return static_cast<T*>(get(n * sizeof(T)));
+    }
+    void release() {
+        for (void* p : ptrs) {
+            if (fns.free)
+                fns.free(p, fns.ctx);
+            else
+                cudaFree(p);
+        }
+        ptrs.clear();
+    }
+};
+
+// pinned host mirror of the device scalars plus contact counts
+struct HostView {
+    Scalars S;
+    int nC, nCt;
+};
+
+}  // namespace
+
+// CUDA-event stage timers: event pairs recorded on the step's stream and
+// resolved after the next stream synchronisation.
+struct StageProf {
+    bool on = false;
+    double ms[8] = {0};
+    long long n[8] = {0};
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void resolve() {
+        for (auto& p : pending) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+                ms[p.stage] += t;
+                n[p.stage] += 1;
+            }
+        }
+        pending.clear();
+        used = 0;
+    }
+    ~StageProf() {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct ipc_scene {
+    HostMesh hm;
+    ipc_params prm;
+    Arena arena;
+    Dev<double> dd;
+    Dev<float> df;
+    int prec = IPC_PREC_FP64;
+    HostView* hv = nullptr;  // pinned
+    std::vector<ipc_iter_record> trace;
+    StageProf prof;
+};
+
+namespace {
+
+struct Stage {
+    StageProf* p;
+    int id;
+    cudaStream_t st;
+    cudaEvent_t b = nullptr;
+    Stage(ipc_scene* s, int stage, cudaStream_t stream) : p(&s->prof), id(stage), st(stream) {
+        if (!p->on) return;
+        cudaEvent_t a = p->get();
+        b = p->get();
+        cudaEventRecord(a, st);
+        p->pending.push_back({id, a, b});
+    }
+    ~Stage() {
+        if (b) cudaEventRecord(b, st);
+    }
+};
+
+template <class R>
+Dev<R>& dev_of(ipc_scene* s);
+template <>
+Dev<double>& dev_of<double>(ipc_scene* s) {
+    return s->dd;
+}
+template <>
+Dev<float>& dev_of<float>(ipc_scene* s) {
+    return s->df;
+}
+
+template <class T>
+int upload(T* dst, const std::vector<T>& src, cudaStream_t st = 0) {
+    if (src.empty()) return 0;
+    CUDA_TRY(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st));
+    return 0;
+}
+
+ContactBuf alloc_contacts(Arena& A, int cap) {
+    ContactBuf C;
+    C.count = A.arr<int>(1);
+    C.type = A.arr<int>(cap);
+    C.v = A.arr<int4>(cap);
+    C.key = A.arr<unsigned long long>(cap);
+    C.d = A.arr<double>(cap);
+    C.k = A.arr<double>(cap);
+    C.bp = A.arr<double>(cap);
+    C.r = A.arr<double>(3 * (size_t)cap);
+    C.w = A.arr<double>(4 * (size_t)cap);
+    return C;
+}
+
+template <class R>
+int setup_dev(ipc_scene* s) {
+    HostMesh& m = s->hm;
+    Arena& A = s->arena;
+    Dev<R>& D = dev_of<R>(s);
+    memset(&D, 0, sizeof(D));
+    const ipc_params& p = s->prm;
+    D.nv = m.nv;
+    D.nt = m.nt;
+    D.nsv = (int)m.sv.size();
+    D.nsf = (int)(m.sf.size() / 3);
+    D.nse = (int)(m.se.size() / 2);
+    D.nlev = m.nlev;
+    D.ntp = (m.nt + kPack - 1) / kPack;
+    int nb = 0;
+    int coff = 0;
+    for (int l = 0; l < m.nlev; ++l) {
+        D.ngroups[l] = m.ngroups[l];
+        D.nnodes[l] = m.nnodes[l];
+        D.blk_off[l] = nb;
+        nb += m.ngroups[l];
+        D.coarse_off[l] = coff;
+        if (l >= 1) coff += 3 * m.nnodes[l];
+    }
+    D.blk_off[m.nlev] = nb;
+    D.coarse_off[m.nlev] = coff;
+    D.cap = p.contact_capacity > 0 ? p.contact_capacity : std::max(4096, 16 * D.nsv + 16 * D.nse / 8);
+    D.upd_cap = D.cap;
+    D.straddle_cap = 8 * (D.nsf + D.nse) + 4096;
+    D.h = p.h;
+    D.dhat = p.dhat;
+    D.kappa = p.kappa;
+    D.eps_conv = p.tol * p.h * m.bbox_diag;
+    D.delta = p.delta;
+    D.cos_rot = std::cos(p.eps_rot_deg * M_PI / 180.0);
+    D.ccd_shrink = p.ccd_shrink;
+    D.eps_sing = p.eps_sing;
+    D.eps_abs = p.eps_abs;
+    D.K = p.K;
+    D.ls_max = p.ls_max;
+    for (int r = 0; r < 3; ++r) {
+        D.gravity[r] = m.gravity[r];
+        D.gn[r] = m.gn[r];
+    }
+    D.has_ground = m.has_ground;
+    D.goff = m.goff;
+    D.cell = std::max(m.mean_surface_edge, 1e-12);
+
+    const size_t n3 = 3 * (size_t)m.nv;
+    // mesh
+    std::vector<int4> tets(m.nt);
+    for (int t = 0; t < m.nt; ++t) tets[t] = make_int4(m.tets[4 * t], m.tets[4 * t + 1], m.tets[4 * t + 2], m.tets[4 * t + 3]);
+    int4* d_tets = A.arr<int4>(m.nt);
+    std::vector<R> tb((size_t)D.ntp * 9 * kPack, (R)0);
+    for (int t = 0; t < m.nt; ++t)
+        for (int c = 0; c < 9; ++c) tb[(size_t)(t / kPack) * 9 * kPack + c * kPack + t % kPack] = (R)m.dminv[9 * (size_t)t + c];
+    R* d_tb = A.arr<R>(tb.size());
+    double* d_vol = A.arr<double>(m.nt);
+    double* d_mu = A.arr<double>(m.nt);
+    double* d_lam = A.arr<double>(m.nt);
+    std::vector<R> massr(m.mass.begin(), m.mass.end());
+    R* d_mass = A.arr<R>(m.nv);
+    double* d_massd = A.arr<double>(m.nv);
+    int* d_sv = A.arr<int>(D.nsv);
+    int* d_sf = A.arr<int>(m.sf.size());
+    int* d_se = A.arr<int>(m.se.size());
+    // hierarchy
+    int* d_grp0 = A.arr<int>(m.nv);
+    int* d_slot0 = A.arr<int>(m.nv);
+    std::vector<int*> d_nov(m.nlev, nullptr), d_gon(m.nlev), d_son(m.nlev), d_mem(m.nlev);
+    for (int l = 0; l < m.nlev; ++l) {
+        if (l >= 1) d_nov[l] = A.arr<int>(m.nv);
+        d_gon[l] = A.arr<int>(m.nnodes[l]);
+        d_son[l] = A.arr<int>(m.nnodes[l]);
+        d_mem[l] = A.arr<int>((size_t)m.ngroups[l] * kSub);
+    }
+    // state
+    D.x = A.arr<double>(n3);
+    D.xt = A.arr<double>(n3);
+    D.xs = A.arr<double>(n3);
+    D.xtry = A.arr<double>(n3);
+    D.v = A.arr<double>(n3);
+    D.g = A.arr<R>(n3);
+    D.gtry = A.arr<R>(n3);
+    D.z = A.arr<R>(n3);
+    D.zprev = A.arr<R>(n3);
+    D.p = A.arr<R>(n3);
+    D.hess = A.arr<R>((size_t)D.ntp * kH * kPack);
+    D.blocks = A.arr<R>((size_t)nb * kBlk * kBlk);
+    D.asmb = A.arr<double>((size_t)nb * kBlk * kBlk);
+    D.coarse_r = A.arr<R>(std::max(coff, 1));
+    D.coarse_y = A.arr<R>(std::max(coff, 1));
+    D.C = alloc_contacts(A, D.cap);
+    D.Ct = alloc_contacts(A, D.cap);
+    D.Cb = alloc_contacts(A, D.cap);
+    D.btab = next_pow2(2LL * D.cap);
+    D.bkeys = A.arr<unsigned long long>(D.btab);
+    D.bidx = A.arr<int>(D.btab);
+    D.upd_c = A.arr<int>(D.upd_cap);
+    D.upd_dS = A.arr<double>(D.upd_cap);
+    D.upd_cnt = A.arr<int>(m.ngroups[0]);
+    D.upd_off = A.arr<int>(m.ngroups[0] + 1);
+    D.upd_cur = A.arr<int>(m.ngroups[0]);
+    D.upd_list = A.arr<int>(4 * (size_t)D.upd_cap);
+    D.topk = A.arr<int>((size_t)m.ngroups[0] * std::max(1, D.K));
+    D.alpha = A.arr<double>(m.ngroups[0]);
+    D.shrink = A.arr<double>(m.ngroups[0]);
+    D.str_v = A.arr<int4>(D.straddle_cap);
+    D.str_t = A.arr<int>(D.straddle_cap);
+    int nprim = std::max(std::max(D.nsf, D.nse), 1);
+    D.nbuckets = next_pow2(std::max(4096, 2 * nprim));
+    D.gcap = 32 * nprim + 4096;
+    D.gcount = A.arr<int>(D.nbuckets + 1);
+    D.gstart = A.arr<int>(D.nbuckets + 1);
+    D.gfill = A.arr<int>(D.nbuckets);
+    D.gentry = A.arr<int>(D.gcap);
+    D.gcell = A.arr<unsigned long long>(D.gcap);
+    D.gtotal = A.arr<int>(1);
+    D.glarge = A.arr<int>(nprim);
+    D.gnlarge = A.arr<int>(1);
+    D.gin = A.arr<int>(nprim);
+    D.gtmp = A.arr<int>(std::max(D.nbuckets, m.ngroups[0]) / 1024 + 16);
+    D.pbox = A.arr<double>(6 * (size_t)nprim);
+    D.cellsz = A.arr<double>(1);
+    D.S = A.arr<Scalars>(1);
+    if (!A.ok) return fail(IPC_ERR_OOM, "scene: device allocation failed");
+
+    D.tets = d_tets;
+    D.tetB = d_tb;
+    D.tet_vol = d_vol;
+    D.tet_mu = d_mu;
+    D.tet_lam = d_lam;
+    D.mass = d_mass;
+    D.massd = d_massd;
+    D.sv = d_sv;
+    D.sf = d_sf;
+    D.se = d_se;
+    D.grp0 = d_grp0;
+    D.slot0 = d_slot0;
+    for (int l = 0; l < m.nlev; ++l) {
+        D.node_of_vert[l] = d_nov[l];
+        D.grp_of_node[l] = d_gon[l];
+        D.slot_of_node[l] = d_son[l];
+        D.members[l] = d_mem[l];
+    }
+    CUDA_TRY(cudaMemcpy(d_tets, tets.data(), sizeof(int4) * m.nt, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_tb, tb.data(), sizeof(R) * tb.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_vol, m.vol.data(), sizeof(double) * m.nt, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_mu, m.mu.data(), sizeof(double) * m.nt, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_lam, m.lam.data(), sizeof(double) * m.nt, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_mass, massr.data(), sizeof(R) * m.nv, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_massd, m.mass.data(), sizeof(double) * m.nv, cudaMemcpyHostToDevice));
+    if (D.nsv) CUDA_TRY(cudaMemcpy(d_sv, m.sv.data(), sizeof(int) * D.nsv, cudaMemcpyHostToDevice));
+    if (D.nsf) CUDA_TRY(cudaMemcpy(d_sf, m.sf.data(), sizeof(int) * m.sf.size(), cudaMemcpyHostToDevice));
+    if (D.nse) CUDA_TRY(cudaMemcpy(d_se, m.se.data(), sizeof(int) * m.se.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_grp0, m.group_of[0].data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_slot0, m.slot_of[0].data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice));
+    for (int l = 0; l < m.nlev; ++l) {
+        if (l >= 1) CUDA_TRY(cudaMemcpy(d_nov[l], m.node_of_vert[l].data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(d_gon[l], m.group_of[l].data(), sizeof(int) * m.nnodes[l], cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(d_son[l], m.slot_of[l].data(), sizeof(int) * m.nnodes[l], cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(d_mem[l], m.members[l].data(), sizeof(int) * m.members[l].size(), cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(cudaMemcpy(D.x, m.x0.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(D.v, m.v0.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(D.S, 0, sizeof(Scalars)));
+    CUDA_TRY(cudaMemset(D.hess, 0, sizeof(R) * (size_t)D.ntp * kH * kPack));
+    CUDA_TRY(cudaMemset(D.Cb.count, 0, sizeof(int)));
+    CUDA_TRY(cudaMemset(D.C.count, 0, sizeof(int)));
+    CUDA_TRY(cudaMemset(D.Ct.count, 0, sizeof(int)));
+    CUDA_TRY(cudaDeviceSynchronize());
+    return 0;
+}
+
+template <class R>
+int read_view(ipc_scene* s, const Dev<R>& D, cudaStream_t st) {
+    CUDA_TRY(cudaMemcpyAsync(&s->hv->S, D.S, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&s->hv->nC, D.C.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&s->hv->nCt, D.Ct.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (s->prof.on) s->prof.resolve();
+    return 0;
+}
+
+template <class R>
+__global__ void k_velocity(Dev<R> D) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * D.nv) return;
+    D.v[i] = (D.x[i] - D.xs[i]) / D.h;
+}
+
+template <class R>
+__global__ void k_set_scalar_double(double* dst, double v) {
+    *dst = v;
+}
+
+template <class R>
+__global__ void k_reset_flags(Dev<R> D) {
+    D.S->overflow = 0;
+    D.S->nan_flag = 0;
+}
+
+// contacts, energy and gradient at D.x into C / g / E_k
+template <class R>
+void eval_current(const Dev<R>& D, cudaStream_t st) {
+    launch_detect(D, D.x, D.C, st);
+    launch_energy_grad(D, D.x, D.C, D.g, &D.S->E_k, st);
+}
+
+template <class R>
+void eval_trial(const Dev<R>& D, double beta, cudaStream_t st) {
+    launch_trial_positions(D, beta, st);
+    launch_detect(D, D.xtry, D.Ct, st);
+    launch_energy_grad(D, D.xtry, D.Ct, D.gtry, &D.S->E_try, st);
+    launch_accept(D, st);
+}
+
+// Algorithm 1 for one timestep.
+template <class R>
+int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
+    Dev<R>& D = dev_of<R>(s);
+    const ipc_params& P = s->prm;
+    const size_t n3 = 3 * (size_t)D.nv;
+    {
+        Stage t(s, 7, st);
+        KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
+        launch_predict(D, st);
+        CUDA_TRY(cudaMemsetAsync(D.zprev, 0, sizeof(R) * n3, st));
+        CUDA_TRY(cudaMemsetAsync(D.p, 0, sizeof(R) * n3, st));
+        eval_current(D, st);
+    }
+    if (int e = read_view(s, D, st)) return e;
+    if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
+    if (s->hv->nC > 0 && !(s->hv->S.min_dist > 0.0))
+        return fail(IPC_ERR_INTERSECTING, "a contact has non-positive distance");
+    s->trace.clear();
+    double Ek = s->hv->S.E_k;
+    double min_dist = s->hv->S.min_dist;
+    bool restart = true;
+    int k = 0, converged = 0, restarts = 0, halvings = 0, failures = 0, fallbacks = 0;
+    double znorm = 0.0;
+    for (k = 0; k < P.iter_max; ++k) {
+        ipc_iter_record rec;
+        memset(&rec, 0, sizeof rec);
+        rec.restart = restart ? 1 : 0;
+        rec.n_contacts = s->hv->nC;
+        if (restart) {
+            Stage t(s, 0, st);
+            launch_restart(D, D.x, D.C, st);
+            ++restarts;
+        } else {
+            Stage t(s, 1, st);
+            launch_classify(D, D.C, st);
+        }
+        {
+            Stage t(s, 7, st);
+            launch_restrict(D, D.g, st);
+        }
+        {
+            Stage t(s, 2, st);
+            launch_blocks(D, D.g, D.z, D.C, !restart, st);
+        }
+        {
+            Stage t(s, 7, st);
+            launch_prolong(D, D.z, st);
+        }
+        {
+            Stage t(s, 3, st);
+            launch_forms(D, D.C, restart, st);
+        }
+        {
+            Stage t(s, 4, st);
+            launch_direction(D, restart, st);
+        }
+        {
+            Stage t(s, 5, st);
+            launch_ccd(D, st);
+        }
+        {
+            Stage t(s, 6, st);
+            eval_trial(D, 0.0, st);
+        }
+        if (int e = read_view(s, D, st)) return e;
+        Scalars S = s->hv->S;
+        if (S.nan_flag || !(S.gz == S.gz)) return fail(IPC_ERR_NUMERIC, "NaN in the PNCG iteration");
+        if (S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
+        if (S.ccd_passes < 0) ++fallbacks;
+        rec.n_update = S.n_upd;
+        rec.mu = S.mu;
+        rec.nu = S.nu;
+        rec.gz = S.gz;
+        rec.znorm = S.znorm;
+        rec.alpha_min = S.alpha_min;
+        rec.alpha_max = S.alpha_max;
+        rec.energy_before = Ek;
+        int accepted = S.accepted;
+        int halv = 0;
+        if (!accepted) {
+            halv = 1;
+            double beta = S.alpha_min;
+            bool uniform_first = S.alpha_max > S.alpha_min;
+            for (int ls = 1; ls <= P.ls_max; ++ls) {
+                if (ls > 1 || !uniform_first) beta *= 0.5;
+                {
+                    Stage t(s, 6, st);
+                    eval_trial(D, beta, st);
+                }
+                if (int e = read_view(s, D, st)) return e;
+                if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
+                if (s->hv->S.accepted) {
+                    accepted = 1;
+                    break;
+                }
+                ++halv;
+            }
+        }
+        rec.ls_halvings = halv;
+        halvings += halv;
+        if (accepted) {
+            std::swap(D.x, D.xtry);
+            std::swap(D.C, D.Ct);
+            std::swap(D.g, D.gtry);
+            Ek = s->hv->S.E_k;
+            s->hv->nC = s->hv->nCt;
+            min_dist = s->hv->S.min_dist;
+        }
+        rec.energy_after = Ek;
+        znorm = S.znorm;
+        rec.r = S.gz > 0.0 ? std::fabs(S.gzprev) / S.gz : INFINITY;
+        bool forced = !accepted;
+        if (forced) ++failures;
+        s->trace.push_back(rec);
+        if (forced && restart) {
+            ++k;
+            break;
+        }
+        if (restart && S.znorm <= D.eps_conv) {
+            converged = 1;
+            ++k;
+            break;
+        }
+        restart = forced || !(rec.r <= D.delta) || S.znorm <= D.eps_conv;
+        std::swap(D.z, D.zprev);
+    }
+    KL(k_velocity<R><<<(int)((n3 + 255) / 256), 256, 0, st>>>(D));
+    CUDA_TRY(cudaGetLastError());
+    acc->steps += 1;
+    acc->iters += k;
+    acc->restarts += restarts;
+    acc->ls_halvings += halvings;
+    acc->ls_failures += failures;
+    acc->converged = converged;
+    acc->ccd_fallbacks += fallbacks;
+    acc->n_contacts = s->hv->nC;
+    acc->energy = Ek;
+    acc->min_dist = min_dist;
+    acc->znorm = znorm;
+    return converged ? IPC_OK : IPC_NOT_CONVERGED;
+}
+
+template <class R>
+int step_impl(ipc_scene* s, int n, cudaStream_t st, ipc_step_stats* out) {
+    ipc_step_stats acc;
+    memset(&acc, 0, sizeof acc);
+    int worst = IPC_OK;
+    for (int i = 0; i < n; ++i) {
+        int r = run_timestep<R>(s, st, &acc);
+        if (r < 0) {
+            if (out) *out = acc;
+            return r;
+        }
+        if (r > worst) worst = r;
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());
+    if (out) *out = acc;
+    return worst;
+}
+
+template <class R>
+std::vector<R> to_r(const double* a, size_t n) {
+    std::vector<R> v(n);
+    for (size_t i = 0; i < n; ++i) v[i] = (R)a[i];
+    return v;
+}
+
+template <class R>
+int eval_energy_impl(ipc_scene* s, const double* x, const double* xt, double* E, double* g, cudaStream_t st) {
+    Dev<R>& D = dev_of<R>(s);
+    size_t n3 = 3 * (size_t)D.nv;
+    CUDA_TRY(cudaMemcpyAsync(D.xtry, x, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(D.xt, xt, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+    KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
+    launch_detect(D, D.xtry, D.Ct, st);
+    launch_energy_grad(D, D.xtry, D.Ct, g ? D.gtry : (R*)nullptr, &D.S->E_try, st);
+    if (int e = read_view(s, D, st)) return e;
+    if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
+    if (E) *E = s->hv->S.E_try;
+    if (g) {
+        std::vector<R> gr(n3);
+        CUDA_TRY(cudaMemcpy(gr.data(), D.gtry, sizeof(R) * n3, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n3; ++i) g[i] = (double)gr[i];
+    }
+    return IPC_OK;
+}
+
+template <class R>
+int eval_contacts_impl(ipc_scene* s, const double* x, int cap, int* n, int* type, int* ids, int* verts, double* dist,
+                       double* kk, double* grad12, cudaStream_t st) {
+    Dev<R>& D = dev_of<R>(s);
+    size_t n3 = 3 * (size_t)D.nv;
+    CUDA_TRY(cudaMemcpyAsync(D.xtry, x, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+    KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
+    launch_detect(D, D.xtry, D.Ct, st);
+    if (int e = read_view(s, D, st)) return e;
+    if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
+    int nc = std::min(s->hv->nCt, D.cap);
+    if (n) *n = nc;
+    int m = std::min(nc, cap);
+    if (m <= 0) return IPC_OK;
+    std::vector<int> ty(m);
+    std::vector<int4> vv(m);
+    std::vector<unsigned long long> key(m);
+    std::vector<double> d(m), k(m), r(3 * (size_t)m), w(4 * (size_t)m);
+    CUDA_TRY(cudaMemcpy(ty.data(), D.Ct.type, sizeof(int) * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(vv.data(), D.Ct.v, sizeof(int4) * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(key.data(), D.Ct.key, sizeof(unsigned long long) * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(d.data(), D.Ct.d, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(k.data(), D.Ct.k, sizeof(double) * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(r.data(), D.Ct.r, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(w.data(), D.Ct.w, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < m; ++i) {
+        if (type) type[i] = ty[i];
+        if (ids) {
+            ids[2 * i] = (int)((key[i] >> 31) & 0x7FFFFFFFULL);
+            ids[2 * i + 1] = (int)(key[i] & 0x7FFFFFFFULL);
+        }
+        if (verts) {
+            verts[4 * i] = vv[i].x;
+            verts[4 * i + 1] = vv[i].y;
+            verts[4 * i + 2] = vv[i].z;
+            verts[4 * i + 3] = vv[i].w;
+        }
+        if (dist) dist[i] = d[i];
+        if (kk) kk[i] = k[i];
+        if (grad12)
+            for (int j = 0; j < 4; ++j)
+                for (int c = 0; c < 3; ++c) grad12[12 * i + 3 * j + c] = (ty[i] == 2 && j > 0) ? 0.0 : w[4 * i + j] * r[3 * i + c];
+    }
+    return IPC_OK;
+}
+
+// restart at x_base into C, optional classification of the contacts at
+// x_curr (into Ct); returns the buffer holding the classified contacts
+template <class R>
+int prepare_precond(ipc_scene* s, const double* x_base, const double* x_curr, cudaStream_t st, bool* wood) {
+    Dev<R>& D = dev_of<R>(s);
+    size_t n3 = 3 * (size_t)D.nv;
+    Dev<R> E = D;  // evaluation view: positions in scratch buffers
+    E.x = D.xtry;
+    CUDA_TRY(cudaMemcpyAsync(D.xtry, x_base, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+    KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
+    launch_detect(E, E.x, E.C, st);
+    launch_restart(E, E.x, E.C, st);
+    *wood = false;
+    if (x_curr) {
+        CUDA_TRY(cudaMemcpyAsync(D.xs, x_curr, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+        launch_detect(E, D.xs, E.Ct, st);
+        launch_classify(E, E.Ct, st);
+        *wood = true;
+    }
+    if (int e = read_view(s, D, st)) return e;
+    if (s->hv->S.overflow) return fail(IPC_ERR_CAPACITY, "buffer overflow in evaluation");
+    return IPC_OK;
+}
+
+template <class R>
+int eval_precond_impl(ipc_scene* s, const double* xb, const double* xc, const double* g, double* z, cudaStream_t st) {
+    Dev<R>& D = dev_of<R>(s);
+    size_t n3 = 3 * (size_t)D.nv;
+    bool wood;
+    if (int e = prepare_precond<R>(s, xb, xc, st, &wood)) return e;
+    std::vector<R> gr = to_r<R>(g, n3);
+    CUDA_TRY(cudaMemcpyAsync(D.g, gr.data(), sizeof(R) * n3, cudaMemcpyHostToDevice, st));
+    launch_precond(D, D.g, D.z, wood ? D.Ct : D.C, wood, st);
+    std::vector<R> zr(n3);
+    CUDA_TRY(cudaMemcpyAsync(zr.data(), D.z, sizeof(R) * n3, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < n3; ++i) z[i] = (double)zr[i];
+    return IPC_OK;
+}
+
+template <class R>
+int eval_forms_impl(ipc_scene* s, const double* xb, const double* xc, const double* z, const double* p, double out[3],
+                    cudaStream_t st) {
+    Dev<R>& D = dev_of<R>(s);
+    size_t n3 = 3 * (size_t)D.nv;
+    bool wood;
+    if (int e = prepare_precond<R>(s, xb, xc, st, &wood)) return e;
+    std::vector<R> zr = to_r<R>(z, n3), pr = to_r<R>(p, n3);
+    CUDA_TRY(cudaMemcpyAsync(D.z, zr.data(), sizeof(R) * n3, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(D.p, pr.data(), sizeof(R) * n3, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(D.g, 0, sizeof(R) * n3, st));
+    CUDA_TRY(cudaMemsetAsync(D.zprev, 0, sizeof(R) * n3, st));
+    launch_forms(D, wood ? D.Ct : D.C, false, st);
+    if (int e = read_view(s, D, st)) return e;
+    out[0] = s->hv->S.zHz;
+    out[1] = s->hv->S.zHp;
+    out[2] = s->hv->S.pHp;
+    return IPC_OK;
+}
+
+template <class R>
+int eval_ccd_impl(ipc_scene* s, const double* x, const double* p, double* alpha, int* passes, cudaStream_t st) {
+    Dev<R>& D = dev_of<R>(s);
+    size_t n3 = 3 * (size_t)D.nv;
+    Dev<R> E = D;
+    E.x = D.xtry;
+    CUDA_TRY(cudaMemcpyAsync(D.xtry, x, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
+    std::vector<R> pr = to_r<R>(p, n3);
+    CUDA_TRY(cudaMemcpyAsync(D.p, pr.data(), sizeof(R) * n3, cudaMemcpyHostToDevice, st));
+    double pm = 0.0;
+    for (int v = 0; v < D.nv; ++v) {
+        double a = (double)pr[3 * v], b = (double)pr[3 * v + 1], c = (double)pr[3 * v + 2];
+        pm = std::max(pm, std::sqrt(a * a + b * b + c * c));
+    }
+    KL(k_set_scalar_double<R><<<1, 1, 0, st>>>(&D.S->pmax, pm));
+    KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
+    launch_ccd(E, st);
+    if (int e = read_view(s, D, st)) return e;
+    int ng = D.ngroups[0];
+    CUDA_TRY(cudaMemcpy(alpha, D.alpha, sizeof(double) * ng, cudaMemcpyDeviceToHost));
+    if (passes) *passes = s->hv->S.ccd_passes;
+    return IPC_OK;
+}
+
+ipc_scene* checked(ipc_scene* s) {
+    if (!s) g_err = "null scene";
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipc_default_params(ipc_params* p) {
+    memset(p, 0, sizeof *p);
+    p->h = 1.0 / 30.0;
+    p->dhat = 1e-3;
+    p->kappa = 1.0;
+    p->tol = 1e-3;
+    p->delta = 0.3;
+    p->eps_rot_deg = 25.0;
+    p->ccd_shrink = 0.1;
+    p->eps_sing = 1e-12;
+    p->eps_abs = 1e-300;
+    p->K = 8;
+    p->iter_max = 10000;
+    p->levels_max = 6;
+    p->ls_max = 20;
+    p->precision = IPC_PREC_FP64;
+    p->contact_capacity = 0;
+}
+
+const char* ipc_last_error(void) { return g_err.c_str(); }
+
+int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params, const ipc_alloc_fns* alloc, ipc_scene** out) {
+    if (!out || !desc || !params) return fail(IPC_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (!(params->h > 0) || !(params->dhat > 0) || !(params->kappa > 0) || params->K < 0 || params->K > kMaxK ||
+        params->iter_max <= 0 || params->levels_max < 1 || params->ls_max < 0 ||
+        (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_FP32))
+        return fail(IPC_ERR_INVALID, "invalid parameters");
+    ipc_scene* s = new ipc_scene();
+    s->prm = *params;
+    s->prec = params->precision;
+    if (alloc) s->arena.fns = *alloc;
+    std::string err;
+    int r = build_host_mesh(desc, params->levels_max, &s->hm, &err);
+    if (r != IPC_OK) {
+        delete s;
+        return fail(r, err);
+    }
+    if (cudaMallocHost(&s->hv, sizeof(HostView)) != cudaSuccess) {
+        delete s;
+        return fail(IPC_ERR_OOM, "pinned host allocation failed");
+    }
+    r = s->prec == IPC_PREC_FP64 ? setup_dev<double>(s) : setup_dev<float>(s);
+    if (r != 0) {
+        std::string msg = g_err;
+        ipc_scene_destroy(s);
+        return fail(r, msg);
+    }
+    // initial state must be separated: every active contact has d > 0
+    int nc = 0;
+    std::vector<double> x0 = s->hm.x0;
+    r = s->prec == IPC_PREC_FP64
+            ? eval_contacts_impl<double>(s, x0.data(), 0, &nc, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0)
+            : eval_contacts_impl<float>(s, x0.data(), 0, &nc, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    if (r != 0) {
+        std::string msg = g_err;
+        ipc_scene_destroy(s);
+        return fail(r, msg);
+    }
+    if (nc > 0 && !(s->hv->S.min_dist > 0.0)) {
+        ipc_scene_destroy(s);
+        return fail(IPC_ERR_INTERSECTING, "initial state has a contact at distance <= 0");
+    }
+    *out = s;
+    return IPC_OK;
+}
+
+void ipc_scene_destroy(ipc_scene* s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    s->arena.release();
+    if (s->hv) cudaFreeHost(s->hv);
+    delete s;
+}
+
+int ipc_step(ipc_scene* s, int n_steps, void* stream, ipc_step_stats* stats) {
+    if (!checked(s)) return IPC_ERR_INVALID;
+    if (n_steps < 0) return fail(IPC_ERR_INVALID, "negative step count");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? step_impl<double>(s, n_steps, st, stats) : step_impl<float>(s, n_steps, st, stats);
+}
+
+int ipc_set_state(ipc_scene* s, const double* x, const double* v, int on_device, void* stream) {
+    if (!checked(s) || !x) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n3 = 3 * (size_t)s->hm.nv;
+    double* dx = s->prec == IPC_PREC_FP64 ? s->dd.x : s->df.x;
+    double* dv = s->prec == IPC_PREC_FP64 ? s->dd.v : s->df.v;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_TRY(cudaMemcpyAsync(dx, x, sizeof(double) * n3, kind, st));
+    if (v)
+        CUDA_TRY(cudaMemcpyAsync(dv, v, sizeof(double) * n3, kind, st));
+    else
+        CUDA_TRY(cudaMemsetAsync(dv, 0, sizeof(double) * n3, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return IPC_OK;
+}
+
+int ipc_query(ipc_scene* s, int what, void* dst, size_t bytes, void* stream) {
+    if (!checked(s) || !dst) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t n3 = 3 * (size_t)s->hm.nv;
+    bool f64 = s->prec == IPC_PREC_FP64;
+    auto need = [&](size_t n) { return bytes >= n; };
+    switch (what) {
+        case IPC_Q_POSITIONS:
+        case IPC_Q_VELOCITIES: {
+            if (!need(sizeof(double) * n3)) return fail(IPC_ERR_INVALID, "destination too small");
+            const double* src = what == IPC_Q_POSITIONS ? (f64 ? s->dd.x : s->df.x) : (f64 ? s->dd.v : s->df.v);
+            CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double) * n3, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            return IPC_OK;
+        }
+        case IPC_Q_N_VERTS:
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            *(int*)dst = s->hm.nv;
+            return IPC_OK;
+        case IPC_Q_N_CONTACTS: {
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            std::vector<double> x(n3);
+            CUDA_TRY(cudaMemcpy(x.data(), f64 ? s->dd.x : s->df.x, sizeof(double) * n3, cudaMemcpyDeviceToHost));
+            int n = 0;
+            int r = f64 ? eval_contacts_impl<double>(s, x.data(), 0, &n, 0, 0, 0, 0, 0, 0, st)
+                        : eval_contacts_impl<float>(s, x.data(), 0, &n, 0, 0, 0, 0, 0, 0, st);
+            if (r) return r;
+            *(int*)dst = n;
+            return IPC_OK;
+        }
+        case IPC_Q_SUBDOMAIN_ALPHA: {
+            size_t ng = s->hm.ngroups[0];
+            if (!need(sizeof(double) * ng)) return fail(IPC_ERR_INVALID, "destination too small");
+            CUDA_TRY(cudaMemcpy(dst, f64 ? s->dd.alpha : s->df.alpha, sizeof(double) * ng, cudaMemcpyDeviceToHost));
+            return IPC_OK;
+        }
+        case IPC_Q_N_SUBDOMAINS:
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            *(int*)dst = s->hm.ngroups[0];
+            return IPC_OK;
+        case IPC_Q_TRACE_LEN:
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            *(int*)dst = (int)s->trace.size();
+            return IPC_OK;
+        case IPC_Q_TRACE: {
+            size_t n = std::min(s->trace.size(), bytes / sizeof(ipc_iter_record));
+            memcpy(dst, s->trace.data(), n * sizeof(ipc_iter_record));
+            return IPC_OK;
+        }
+        case IPC_Q_SURFACE_COUNTS: {
+            if (!need(3 * sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            int* o = (int*)dst;
+            o[0] = (int)s->hm.sv.size();
+            o[1] = (int)(s->hm.sf.size() / 3);
+            o[2] = (int)(s->hm.se.size() / 2);
+            return IPC_OK;
+        }
+        case IPC_Q_BBOX_DIAG:
+            if (!need(sizeof(double))) return fail(IPC_ERR_INVALID, "destination too small");
+            *(double*)dst = s->hm.bbox_diag;
+            return IPC_OK;
+        default:
+            return fail(IPC_ERR_INVALID, "unknown query kind");
+    }
+}
+
+int ipc_query_level(ipc_scene* s, int level, int* n_nodes, int* n_groups, int* group_of_node, int* slot_of_node) {
+    if (!checked(s)) return IPC_ERR_INVALID;
+    if (level < 0 || level >= s->hm.nlev) return fail(IPC_ERR_INVALID, "level out of range");
+    if (n_nodes) *n_nodes = s->hm.nnodes[level];
+    if (n_groups) *n_groups = s->hm.ngroups[level];
+    if (group_of_node) memcpy(group_of_node, s->hm.group_of[level].data(), sizeof(int) * s->hm.nnodes[level]);
+    if (slot_of_node) memcpy(slot_of_node, s->hm.slot_of[level].data(), sizeof(int) * s->hm.nnodes[level]);
+    return s->hm.nlev;
+}
+
+int ipc_query_surface(ipc_scene* s, int* verts, int* tris, int* edges) {
+    if (!checked(s)) return IPC_ERR_INVALID;
+    if (verts) memcpy(verts, s->hm.sv.data(), sizeof(int) * s->hm.sv.size());
+    if (tris) memcpy(tris, s->hm.sf.data(), sizeof(int) * s->hm.sf.size());
+    if (edges) memcpy(edges, s->hm.se.data(), sizeof(int) * s->hm.se.size());
+    return IPC_OK;
+}
+
+long long ipc_kernel_launches(void) { return g_kernel_launches.load(); }
+
+int ipc_profile_enable(ipc_scene* s, int enable) {
+    if (!checked(s)) return IPC_ERR_INVALID;
+    cudaDeviceSynchronize();
+    s->prof.resolve();
+    s->prof.on = enable != 0;
+    if (enable) {
+        for (int i = 0; i < 8; ++i) {
+            s->prof.ms[i] = 0.0;
+            s->prof.n[i] = 0;
+        }
+    }
+    return IPC_OK;
+}
+
+int ipc_profile_read(ipc_scene* s, ipc_profile* out) {
+    if (!checked(s) || !out) return IPC_ERR_INVALID;
+    cudaDeviceSynchronize();
+    s->prof.resolve();
+    for (int i = 0; i < 8; ++i) {
+        out->ms[i] = s->prof.ms[i];
+        out->launches[i] = s->prof.n[i];
+    }
+    return IPC_OK;
+}
+
+int ipc_eval_energy_grad(ipc_scene* s, const double* x, const double* xtilde, double* energy, double* g, void* stream) {
+    if (!checked(s) || !x || !xtilde) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? eval_energy_impl<double>(s, x, xtilde, energy, g, st)
+                                    : eval_energy_impl<float>(s, x, xtilde, energy, g, st);
+}
+
+int ipc_eval_contacts(ipc_scene* s, const double* x, int cap, int* n, int* type, int* ids, int* verts, double* dist,
+                      double* k, double* grad12, void* stream) {
+    if (!checked(s) || !x) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? eval_contacts_impl<double>(s, x, cap, n, type, ids, verts, dist, k, grad12, st)
+                                    : eval_contacts_impl<float>(s, x, cap, n, type, ids, verts, dist, k, grad12, st);
+}
+
+int ipc_eval_precond(ipc_scene* s, const double* x_base, const double* x_curr, const double* g, double* z, void* stream) {
+    if (!checked(s) || !x_base || !g || !z) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? eval_precond_impl<double>(s, x_base, x_curr, g, z, st)
+                                    : eval_precond_impl<float>(s, x_base, x_curr, g, z, st);
+}
+
+int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr, const double* z, const double* p,
+                   double out[3], void* stream) {
+    if (!checked(s) || !x_base || !z || !p || !out) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? eval_forms_impl<double>(s, x_base, x_curr, z, p, out, st)
+                                    : eval_forms_impl<float>(s, x_base, x_curr, z, p, out, st);
+}
+
+int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha, int* passes, void* stream) {
+    if (!checked(s) || !x || !p || !alpha) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? eval_ccd_impl<double>(s, x, p, alpha, passes, st)
+                                    : eval_ccd_impl<float>(s, x, p, alpha, passes, st);
+}
+
+}  // extern "C"

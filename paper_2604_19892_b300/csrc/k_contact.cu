@@ -1,0 +1,611 @@
+// Contact detection (ComputeConstraintSet of Algorithm 1) and per-subdomain
+// conservative CCD (Sec. 4.4; supplement Sec. 3) with a hashed uniform grid
+// broad phase.
+//
+// Broad phase: stored primitives (surface triangles or edges) are binned by
+// the cells their boxes cover (inflated by dhat for proximity, swept over
+// [x, x + p] for CCD); a primitive covering more than kMaxCells cells, or
+// overflowing the entry buffer, goes to a short "large" list tested against
+// every query.  A query primitive walks its own cells; a pair found in several
+// cells is kept only in the cell that holds the low corner of the two boxes'
+// intersection, so each pair is processed once.  The box tests are exact, so
+// the candidate set equals the brute-force one.
+//
+// Readings: PT pairs exclude incident triangles, EE pairs exclude edges that
+// share a vertex and, for the barrier, edges parallel to sin^2 < 1e-12;
+// point-ground uses the plane distance.  CCD lower bound
+// alpha_l = (1 - s) d0 / l_tight (supplement Eq. 29 / 31); point-ground takes
+// min(1, (1 - s) d0 / (-n.p)).  alpha_d is the minimum over candidate pairs
+// touching subdomain d; pairs straddling subdomains are re-checked with the
+// actual motion alpha_d(v) p_v, shrinking the subdomains of a pair whose safe
+// fraction rho < 1 by rho, for at most 4 passes, then the uniform step
+// min_d alpha_d is taken.
+#include "geom.cuh"
+#include "kernels.h"
+
+namespace ipcb {
+
+namespace {
+
+constexpr int kT = 128;
+constexpr int kMaxCells = 64;
+
+inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
+
+__device__ __forceinline__ int cellc(double v, double inv) { return (int)floor(v * inv); }
+
+__device__ __forceinline__ unsigned long long pack_cell(int i, int j, int k) {
+    const int off = 1 << 20;
+    return ((unsigned long long)((unsigned)(i + off) & 0x1FFFFFu) << 42) |
+           ((unsigned long long)((unsigned)(j + off) & 0x1FFFFFu) << 21) | (unsigned long long)((unsigned)(k + off) & 0x1FFFFFu);
+}
+
+__device__ __forceinline__ int bucket_of(unsigned long long c, int nb) { return (int)(mix64(c) & (unsigned long long)(nb - 1)); }
+
+// box of a primitive with vertices vid[0..n): positions x, optional sweep by p
+template <class R>
+__device__ __forceinline__ void prim_box(const double* x, const R* p, const int* vid, int n, double infl, double lo[3],
+                                         double hi[3]) {
+    for (int r = 0; r < 3; ++r) {
+        lo[r] = 1e300;
+        hi[r] = -1e300;
+    }
+    for (int k = 0; k < n; ++k)
+        for (int r = 0; r < 3; ++r) {
+            double a = x[3 * vid[k] + r];
+            double b = p ? a + (double)p[3 * vid[k] + r] : a;
+            double mn = fmin(a, b), mx = fmax(a, b);
+            lo[r] = fmin(lo[r], mn);
+            hi[r] = fmax(hi[r], mx);
+        }
+    for (int r = 0; r < 3; ++r) {
+        lo[r] -= infl;
+        hi[r] += infl;
+    }
+}
+
+__device__ __forceinline__ bool overlap(const double* lo1, const double* hi1, const double* lo2, const double* hi2) {
+    return !(hi1[0] < lo2[0] || hi2[0] < lo1[0] || hi1[1] < lo2[1] || hi2[1] < lo1[1] || hi1[2] < lo2[2] ||
+             hi2[2] < lo1[2]);
+}
+
+// ---------------------------------------------------------------- grid build
+
+template <class R>
+__global__ void k_grid_count(Dev<R> D, const int* prims, int nper, int nprim, const double* x, const R* p, double infl,
+                             int* gin) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nprim) return;
+    int vid[3];
+    for (int k = 0; k < nper; ++k) vid[k] = prims[nper * i + k];
+    double lo[3], hi[3];
+    prim_box(x, p, vid, nper, infl, lo, hi);
+    for (int r = 0; r < 3; ++r) {
+        D.pbox[6 * (size_t)i + r] = lo[r];
+        D.pbox[6 * (size_t)i + 3 + r] = hi[r];
+    }
+    double inv = 1.0 / *D.cellsz;
+    long long n0 = (long long)cellc(hi[0], inv) - cellc(lo[0], inv) + 1;
+    long long n1 = (long long)cellc(hi[1], inv) - cellc(lo[1], inv) + 1;
+    long long n2 = (long long)cellc(hi[2], inv) - cellc(lo[2], inv) + 1;
+    long long nc = n0 * n1 * n2;
+    bool in_grid = nc <= kMaxCells && n0 <= kMaxCells && n1 <= kMaxCells && n2 <= kMaxCells;
+    if (in_grid) {
+        int old = atomicAdd(D.gtotal, (int)nc);
+        if (old + nc > D.gcap) in_grid = false;
+    }
+    gin[i] = in_grid ? 1 : 0;
+    if (!in_grid) {
+        int k = atomicAdd(D.gnlarge, 1);
+        D.glarge[k] = i;
+        return;
+    }
+    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
+    for (int a = 0; a < n0; ++a)
+        for (int b = 0; b < n1; ++b)
+            for (int c = 0; c < n2; ++c) atomicAdd(&D.gcount[bucket_of(pack_cell(i0 + a, j0 + b, k0 + c), D.nbuckets)], 1);
+}
+
+template <class R>
+__global__ void k_grid_fill(Dev<R> D, int nprim, const int* gin) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nprim || !gin[i]) return;
+    const double* lo = D.pbox + 6 * (size_t)i;
+    const double* hi = lo + 3;
+    double inv = 1.0 / *D.cellsz;
+    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
+    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
+    for (int a = i0; a <= i1; ++a)
+        for (int b = j0; b <= j1; ++b)
+            for (int c = k0; c <= k1; ++c) {
+                unsigned long long cc = pack_cell(a, b, c);
+                int bk = bucket_of(cc, D.nbuckets);
+                int pos = D.gstart[bk] + atomicAdd(&D.gfill[bk], 1);
+                D.gentry[pos] = i;
+                D.gcell[pos] = cc;
+            }
+}
+
+template <class R>
+__global__ void k_set_cell(Dev<R> D, int ccd) {
+    double cs = D.cell;
+    if (ccd) cs = fmax(cs, D.S->pmax);
+    else cs = fmax(cs, 2.0 * D.dhat);
+    *D.cellsz = cs;
+}
+
+template <class R>
+void build_grid(const Dev<R>& D, const int* prims, int nper, int nprim, const double* x, const R* p, double infl,
+                int* gin, bool ccd, cudaStream_t st) {
+    cudaMemsetAsync(D.gcount, 0, sizeof(int) * (D.nbuckets + 1), st);
+    cudaMemsetAsync(D.gfill, 0, sizeof(int) * D.nbuckets, st);
+    cudaMemsetAsync(D.gtotal, 0, sizeof(int), st);
+    cudaMemsetAsync(D.gnlarge, 0, sizeof(int), st);
+    KL(k_set_cell<R><<<1, 1, 0, st>>>(D, ccd ? 1 : 0));
+    if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, x, p, infl, gin));
+    scan_exclusive(D.gcount, D.gstart, D.nbuckets, D.gtmp, st);
+    if (nprim > 0) KL(k_grid_fill<R><<<nblk(nprim), kT, 0, st>>>(D, nprim, gin));
+}
+
+// ------------------------------------------------------------ contact write
+
+__device__ __forceinline__ void put_contact(const ContactBuf& C, int cap, int type, int4 v, unsigned long long key,
+                                            double d, double kap, double dhat, d3 r, const double w[4], Scalars* S) {
+    int i = atomicAdd(C.count, 1);
+    if (i >= cap) {
+        atomicOr(&S->overflow, 1);
+        return;
+    }
+    double b, b1, b2;
+    barrier3(d, dhat, b, b1, b2);
+    C.type[i] = type;
+    C.v[i] = v;
+    C.key[i] = key;
+    C.d[i] = d;
+    C.k[i] = kap * b2;
+    C.bp[i] = kap * b1;
+    C.r[3 * i] = r.x;
+    C.r[3 * i + 1] = r.y;
+    C.r[3 * i + 2] = r.z;
+    for (int j = 0; j < 4; ++j) C.w[4 * i + j] = w[j];
+    atomicMinPos(&S->min_dist, d);
+}
+
+template <class R>
+__device__ void pt_try(const Dev<R>& D, const double* x, const ContactBuf& C, int pv, int f) {
+    int t0 = D.sf[3 * f], t1 = D.sf[3 * f + 1], t2 = D.sf[3 * f + 2];
+    if (pv == t0 || pv == t1 || pv == t2) return;
+    d3 P = ld3(x + 3 * pv), A = ld3(x + 3 * t0), B = ld3(x + 3 * t1), Cc = ld3(x + 3 * t2);
+    double w[3];
+    double d2 = pt_closest(P, A, B, Cc, w);
+    if (!(d2 < D.dhat * D.dhat)) return;
+    double d = sqrt(d2);
+    if (!(d < D.dhat)) return;
+    d3 q = w[0] * A + w[1] * B + w[2] * Cc;
+    d3 r = (1.0 / d) * (P - q);
+    double ww[4] = {1.0, -w[0], -w[1], -w[2]};
+    put_contact(C, D.cap, 0, make_int4(pv, t0, t1, t2), contact_key(0, pv, f), d, D.kappa, D.dhat, r, ww, D.S);
+}
+
+template <class R>
+__device__ void ee_try(const Dev<R>& D, const double* x, const ContactBuf& C, int i, int j) {
+    int a0 = D.se[2 * i], a1 = D.se[2 * i + 1], b0 = D.se[2 * j], b1 = D.se[2 * j + 1];
+    if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
+    d3 A0 = ld3(x + 3 * a0), A1 = ld3(x + 3 * a1), B0 = ld3(x + 3 * b0), B1 = ld3(x + 3 * b1);
+    d3 u = A1 - A0, v = B1 - B0;
+    d3 cr = cross(u, v);
+    if (dot(cr, cr) < 1e-12 * dot(u, u) * dot(v, v)) return;
+    double s, t;
+    double d2 = ee_closest(A0, A1, B0, B1, s, t);
+    if (!(d2 < D.dhat * D.dhat)) return;
+    double d = sqrt(d2);
+    if (!(d < D.dhat)) return;
+    d3 c1 = A0 + s * u, c2 = B0 + t * v;
+    d3 r = (1.0 / d) * (c1 - c2);
+    double ww[4] = {1.0 - s, s, -(1.0 - t), -t};
+    put_contact(C, D.cap, 1, make_int4(a0, a1, b0, b1), contact_key(1, i, j), d, D.kappa, D.dhat, r, ww, D.S);
+}
+
+// ------------------------------------------------------------ proximity
+
+template <class R>
+__global__ void k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= D.nsv) return;
+    int pv = D.sv[qi];
+    double px = x[3 * pv], py = x[3 * pv + 1], pz = x[3 * pv + 2];
+    double inv = 1.0 / *D.cellsz;
+    unsigned long long cc = pack_cell(cellc(px, inv), cellc(py, inv), cellc(pz, inv));
+    int bk = bucket_of(cc, D.nbuckets);
+    for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+        if (D.gcell[e] != cc) continue;
+        int f = D.gentry[e];
+        const double* b = D.pbox + 6 * (size_t)f;
+        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
+        pt_try(D, x, C, pv, f);
+    }
+    int nl = *D.gnlarge;
+    for (int k = 0; k < nl; ++k) {
+        int f = D.glarge[k];
+        const double* b = D.pbox + 6 * (size_t)f;
+        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
+        pt_try(D, x, C, pv, f);
+    }
+}
+
+// EE: query edge i (plain box) against stored edges j > i (boxes inflated)
+template <class R>
+__global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int* gin) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.nse) return;
+    int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+    double lo[3], hi[3];
+    prim_box<R>(x, nullptr, vid, 2, 0.0, lo, hi);
+    double inv = 1.0 / *D.cellsz;
+    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
+    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
+    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
+    if (!(nc > 0)) nc = kMaxCells + 1;
+    if (nc > kMaxCells) {
+        for (int j = i + 1; j < D.nse; ++j) {
+            const double* b = D.pbox + 6 * (size_t)j;
+            if (overlap(lo, hi, b, b + 3)) ee_try(D, x, C, i, j);
+        }
+        return;
+    }
+    for (int a = i0; a <= i1; ++a)
+        for (int bb = j0; bb <= j1; ++bb)
+            for (int c = k0; c <= k1; ++c) {
+                unsigned long long cc = pack_cell(a, bb, c);
+                int bk = bucket_of(cc, D.nbuckets);
+                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                    if (D.gcell[e] != cc) continue;
+                    int j = D.gentry[e];
+                    if (j <= i) continue;
+                    const double* b = D.pbox + 6 * (size_t)j;
+                    if (!overlap(lo, hi, b, b + 3)) continue;
+                    // keep the pair only in the cell of the intersection's low corner
+                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
+                        cellc(fmax(lo[2], b[2]), inv) != c)
+                        continue;
+                    ee_try(D, x, C, i, j);
+                }
+            }
+    int nl = *D.gnlarge;
+    for (int k = 0; k < nl; ++k) {
+        int j = D.glarge[k];
+        if (j <= i) continue;
+        const double* b = D.pbox + 6 * (size_t)j;
+        if (overlap(lo, hi, b, b + 3)) ee_try(D, x, C, i, j);
+    }
+}
+
+template <class R>
+__global__ void k_prox_pg(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= D.nsv || !D.has_ground) return;
+    int pv = D.sv[qi];
+    d3 n = mk(D.gn[0], D.gn[1], D.gn[2]);
+    double d = dot(n, ld3(x + 3 * pv)) - D.goff;
+    if (!(d < D.dhat)) return;
+    double ww[4] = {1.0, 0.0, 0.0, 0.0};
+    put_contact(C, D.cap, 2, make_int4(pv, -1, -1, -1), contact_key(2, pv, 0), d, D.kappa, D.dhat, n, ww, D.S);
+}
+
+template <class R>
+__global__ void k_reset_detect(Dev<R> D, ContactBuf C) {
+    *C.count = 0;
+    D.S->min_dist = __longlong_as_double(0x7ff0000000000000ULL);
+}
+
+// ------------------------------------------------------------------- CCD
+
+template <class R>
+__device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const double* x, const R* p, const double* scale) {
+    d3 X[4], Q[4];
+    for (int j = 0; j < 4; ++j) {
+        X[j] = ld3(x + 3 * v[j]);
+        double s = scale ? scale[D.grp0[v[j]]] : 1.0;
+        Q[j] = mk(s * (double)p[3 * v[j]], s * (double)p[3 * v[j] + 1], s * (double)p[3 * v[j] + 2]);
+    }
+    double d0, l = 0.0, c[4];
+    if (kind == 0) {  // (p, t0, t1, t2)
+        double w[3];
+        d0 = sqrt(pt_closest(X[0], X[1], X[2], X[3], w));
+        for (int j = 1; j < 4; ++j) {
+            d3 dd = Q[0] - Q[j];
+            l = fmax(l, sqrt(dot(dd, dd)));
+        }
+        cubic_of(X[2] - X[1], Q[2] - Q[1], X[3] - X[1], Q[3] - Q[1], X[0] - X[1], Q[0] - Q[1], c);
+    } else {  // (a0, a1, b0, b1)
+        double s, t;
+        d0 = sqrt(ee_closest(X[0], X[1], X[2], X[3], s, t));
+        for (int i = 0; i < 2; ++i)
+            for (int j = 2; j < 4; ++j) {
+                d3 dd = Q[i] - Q[j];
+                l = fmax(l, sqrt(dot(dd, dd)));
+            }
+        cubic_of(X[2] - X[0], Q[2] - Q[0], X[1] - X[0], Q[1] - Q[0], X[3] - X[0], Q[3] - Q[0], c);
+    }
+    double al = l > 0.0 ? (1.0 - D.ccd_shrink) * d0 / l : __longlong_as_double(0x7ff0000000000000ULL);
+    return cubic_safe(c, al);
+}
+
+template <class R>
+__device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
+    double a = pair_alpha(D, kind, v, D.x, D.p, nullptr);
+    int g0 = D.grp0[v[0]], g1 = D.grp0[v[1]], g2 = D.grp0[v[2]], g3 = D.grp0[v[3]];
+    if (a < 1.0) {
+        atomicMinPos(&D.alpha[g0], a);
+        if (g1 != g0) atomicMinPos(&D.alpha[g1], a);
+        if (g2 != g0 && g2 != g1) atomicMinPos(&D.alpha[g2], a);
+        if (g3 != g0 && g3 != g1 && g3 != g2) atomicMinPos(&D.alpha[g3], a);
+    }
+    if (!(g1 == g0 && g2 == g0 && g3 == g0)) {
+        int k = atomicAdd(&D.S->n_straddle, 1);
+        if (k < D.straddle_cap) {
+            D.str_v[k] = make_int4(v[0], v[1], v[2], v[3]);
+            D.str_t[k] = kind;
+        } else {
+            atomicOr(&D.S->overflow, 2);
+        }
+    }
+}
+
+template <class R>
+__global__ void k_ccd_pt(Dev<R> D, const int* gin) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= D.nsv) return;
+    int pv = D.sv[qi];
+    double lo[3], hi[3];
+    prim_box(D.x, D.p, &pv, 1, 0.0, lo, hi);
+    double inv = 1.0 / *D.cellsz;
+    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
+    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
+    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
+    if (!(nc > 0)) nc = kMaxCells + 1;
+    auto visit = [&](int f) {
+        int v[4] = {pv, D.sf[3 * f], D.sf[3 * f + 1], D.sf[3 * f + 2]};
+        if (pv == v[1] || pv == v[2] || pv == v[3]) return;
+        ccd_pair(D, 0, v);
+    };
+    if (nc > kMaxCells) {
+        for (int f = 0; f < D.nsf; ++f) {
+            const double* b = D.pbox + 6 * (size_t)f;
+            if (overlap(lo, hi, b, b + 3)) visit(f);
+        }
+        return;
+    }
+    for (int a = i0; a <= i1; ++a)
+        for (int bb = j0; bb <= j1; ++bb)
+            for (int c = k0; c <= k1; ++c) {
+                unsigned long long cc = pack_cell(a, bb, c);
+                int bk = bucket_of(cc, D.nbuckets);
+                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                    if (D.gcell[e] != cc) continue;
+                    int f = D.gentry[e];
+                    const double* b = D.pbox + 6 * (size_t)f;
+                    if (!overlap(lo, hi, b, b + 3)) continue;
+                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
+                        cellc(fmax(lo[2], b[2]), inv) != c)
+                        continue;
+                    visit(f);
+                }
+            }
+    int nl = *D.gnlarge;
+    for (int k = 0; k < nl; ++k) {
+        int f = D.glarge[k];
+        const double* b = D.pbox + 6 * (size_t)f;
+        if (overlap(lo, hi, b, b + 3)) visit(f);
+    }
+}
+
+template <class R>
+__global__ void k_ccd_ee(Dev<R> D, const int* gin) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.nse) return;
+    int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+    double lo[3], hi[3];
+    prim_box(D.x, D.p, vid, 2, 0.0, lo, hi);
+    double inv = 1.0 / *D.cellsz;
+    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
+    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
+    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
+    if (!(nc > 0)) nc = kMaxCells + 1;
+    auto visit = [&](int j) {
+        int v[4] = {vid[0], vid[1], D.se[2 * j], D.se[2 * j + 1]};
+        if (v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3]) return;
+        ccd_pair(D, 1, v);
+    };
+    if (nc > kMaxCells) {
+        for (int j = i + 1; j < D.nse; ++j) {
+            const double* b = D.pbox + 6 * (size_t)j;
+            if (overlap(lo, hi, b, b + 3)) visit(j);
+        }
+        return;
+    }
+    for (int a = i0; a <= i1; ++a)
+        for (int bb = j0; bb <= j1; ++bb)
+            for (int c = k0; c <= k1; ++c) {
+                unsigned long long cc = pack_cell(a, bb, c);
+                int bk = bucket_of(cc, D.nbuckets);
+                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                    if (D.gcell[e] != cc) continue;
+                    int j = D.gentry[e];
+                    if (j <= i) continue;
+                    const double* b = D.pbox + 6 * (size_t)j;
+                    if (!overlap(lo, hi, b, b + 3)) continue;
+                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
+                        cellc(fmax(lo[2], b[2]), inv) != c)
+                        continue;
+                    visit(j);
+                }
+            }
+    int nl = *D.gnlarge;
+    for (int k = 0; k < nl; ++k) {
+        int j = D.glarge[k];
+        if (j <= i) continue;
+        const double* b = D.pbox + 6 * (size_t)j;
+        if (overlap(lo, hi, b, b + 3)) visit(j);
+    }
+}
+
+template <class R>
+__global__ void k_ccd_pg(Dev<R> D) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= D.nsv || !D.has_ground) return;
+    int pv = D.sv[qi];
+    d3 n = mk(D.gn[0], D.gn[1], D.gn[2]);
+    d3 pp = mk((double)D.p[3 * pv], (double)D.p[3 * pv + 1], (double)D.p[3 * pv + 2]);
+    double vn = dot(n, pp);
+    if (!(vn < 0.0)) return;
+    double d0 = dot(n, ld3(D.x + 3 * pv)) - D.goff;
+    double a = fmin(1.0, (1.0 - D.ccd_shrink) * d0 / (-vn));
+    if (!(a > 0.0)) a = 0.0;
+    if (a < 1.0) atomicMinPos(&D.alpha[D.grp0[pv]], a);
+}
+
+template <class R>
+__global__ void k_fill(Dev<R> D, double* a, int n, double v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+template <class R>
+__global__ void k_ccd_begin(Dev<R> D) {
+    Scalars* S = D.S;
+    S->n_straddle = 0;
+    S->ccd_viol = 0;
+    S->ccd_uniform = 0;
+    S->ccd_passes = 0;
+}
+
+// one block: min / max of alpha over subdomains; which = 0 stores alpha_min
+// for the fallback, 1 stores the final min / max
+template <class R>
+__global__ void k_alpha_minmax(Dev<R> D, int which) {
+    __shared__ double smin[32], smax[32];
+    double mn = 1.0, mx = 0.0;
+    for (int g = threadIdx.x; g < D.ngroups[0]; g += blockDim.x) {
+        mn = fmin(mn, D.alpha[g]);
+        mx = fmax(mx, D.alpha[g]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smin[threadIdx.x >> 5] = mn;
+        smax[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mn = fmin(mn, smin[w]);
+            mx = fmax(mx, smax[w]);
+        }
+        if (which == 0) {
+            D.S->alpha_min = mn;  // pre-verification minimum for the uniform fallback
+        } else {
+            D.S->alpha_min = mn;
+            D.S->alpha_max = mx;
+        }
+    }
+}
+
+// verification pass: re-check straddling pairs with the actual motion
+template <class R>
+__global__ void k_verify(Dev<R> D) {
+    Scalars* S = D.S;
+    if (S->ccd_uniform == 2) return;  // finished
+    int n = min(S->n_straddle, D.straddle_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int4 q = D.str_v[k];
+        int v[4] = {q.x, q.y, q.z, q.w};
+        double rho = pair_alpha(D, D.str_t[k], v, D.x, D.p, D.alpha);
+        if (rho < 1.0) {
+            S->ccd_viol = 1;
+            for (int j = 0; j < 4; ++j) atomicMinPos(&D.shrink[D.grp0[v[j]]], rho);
+        }
+    }
+}
+
+template <class R>
+__global__ void k_verify_apply(Dev<R> D) {
+    Scalars* S = D.S;
+    if (S->ccd_uniform == 2 || !S->ccd_viol) return;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < D.ngroups[0]; g += gridDim.x * blockDim.x) {
+        D.alpha[g] *= D.shrink[g];
+        D.shrink[g] = 1.0;
+    }
+}
+
+// after pass `pass`: stop if clean; after the last pass with a violation
+// mark the uniform fallback
+template <class R>
+__global__ void k_verify_flag(Dev<R> D, int pass, int last) {
+    Scalars* S = D.S;
+    if (S->ccd_uniform == 2) return;
+    if (!S->ccd_viol) {
+        S->ccd_uniform = 2;  // verified
+        S->ccd_passes = pass + 1;
+        return;
+    }
+    S->ccd_viol = 0;
+    if (last) {
+        S->ccd_uniform = 1;
+        S->ccd_passes = -1;
+    }
+}
+
+template <class R>
+__global__ void k_uniform(Dev<R> D, double amin_dummy) {
+    Scalars* S = D.S;
+    if (S->ccd_uniform != 1) return;
+    double a = S->alpha_min;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < D.ngroups[0]; g += gridDim.x * blockDim.x) D.alpha[g] = a;
+}
+
+}  // namespace
+
+template <class R>
+void launch_detect(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
+    KL(k_reset_detect<R><<<1, 1, 0, st>>>(D, C));
+    int* gin = D.gin;
+    build_grid<R>(D, D.sf, 3, D.nsf, x, nullptr, D.dhat, gin, false, st);
+    if (D.nsv) KL(k_prox_pt<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
+    build_grid<R>(D, D.se, 2, D.nse, x, nullptr, D.dhat, gin, false, st);
+    if (D.nse) KL(k_prox_ee<R><<<nblk(D.nse), kT, 0, st>>>(D, x, C, gin));
+    if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
+}
+
+template <class R>
+void launch_ccd(const Dev<R>& D, cudaStream_t st) {
+    int ng = D.ngroups[0];
+    KL(k_ccd_begin<R><<<1, 1, 0, st>>>(D));
+    KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
+    KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.shrink, ng, 1.0));
+    int* gin = D.gin;
+    build_grid<R>(D, D.sf, 3, D.nsf, D.x, D.p, 0.0, gin, true, st);
+    if (D.nsv) KL(k_ccd_pt<R><<<nblk(D.nsv), kT, 0, st>>>(D, gin));
+    build_grid<R>(D, D.se, 2, D.nse, D.x, D.p, 0.0, gin, true, st);
+    if (D.nse) KL(k_ccd_ee<R><<<nblk(D.nse), kT, 0, st>>>(D, gin));
+    if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
+    KL(k_alpha_minmax<R><<<1, 1024, 0, st>>>(D, 0));
+    for (int pass = 0; pass < 4; ++pass) {
+        KL(k_verify<R><<<592, kT, 0, st>>>(D));
+        KL(k_verify_apply<R><<<nblk(ng), kT, 0, st>>>(D));
+        KL(k_verify_flag<R><<<1, 1, 0, st>>>(D, pass, pass == 3 ? 1 : 0));
+    }
+    KL(k_uniform<R><<<nblk(ng), kT, 0, st>>>(D, 0.0));
+    KL(k_alpha_minmax<R><<<1, 1024, 0, st>>>(D, 1));
+}
+
+#define INST(R)                                                                               \
+    template void launch_detect<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t); \
+    template void launch_ccd<R>(const Dev<R>&, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace ipcb

@@ -1,0 +1,283 @@
+// Incremental potential (Eq. 1) and its gradient: inertia, stable neo-Hookean
+// elasticity and the IPC barrier; the predictor; trial positions; prefix scan.
+//
+// Elastic energy density (reading of the SNH the paper cites):
+//   Psi(F) = mu/2 (|F|^2 - 3) - mu (J - 1) + lambda/2 (J - 1)^2,
+//   P = mu F + (lambda (J - 1) - mu) cof(F),  F = Ds B,  grad_{x_j} = V P B^T e_j.
+// Energies are accumulated in FP64; gradients in R.
+#include "kernels.h"
+
+namespace ipcb {
+
+namespace {
+
+constexpr int kT = 256;
+
+inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
+
+template <class R>
+__global__ void k_predict(Dev<R> D) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * D.nv) return;
+    int r = i % 3;
+    double x = D.x[i];
+    D.xs[i] = x;
+    D.xt[i] = x + D.h * D.v[i] + D.h * D.h * D.gravity[r];
+}
+
+template <class R>
+__global__ void k_trial(Dev<R> D, double beta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * D.nv) return;
+    double a = beta > 0.0 ? beta : D.alpha[D.grp0[i / 3]];
+    D.xtry[i] = D.x[i] + a * (double)D.p[i];
+}
+
+// g = M (x - x~), E += 1/2 (x - x~)^T M (x - x~)
+template <class R>
+__global__ void k_inertia(Dev<R> D, const double* __restrict__ x, R* __restrict__ g, double* E) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (v < D.nv) {
+        double m = D.massd[v];
+        double d0 = x[3 * v] - D.xt[3 * v];
+        double d1 = x[3 * v + 1] - D.xt[3 * v + 1];
+        double d2 = x[3 * v + 2] - D.xt[3 * v + 2];
+        e = 0.5 * m * (d0 * d0 + d1 * d1 + d2 * d2);
+        if (g) {
+            g[3 * v] = (R)(m * d0);
+            g[3 * v + 1] = (R)(m * d1);
+            g[3 * v + 2] = (R)(m * d2);
+        }
+    }
+    warp_add_to(E, e);
+}
+
+template <class R>
+__device__ __forceinline__ void load_B(const Dev<R>& D, int t, double B[3][3]) {
+    const R* base = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = (double)base[c * kPack];
+}
+
+template <class R>
+__global__ void k_elastic(Dev<R> D, const double* __restrict__ x, R* __restrict__ g, double* E) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (t < D.nt) {
+        int4 q = D.tets[t];
+        int vid[4] = {q.x, q.y, q.z, q.w};
+        double X[4][3];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) X[j][r] = x[3 * vid[j] + r];
+        double B[3][3];
+        load_B(D, t, B);
+        double F[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double s = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) s += (X[j + 1][r] - X[0][r]) * B[j][c];
+                F[r][c] = s;
+            }
+        // columns f0, f1, f2 and cofactor columns
+        double C[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            int a = (c + 1) % 3, b = (c + 2) % 3;
+            C[0][c] = F[1][a] * F[2][b] - F[2][a] * F[1][b];
+            C[1][c] = F[2][a] * F[0][b] - F[0][a] * F[2][b];
+            C[2][c] = F[0][a] * F[1][b] - F[1][a] * F[0][b];
+        }
+        double J = F[0][0] * C[0][0] + F[1][0] * C[1][0] + F[2][0] * C[2][0];
+        double Ic = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Ic += F[r][c] * F[r][c];
+        double mu = D.tet_mu[t], lam = D.tet_lam[t], V = D.tet_vol[t];
+        double h2V = D.h * D.h * V;
+        e = h2V * (0.5 * mu * (Ic - 3.0) - mu * (J - 1.0) + 0.5 * lam * (J - 1.0) * (J - 1.0));
+        if (g) {
+            R s = (R)(lam * (J - 1.0) - mu);
+            R Pm[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Pm[r][c] = (R)mu * (R)F[r][c] + s * (R)C[r][c];
+            R G[3][3];  // h^2 V P B^T: column j -> gradient of vertex j+1
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    R acc = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc += Pm[r][c] * (R)B[j][c];
+                    G[r][j] = (R)h2V * acc;
+                }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                atomicAdd(&g[3 * vid[0] + r], -(G[r][0] + G[r][1] + G[r][2]));
+#pragma unroll
+                for (int j = 0; j < 3; ++j) atomicAdd(&g[3 * vid[j + 1] + r], G[r][j]);
+            }
+        }
+    }
+    warp_add_to(E, e);
+}
+
+template <class R>
+__global__ void k_barrier(Dev<R> D, ContactBuf C, R* __restrict__ g, double* E) {
+    int n = min(*C.count, D.cap);
+    double e = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double b, b1, b2;
+        barrier3(C.d[i], D.dhat, b, b1, b2);
+        e += D.kappa * b;
+        if (g) {
+            int4 q = C.v[i];
+            int vid[4] = {q.x, q.y, q.z, q.w};
+            double bp = C.bp[i];
+            double r0 = C.r[3 * i], r1 = C.r[3 * i + 1], r2 = C.r[3 * i + 2];
+            int nvv = C.type[i] == 2 ? 1 : 4;
+            for (int j = 0; j < nvv; ++j) {
+                double s = bp * C.w[4 * i + j];
+                atomicAdd(&g[3 * vid[j]], (R)(s * r0));
+                atomicAdd(&g[3 * vid[j] + 1], (R)(s * r1));
+                atomicAdd(&g[3 * vid[j] + 2], (R)(s * r2));
+            }
+        }
+    }
+    warp_add_to(E, e);
+}
+
+template <class R>
+__global__ void k_accept(Dev<R> D) {
+    Scalars* S = D.S;
+    double Et = S->E_try;
+    S->accepted = (Et <= S->E_k) ? 1 : 0;
+    if (S->accepted) S->E_k = Et;
+}
+
+template <class R>
+__global__ void k_zero_scalars(Dev<R> D) {
+    Scalars* S = D.S;
+    S->gz = S->gp = S->gzprev = 0.0;
+    S->zHz = S->zHp = S->pHp = 0.0;
+    S->znorm = 0.0;
+    S->pmax = 0.0;
+}
+
+// ---- scan: block sums, scan of sums, block scan + offset
+__global__ void k_scan_sums(const int* in, int n, int* sums) {
+    __shared__ int sh[32];
+    int i = blockIdx.x * 1024 + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = sh[threadIdx.x];
+        w = warp_sum(w);
+        if (threadIdx.x == 0) sums[blockIdx.x] = w;
+    }
+}
+
+__global__ void k_scan_top(int* sums, int nb) {
+    // single block, sequential over chunks of 1024
+    __shared__ int sh[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < nb ? sums[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) sums[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_scan_apply(const int* in, int* out, int n, const int* sums) {
+    __shared__ int sh[1024];
+    int i = blockIdx.x * 1024 + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < n) out[i] = sums[blockIdx.x] + sh[threadIdx.x] - v;
+    if (i == n - 1) out[n] = sums[blockIdx.x] + sh[threadIdx.x];
+}
+
+}  // namespace
+
+void scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st) {
+    if (n <= 0) {
+        cudaMemsetAsync(out, 0, sizeof(int), st);
+        return;
+    }
+    int nb = (n + 1023) / 1024;
+    KL(k_scan_sums<<<nb, 1024, 0, st>>>(in, n, tmp));
+    KL(k_scan_top<<<1, 1024, 0, st>>>(tmp, nb));
+    KL(k_scan_apply<<<nb, 1024, 0, st>>>(in, out, n, tmp));
+}
+
+template <class R>
+void launch_predict(const Dev<R>& D, cudaStream_t st) {
+    KL(k_predict<R><<<nblk(3LL * D.nv), kT, 0, st>>>(D));
+}
+
+template <class R>
+void launch_trial_positions(const Dev<R>& D, double beta, cudaStream_t st) {
+    KL(k_trial<R><<<nblk(3LL * D.nv), kT, 0, st>>>(D, beta));
+}
+
+template <class R>
+void launch_energy_grad(const Dev<R>& D, const double* x, const ContactBuf& C, R* g, double* E, cudaStream_t st) {
+    cudaMemsetAsync(E, 0, sizeof(double), st);
+    KL(k_inertia<R><<<nblk(D.nv), kT, 0, st>>>(D, x, g, E));
+    KL(k_elastic<R><<<nblk(D.nt), kT, 0, st>>>(D, x, g, E));
+    KL(k_barrier<R><<<1184, kT, 0, st>>>(D, C, g, E));
+}
+
+template <class R>
+void launch_accept(const Dev<R>& D, cudaStream_t st) {
+    KL(k_accept<R><<<1, 1, 0, st>>>(D));
+}
+
+template <class R>
+void launch_zero_scalars(const Dev<R>& D, cudaStream_t st) {
+    KL(k_zero_scalars<R><<<1, 1, 0, st>>>(D));
+}
+
+#define INST(R)                                                                                              \
+    template void launch_predict<R>(const Dev<R>&, cudaStream_t);                                            \
+    template void launch_trial_positions<R>(const Dev<R>&, double, cudaStream_t);                            \
+    template void launch_energy_grad<R>(const Dev<R>&, const double*, const ContactBuf&, R*, double*,        \
+                                        cudaStream_t);                                                       \
+    template void launch_accept<R>(const Dev<R>&, cudaStream_t);                                             \
+    template void launch_zero_scalars<R>(const Dev<R>&, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace ipcb

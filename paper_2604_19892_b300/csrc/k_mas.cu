@@ -1,0 +1,702 @@
+// MAS preconditioner (Sec. 3.3; supplement Eq. 1-4), its restart rebuild, and
+// the Sparse-Input Woodbury update of the level-0 inverses (Sec. 4.1, Eq. 7-8).
+//
+// RebuildMAS at x:
+//  1. per tet: dP/dF (9x9) of the SNH density, PSD-projected by cyclic Jacobi
+//     (negative eigenvalues clamped), times h^2 V, stored packed (45 values);
+//  2. level blocks of H_base = M + h^2 sum_t K_t + sum_{c in C} k n n^T:
+//     level 0 takes the 3x3 couplings between vertices of one subdomain;
+//     level l >= 1 takes C_l H C_l^T restricted to one level-l subdomain.
+//     Elastic and PT/EE contact terms annihilate rigid translations, so a
+//     term whose vertices all fall in one level-l node adds nothing to that
+//     level and is skipped; mass and point-ground terms always add;
+//  3. every 96x96 block is inverted by Gauss-Jordan elimination in shared
+//     memory (the blocks are SPD), padded slots carry an identity;
+//  4. the contact set is snapshot as C_base with a key table.
+// Woodbury (non-restart iterations): each current contact is classified
+// against C_base (new / rotated: dS = k, u = sqrt(k) n; stiffer: dS = k - k_b,
+// u = sqrt(dS) n; softer: skipped); every subdomain keeps the K updates of
+// largest dS (ties by ascending key) touching it; the block apply reads B_d
+// once for [g_d, U_d], solves the K x K capacitance system in FP64 and
+// corrects z_d = B g_d - W lambda (Eq. 7).  Coarse levels stay frozen (Eq. 8).
+#include "kernels.h"
+
+namespace ipcb {
+
+namespace {
+
+constexpr int kT = 128;
+inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
+
+__host__ __device__ __forceinline__ int pk(int i, int j) {  // packed upper index, i <= j
+    return i * 9 - (i * (i - 1)) / 2 + (j - i);
+}
+
+template <class R>
+__device__ __forceinline__ void load_B(const Dev<R>& D, int t, R B[3][3]) {
+    const R* base = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = base[c * kPack];
+}
+
+// ------------------------------------------------------ per-tet projected Hessian
+
+template <class R>
+__global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __restrict__ x) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= D.nt) return;
+    int4 q = D.tets[t];
+    int vid[4] = {q.x, q.y, q.z, q.w};
+    R B[3][3];
+    load_B(D, t, B);
+    R F[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (int j = 0; j < 3; ++j) s += (x[3 * vid[j + 1] + r] - x[3 * vid[0] + r]) * (double)B[j][c];
+            F[r][c] = (R)s;
+        }
+    R f[3][3];  // columns
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) f[c][r] = F[r][c];
+    R g[9];  // vec(cof F), column-major
+    for (int c = 0; c < 3; ++c) {
+        const R* a = f[(c + 1) % 3];
+        const R* b = f[(c + 2) % 3];
+        g[3 * c + 0] = a[1] * b[2] - a[2] * b[1];
+        g[3 * c + 1] = a[2] * b[0] - a[0] * b[2];
+        g[3 * c + 2] = a[0] * b[1] - a[1] * b[0];
+    }
+    R J = f[0][0] * g[0] + f[0][1] * g[1] + f[0][2] * g[2];
+    R mu = (R)D.tet_mu[t], lam = (R)D.tet_lam[t];
+    R s = lam * (J - (R)1) - mu;
+    R A[9][9];
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) A[i][j] = lam * g[i] * g[j] + (i == j ? mu : (R)0);
+    // s * d cof / dF: block (c, c') = s * d(cof_c)/d(f_c'), hat(a) b = a x b
+    auto add_hat = [&](int rb, int cb, const R* a, R sc) {
+        A[3 * rb + 0][3 * cb + 1] += -sc * a[2];
+        A[3 * rb + 0][3 * cb + 2] += sc * a[1];
+        A[3 * rb + 1][3 * cb + 0] += sc * a[2];
+        A[3 * rb + 1][3 * cb + 2] += -sc * a[0];
+        A[3 * rb + 2][3 * cb + 0] += -sc * a[1];
+        A[3 * rb + 2][3 * cb + 1] += sc * a[0];
+    };
+    add_hat(0, 1, f[2], -s);
+    add_hat(0, 2, f[1], s);
+    add_hat(1, 0, f[2], s);
+    add_hat(1, 2, f[0], -s);
+    add_hat(2, 0, f[1], -s);
+    add_hat(2, 1, f[0], s);
+    // cyclic Jacobi
+    R Q[9][9];
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) Q[i][j] = (i == j) ? (R)1 : (R)0;
+    R fro = 0;
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) fro += A[i][j] * A[i][j];
+    const R tol = (sizeof(R) == 8 ? (R)1e-30 : (R)1e-14) * fro;
+#pragma unroll 1
+    for (int sweep = 0; sweep < 20; ++sweep) {
+        R off = 0;
+        for (int i = 0; i < 9; ++i)
+            for (int j = i + 1; j < 9; ++j) off += A[i][j] * A[i][j];
+        if (off <= tol) break;
+#pragma unroll 1
+        for (int pp = 0; pp < 8; ++pp) {
+#pragma unroll 1
+            for (int qq = pp + 1; qq < 9; ++qq) {
+                R apq = A[pp][qq];
+                if (apq == (R)0) continue;
+                R th = (A[qq][qq] - A[pp][pp]) / (2 * apq);
+                R tt = (th >= 0 ? (R)1 : (R)-1) / (fabs(th) + sqrt(th * th + (R)1));
+                R c = (R)1 / sqrt(tt * tt + (R)1), sn = tt * c;
+                for (int k = 0; k < 9; ++k) {
+                    R akp = A[k][pp], akq = A[k][qq];
+                    A[k][pp] = c * akp - sn * akq;
+                    A[k][qq] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 9; ++k) {
+                    R apk = A[pp][k], aqk = A[qq][k];
+                    A[pp][k] = c * apk - sn * aqk;
+                    A[qq][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 9; ++k) {
+                    R qkp = Q[k][pp], qkq = Q[k][qq];
+                    Q[k][pp] = c * qkp - sn * qkq;
+                    Q[k][qq] = sn * qkp + c * qkq;
+                }
+            }
+        }
+    }
+    R lamv[9];
+    for (int i = 0; i < 9; ++i) lamv[i] = A[i][i] > (R)0 ? A[i][i] : (R)0;
+    R sc = (R)(D.h * D.h * D.tet_vol[t]);
+    R* out = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
+    for (int i = 0; i < 9; ++i)
+        for (int j = i; j < 9; ++j) {
+            R acc = 0;
+            for (int k = 0; k < 9; ++k) acc += Q[i][k] * lamv[k] * Q[j][k];
+            out[pk(i, j) * kPack] = sc * acc;
+        }
+}
+
+// ------------------------------------------------------ block assembly
+
+template <class R>
+__device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb, const double blk[3][3]) {
+    int na, nb, ga, gb, sa, sb;
+    if (l == 0) {
+        ga = D.grp0[va];
+        gb = D.grp0[vb];
+        if (ga != gb) return;
+        sa = D.slot0[va];
+        sb = D.slot0[vb];
+    } else {
+        na = D.node_of_vert[l][va];
+        nb = D.node_of_vert[l][vb];
+        ga = D.grp_of_node[l][na];
+        gb = D.grp_of_node[l][nb];
+        if (ga != gb) return;
+        sa = D.slot_of_node[l][na];
+        sb = D.slot_of_node[l][nb];
+    }
+    double* A = D.asmb + ((size_t)(D.blk_off[l] + ga)) * (kBlk * kBlk);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double v = blk[r][c];
+            if (v != 0.0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
+        }
+}
+
+// is every vertex of the term inside one level-l node? (translation-invariant
+// terms then add nothing at that level)
+template <class R>
+__device__ __forceinline__ bool one_node(const Dev<R>& D, int l, const int* v, int n) {
+    if (l == 0) return false;
+    int a = D.node_of_vert[l][v[0]];
+    for (int j = 1; j < n; ++j)
+        if (D.node_of_vert[l][v[j]] != a) return false;
+    return true;
+}
+
+template <class R>
+__global__ void k_assemble_tets(Dev<R> D) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= D.nt) return;
+    int4 q = D.tets[t];
+    int vid[4] = {q.x, q.y, q.z, q.w};
+    R Bm[3][3];
+    load_B(D, t, Bm);
+    double Bf[4][3];
+    for (int c = 0; c < 3; ++c) {
+        Bf[0][c] = -((double)Bm[0][c] + (double)Bm[1][c] + (double)Bm[2][c]);
+        for (int j = 0; j < 3; ++j) Bf[j + 1][c] = (double)Bm[j][c];
+    }
+    const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
+    double H[9][9];
+    for (int i = 0; i < 9; ++i)
+        for (int j = i; j < 9; ++j) {
+            double v = (double)hp[pk(i, j) * kPack];
+            H[i][j] = v;
+            H[j][i] = v;
+        }
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+            double blk[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 3; ++s) {
+                    double acc = 0.0;
+                    for (int c = 0; c < 3; ++c)
+                        for (int c2 = 0; c2 < 3; ++c2) acc += Bf[a][c] * Bf[b][c2] * H[3 * c + r][3 * c2 + s];
+                    blk[r][s] = acc;
+                }
+            for (int l = 0; l < D.nlev; ++l) {
+                if (one_node(D, l, vid, 4)) continue;
+                add_block(D, l, vid[a], vid[b], blk);
+            }
+        }
+}
+
+template <class R>
+__global__ void k_assemble_mass(Dev<R> D) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= D.nv) return;
+    double m = D.massd[v];
+    double blk[3][3] = {{m, 0, 0}, {0, m, 0}, {0, 0, m}};
+    for (int l = 0; l < D.nlev; ++l) add_block(D, l, v, v, blk);
+}
+
+template <class R>
+__global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
+    int n = min(*C.count, D.cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int4 q = C.v[i];
+        int vid[4] = {q.x, q.y, q.z, q.w};
+        int nvv = C.type[i] == 2 ? 1 : 4;
+        double k = C.k[i];
+        double r[3] = {C.r[3 * i], C.r[3 * i + 1], C.r[3 * i + 2]};
+        double w[4] = {C.w[4 * i], C.w[4 * i + 1], C.w[4 * i + 2], C.w[4 * i + 3]};
+        for (int a = 0; a < nvv; ++a)
+            for (int b = 0; b < nvv; ++b) {
+                double blk[3][3];
+                for (int rr = 0; rr < 3; ++rr)
+                    for (int s = 0; s < 3; ++s) blk[rr][s] = k * w[a] * w[b] * r[rr] * r[s];
+                for (int l = 0; l < D.nlev; ++l) {
+                    if (nvv == 4 && one_node(D, l, vid, 4)) continue;
+                    add_block(D, l, vid[a], vid[b], blk);
+                }
+            }
+    }
+}
+
+// ------------------------------------------------------ batched inversion
+
+// One CTA per 96x96 block; Gauss-Jordan in shared memory in precision T.
+template <class R, class T>
+__global__ void __launch_bounds__(256) k_invert(Dev<R> D) {
+    extern __shared__ unsigned char smem_raw[];
+    T* A = reinterpret_cast<T*>(smem_raw);
+    T* rowk = A + kBlk * kBlk;
+    T* colk = rowk + kBlk;
+    int b = blockIdx.x;
+    int l = 0;
+    while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
+    int grp = b - D.blk_off[l];
+    const int* mem = D.members[l] + (size_t)grp * kSub;
+    const double* src = D.asmb + (size_t)b * kBlk * kBlk;
+    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
+        int r = i / kBlk, c = i % kBlk;
+        T v = (T)src[i];
+        if (mem[r / 3] < 0 || mem[c / 3] < 0) v = (r == c) ? (T)1 : (T)0;
+        A[i] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < kBlk; ++k) {
+        T piv = A[k * kBlk + k];
+        T ip = (T)1 / piv;
+        for (int j = threadIdx.x; j < kBlk; j += blockDim.x) {
+            rowk[j] = (j == k) ? ip : A[k * kBlk + j] * ip;
+            colk[j] = (j == k) ? (T)0 : A[j * kBlk + k];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
+            int r = i / kBlk, c = i % kBlk;
+            if (r == k) {
+                A[i] = rowk[c];
+            } else {
+                T a = (c == k) ? (T)0 : A[i];
+                A[i] = a - colk[r] * rowk[c];
+            }
+        }
+        __syncthreads();
+    }
+    R* dst = D.blocks + (size_t)b * kBlk * kBlk;
+    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) dst[i] = (R)A[i];
+}
+
+// ------------------------------------------------------ C_base snapshot
+
+template <class R>
+__global__ void k_snapshot(Dev<R> D) {
+    int n = min(*D.C.count, D.cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *D.Cb.count = n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        D.Cb.type[i] = D.C.type[i];
+        D.Cb.v[i] = D.C.v[i];
+        unsigned long long key = D.C.key[i];
+        D.Cb.key[i] = key;
+        D.Cb.d[i] = D.C.d[i];
+        D.Cb.k[i] = D.C.k[i];
+        D.Cb.bp[i] = D.C.bp[i];
+        for (int r = 0; r < 3; ++r) D.Cb.r[3 * i + r] = D.C.r[3 * i + r];
+        for (int r = 0; r < 4; ++r) D.Cb.w[4 * i + r] = D.C.w[4 * i + r];
+        unsigned h = (unsigned)(mix64(key) & (unsigned long long)(D.btab - 1));
+        for (int probe = 0; probe < D.btab; ++probe) {
+            unsigned long long old = atomicCAS(&D.bkeys[h], ~0ULL, key);
+            if (old == ~0ULL || old == key) {
+                D.bidx[h] = i;
+                break;
+            }
+            h = (h + 1) & (D.btab - 1);
+        }
+    }
+}
+
+// ------------------------------------------------------ classification
+
+template <class R>
+__device__ __forceinline__ int base_lookup(const Dev<R>& D, unsigned long long key) {
+    unsigned h = (unsigned)(mix64(key) & (unsigned long long)(D.btab - 1));
+    for (int probe = 0; probe < D.btab; ++probe) {
+        unsigned long long k = D.bkeys[h];
+        if (k == key) return D.bidx[h];
+        if (k == ~0ULL) return -1;
+        h = (h + 1) & (D.btab - 1);
+    }
+    return -1;
+}
+
+template <class R>
+__global__ void k_classify(Dev<R> D, ContactBuf C) {
+    int n = min(*C.count, D.cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double k = C.k[i];
+        int b = base_lookup(D, C.key[i]);
+        double dS;
+        if (b < 0) {
+            dS = k;
+        } else {
+            double ww = 0, wb = 0, bb = 0;
+            for (int j = 0; j < 4; ++j) {
+                ww += C.w[4 * i + j] * C.w[4 * i + j];
+                wb += C.w[4 * i + j] * D.Cb.w[4 * b + j];
+                bb += D.Cb.w[4 * b + j] * D.Cb.w[4 * b + j];
+            }
+            double rr = C.r[3 * i] * D.Cb.r[3 * b] + C.r[3 * i + 1] * D.Cb.r[3 * b + 1] + C.r[3 * i + 2] * D.Cb.r[3 * b + 2];
+            double cosang = wb * rr / sqrt(ww * bb);
+            double kb = D.Cb.k[b];
+            if (cosang < D.cos_rot)
+                dS = k;
+            else if (k > kb)
+                dS = k - kb;
+            else
+                dS = 0.0;
+        }
+        if (!(dS > 0.0)) continue;
+        int u = atomicAdd(&D.S->n_upd, 1);
+        if (u >= D.upd_cap) {
+            atomicOr(&D.S->overflow, 4);
+            continue;
+        }
+        D.upd_c[u] = i;
+        D.upd_dS[u] = dS;
+        int4 q = C.v[i];
+        int vid[4] = {q.x, q.y, q.z, q.w};
+        int nvv = C.type[i] == 2 ? 1 : 4;
+        int gs[4];
+        for (int j = 0; j < nvv; ++j) {
+            int g = D.grp0[vid[j]];
+            bool dup = false;
+            for (int m = 0; m < j; ++m) dup |= gs[m] == g;
+            gs[j] = dup ? -1 : g;
+            if (!dup) atomicAdd(&D.upd_cnt[g], 1);
+        }
+    }
+}
+
+template <class R>
+__global__ void k_fill_lists(Dev<R> D, ContactBuf C) {
+    int n = min(D.S->n_upd, D.upd_cap);
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        int i = D.upd_c[u];
+        int4 q = C.v[i];
+        int vid[4] = {q.x, q.y, q.z, q.w};
+        int nvv = C.type[i] == 2 ? 1 : 4;
+        int gs[4];
+        for (int j = 0; j < nvv; ++j) {
+            int g = D.grp0[vid[j]];
+            bool dup = false;
+            for (int m = 0; m < j; ++m) dup |= gs[m] == g;
+            gs[j] = dup ? -1 : g;
+            if (!dup) D.upd_list[D.upd_off[g] + atomicAdd(&D.upd_cur[g], 1)] = u;
+        }
+    }
+}
+
+// one warp per subdomain: K rounds of "best entry ranked below the last pick"
+template <class R>
+__global__ void k_topk(Dev<R> D, ContactBuf C) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= D.ngroups[0]) return;
+    int beg = D.upd_off[warp], end = D.upd_off[warp + 1];
+    double lastS = __longlong_as_double(0x7ff0000000000000ULL);
+    unsigned long long lastK = 0;
+    bool have_last = false;
+    for (int r = 0; r < D.K; ++r) {
+        double bestS = -1.0;
+        unsigned long long bestK = ~0ULL;
+        int bestU = -1;
+        for (int e = beg + lane; e < end; e += 32) {
+            int u = D.upd_list[e];
+            double s = D.upd_dS[u];
+            unsigned long long k = C.key[D.upd_c[u]];
+            // strictly below the last pick in (dS desc, key asc) order
+            if (have_last && !(s < lastS || (s == lastS && k > lastK))) continue;
+            if (s > bestS || (s == bestS && k < bestK)) {
+                bestS = s;
+                bestK = k;
+                bestU = u;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double s2 = __shfl_xor_sync(0xffffffffu, bestS, o);
+            unsigned long long k2 = __shfl_xor_sync(0xffffffffu, bestK, o);
+            int u2 = __shfl_xor_sync(0xffffffffu, bestU, o);
+            if (s2 > bestS || (s2 == bestS && k2 < bestK)) {
+                bestS = s2;
+                bestK = k2;
+                bestU = u2;
+            }
+        }
+        if (lane == 0) D.topk[(size_t)warp * D.K + r] = bestU;
+        if (bestU < 0) {
+            for (int r2 = r + 1 + lane; r2 < D.K; r2 += 32) D.topk[(size_t)warp * D.K + r2] = -1;
+            break;
+        }
+        lastS = bestS;
+        lastK = bestK;
+        have_last = true;
+    }
+}
+
+// ------------------------------------------------------ preconditioner apply
+
+template <class R>
+__global__ void k_restrict(Dev<R> D, const R* __restrict__ g) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= D.nv) return;
+    R gx = g[3 * v], gy = g[3 * v + 1], gz = g[3 * v + 2];
+    for (int l = 1; l < D.nlev; ++l) {
+        R* r = D.coarse_r + D.coarse_off[l] + 3 * D.node_of_vert[l][v];
+        atomicAdd(r, gx);
+        atomicAdd(r + 1, gy);
+        atomicAdd(r + 2, gz);
+    }
+}
+
+// One CTA of 96 threads per block of any level.  Level 0 applies B_d to
+// [g_d, U_d] and the Woodbury correction; coarse levels apply M_l^-1 to the
+// restricted residual.
+template <class R>
+__global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z,
+                                                    ContactBuf C, int woodbury) {
+    __shared__ R rhs[1 + kMaxK][kBlk];
+    __shared__ R Y[1 + kMaxK][kBlk];
+    __shared__ double cap[kMaxK][kMaxK + 1];
+    __shared__ double lam[kMaxK];
+    __shared__ int sel[kMaxK];
+    __shared__ int nsel;
+    int b = blockIdx.x;
+    int l = 0;
+    while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
+    int grp = b - D.blk_off[l];
+    int tid = threadIdx.x;
+    const int* mem = D.members[l] + (size_t)grp * kSub;
+    int node = mem[tid / 3];
+    int comp = tid % 3;
+    if (l == 0)
+        rhs[0][tid] = node >= 0 ? g[3 * node + comp] : (R)0;
+    else
+        rhs[0][tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : (R)0;
+    if (tid == 0) {
+        int n = 0;
+        if (l == 0 && woodbury)
+            for (int a = 0; a < D.K; ++a) {
+                int u = D.topk[(size_t)grp * D.K + a];
+                if (u < 0) break;
+                sel[n++] = u;
+            }
+        nsel = n;
+    }
+    __syncthreads();
+    int ns = nsel;
+    for (int a = 0; a < ns; ++a) rhs[1 + a][tid] = (R)0;
+    __syncthreads();
+    if (tid < ns) {  // build column tid of U_d: u = sqrt(dS) w_j r at slot of vertex j
+        int u = sel[tid];
+        int i = D.upd_c[u];
+        double sc = sqrt(D.upd_dS[u]);
+        int4 q = C.v[i];
+        int vid[4] = {q.x, q.y, q.z, q.w};
+        int nvv = C.type[i] == 2 ? 1 : 4;
+        for (int j = 0; j < nvv; ++j) {
+            if (D.grp0[vid[j]] != grp) continue;
+            int s = D.slot0[vid[j]];
+            double wj = sc * C.w[4 * i + j];
+            for (int r = 0; r < 3; ++r) rhs[1 + tid][3 * s + r] += (R)(wj * C.r[3 * i + r]);
+        }
+    }
+    __syncthreads();
+    // Y = B [rhs]: B symmetric, thread tid computes row tid reading row j of B
+    const R* Bp = D.blocks + (size_t)b * kBlk * kBlk;
+    R acc[1 + kMaxK];
+#pragma unroll
+    for (int a = 0; a < 1 + kMaxK; ++a) acc[a] = 0;
+    if (ns == 0) {
+#pragma unroll 8
+        for (int j = 0; j < kBlk; ++j) acc[0] += Bp[j * kBlk + tid] * rhs[0][j];
+    } else {
+#pragma unroll 4
+        for (int j = 0; j < kBlk; ++j) {
+            R bj = Bp[j * kBlk + tid];
+#pragma unroll
+            for (int a = 0; a < 1 + kMaxK; ++a)
+                if (a <= ns) acc[a] += bj * rhs[a][j];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 1 + kMaxK; ++a)
+        if (a <= ns) Y[a][tid] = acc[a];
+    __syncthreads();
+    R out = Y[0][tid];
+    if (ns > 0) {
+        // capacitance I + U^T W and r = U^T z_base, FP64 dot products per warp
+        int warp = tid >> 5, lane = tid & 31;
+        int nprod = ns * ns + ns;
+        for (int e = warp; e < nprod; e += 3) {
+            int a, c;
+            const R* wv;
+            if (e < ns * ns) {
+                a = e / ns;
+                c = e % ns;
+                wv = Y[1 + c];
+            } else {
+                a = e - ns * ns;
+                c = -1;
+                wv = Y[0];
+            }
+            double s = 0.0;
+            for (int i = lane; i < kBlk; i += 32) s += (double)rhs[1 + a][i] * (double)wv[i];
+            s = warp_sum(s);
+            if (lane == 0) {
+                if (c >= 0)
+                    cap[a][c] = s + (a == c ? 1.0 : 0.0);
+                else
+                    cap[a][kMaxK] = s;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // Cholesky solve of the SPD capacitance system
+            double L[kMaxK][kMaxK];
+            for (int j = 0; j < ns; ++j) {
+                double d = cap[j][j];
+                for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+                d = sqrt(fmax(d, 1e-300));
+                L[j][j] = d;
+                for (int i = j + 1; i < ns; ++i) {
+                    double t = cap[i][j];
+                    for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+                    L[i][j] = t / d;
+                }
+            }
+            double y[kMaxK];
+            for (int i = 0; i < ns; ++i) {
+                double t = cap[i][kMaxK];
+                for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
+                y[i] = t / L[i][i];
+            }
+            for (int i = ns - 1; i >= 0; --i) {
+                double t = y[i];
+                for (int k = i + 1; k < ns; ++k) t -= L[k][i] * lam[k];
+                lam[i] = t / L[i][i];
+            }
+        }
+        __syncthreads();
+        double o = (double)out;
+        for (int a = 0; a < ns; ++a) o -= lam[a] * (double)Y[1 + a][tid];
+        out = (R)o;
+    }
+    if (node >= 0) {
+        if (l == 0)
+            z[3 * node + comp] = out;
+        else
+            D.coarse_y[D.coarse_off[l] + 3 * node + comp] = out;
+    }
+}
+
+template <class R>
+__global__ void k_prolong(Dev<R> D, R* __restrict__ z) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= D.nv) return;
+    R a0 = z[3 * v], a1 = z[3 * v + 1], a2 = z[3 * v + 2];
+    for (int l = 1; l < D.nlev; ++l) {
+        const R* y = D.coarse_y + D.coarse_off[l] + 3 * D.node_of_vert[l][v];
+        a0 += y[0];
+        a1 += y[1];
+        a2 += y[2];
+    }
+    z[3 * v] = a0;
+    z[3 * v + 1] = a1;
+    z[3 * v + 2] = a2;
+}
+
+template <class R>
+__global__ void k_clear_upd(Dev<R> D) {
+    D.S->n_upd = 0;
+}
+
+}  // namespace
+
+template <class R>
+void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
+    int nb = D.blk_off[D.nlev];
+    KL(k_clear_upd<R><<<1, 1, 0, st>>>(D));
+    cudaMemsetAsync(D.asmb, 0, sizeof(double) * (size_t)nb * kBlk * kBlk, st);
+    KL(k_tet_hessian<R><<<nblk(D.nt, 64), 64, 0, st>>>(D, x));
+    KL(k_assemble_tets<R><<<nblk(D.nt), kT, 0, st>>>(D));
+    KL(k_assemble_mass<R><<<nblk(D.nv), kT, 0, st>>>(D));
+    KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
+    using T = double;  // blocks are assembled and inverted in FP64, stored in R
+    size_t smem = sizeof(T) * ((size_t)kBlk * kBlk + 2 * kBlk);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_invert<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    KL(k_invert<R, T><<<nb, 256, smem, st>>>(D));
+    cudaMemsetAsync(D.bkeys, 0xFF, sizeof(unsigned long long) * D.btab, st);
+    KL(k_snapshot<R><<<592, kT, 0, st>>>(D));
+}
+
+template <class R>
+void launch_classify(const Dev<R>& D, const ContactBuf& C, cudaStream_t st) {
+    int ng = D.ngroups[0];
+    KL(k_clear_upd<R><<<1, 1, 0, st>>>(D));
+    cudaMemsetAsync(D.upd_cnt, 0, sizeof(int) * ng, st);
+    cudaMemsetAsync(D.upd_cur, 0, sizeof(int) * ng, st);
+    KL(k_classify<R><<<592, kT, 0, st>>>(D, C));
+    scan_exclusive(D.upd_cnt, D.upd_off, ng, D.gtmp, st);
+    KL(k_fill_lists<R><<<592, kT, 0, st>>>(D, C));
+    KL(k_topk<R><<<nblk(32LL * ng), kT, 0, st>>>(D, C));
+}
+
+template <class R>
+void launch_restrict(const Dev<R>& D, const R* g, cudaStream_t st) {
+    if (D.nlev > 1) {
+        cudaMemsetAsync(D.coarse_r, 0, sizeof(R) * D.coarse_off[D.nlev], st);
+        KL(k_restrict<R><<<nblk(D.nv), kT, 0, st>>>(D, g));
+    }
+}
+
+template <class R>
+void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool woodbury, cudaStream_t st) {
+    KL(k_block_apply<R><<<D.blk_off[D.nlev], 96, 0, st>>>(D, g, z, C, woodbury ? 1 : 0));
+}
+
+template <class R>
+void launch_prolong(const Dev<R>& D, R* z, cudaStream_t st) {
+    if (D.nlev > 1) KL(k_prolong<R><<<nblk(D.nv), kT, 0, st>>>(D, z));
+}
+
+template <class R>
+void launch_precond(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool woodbury, cudaStream_t st) {
+    launch_restrict(D, g, st);
+    launch_blocks(D, g, z, C, woodbury, st);
+    launch_prolong(D, z, st);
+}
+
+#define INST(R)                                                                                            \
+    template void launch_restart<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t);         \
+    template void launch_classify<R>(const Dev<R>&, const ContactBuf&, cudaStream_t);                     \
+    template void launch_precond<R>(const Dev<R>&, const R*, R*, const ContactBuf&, bool, cudaStream_t);   \
+    template void launch_restrict<R>(const Dev<R>&, const R*, cudaStream_t);                              \
+    template void launch_blocks<R>(const Dev<R>&, const R*, R*, const ContactBuf&, bool, cudaStream_t);    \
+    template void launch_prolong<R>(const Dev<R>&, R*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace ipcb

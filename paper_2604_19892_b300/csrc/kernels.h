@@ -1,0 +1,46 @@
+// Launch wrappers of the device kernels (instantiated for R = double, float).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "dev.cuh"
+
+namespace ipcb {
+
+// exclusive prefix sum of n ints (out may alias in); tmp needs >= n/1024 + 2 ints
+void scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st);
+
+// predictor x~ = x + h v + h^2 g_ext and x_start = x (Algorithm 1 input)
+template <class R> void launch_predict(const Dev<R>& D, cudaStream_t st);
+// x_try = x + (beta > 0 ? beta : alpha_{d(v)}) p
+template <class R> void launch_trial_positions(const Dev<R>& D, double beta, cudaStream_t st);
+// E(x) and grad E(x) with the contact set C of x (Eq. 1); E accumulates into *E
+template <class R> void launch_energy_grad(const Dev<R>& D, const double* x, const ContactBuf& C, R* g,
+                                           double* E, cudaStream_t st);
+// active contacts at x into C (ComputeConstraintSet); min distance into S->min_dist
+template <class R> void launch_detect(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st);
+// RebuildMAS at x with contacts C: projected tet Hessians, level blocks,
+// batched inversion, C_base snapshot
+template <class R> void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st);
+// classify C against C_base, per-subdomain top-K (Sec. 4.1.1)
+template <class R> void launch_classify(const Dev<R>& D, const ContactBuf& C, cudaStream_t st);
+// z = P g with optional Woodbury update (Eq. 7-8)
+template <class R> void launch_precond(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool woodbury,
+                                       cudaStream_t st);
+// the three parts of launch_precond: coarse restriction, block apply of all
+// levels (with the Woodbury correction at level 0), prolongation
+template <class R> void launch_restrict(const Dev<R>& D, const R* g, cudaStream_t st);
+template <class R> void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool woodbury,
+                                      cudaStream_t st);
+template <class R> void launch_prolong(const Dev<R>& D, R* z, cudaStream_t st);
+// reductions for the 2x2 system (supplement Eq. 13-19), r_k and |z|_inf
+template <class R> void launch_forms(const Dev<R>& D, const ContactBuf& C, bool restart, cudaStream_t st);
+// (mu, nu) and p <- -mu z + nu p
+template <class R> void launch_direction(const Dev<R>& D, bool restart, cudaStream_t st);
+// per-subdomain step sizes for p at x with verification (supplement Sec. 3)
+template <class R> void launch_ccd(const Dev<R>& D, cudaStream_t st);
+// S->accepted = E_try <= E_k
+template <class R> void launch_accept(const Dev<R>& D, cudaStream_t st);
+// H_base-only forms for evaluation entry points
+template <class R> void launch_zero_scalars(const Dev<R>& D, cudaStream_t st);
+
+}  // namespace ipcb

