@@ -158,7 +158,8 @@ typedef enum ipc_query_kind {
     IPC_Q_SURFACE_COUNTS = 8,/* 3 int: surface verts, tris, edges */
     IPC_Q_LEVEL_MAP = 9,     /* per level: group and slot of each node (see
                                 ipc_query_level) */
-    IPC_Q_BBOX_DIAG = 10     /* double */
+    IPC_Q_BBOX_DIAG = 10,    /* double */
+    IPC_Q_N_BODIES = 11      /* int: connected bodies of the mesh */
 } ipc_query_kind;
 
 /* Copy a piece of state into host memory dst (dst_bytes long). */
@@ -234,9 +235,11 @@ int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr,
 
 /* Per-subdomain conservative step sizes for direction p at x (supplement
  * Sec. 3); alpha has n_subdomains entries; *passes = verification passes
- * used, -1 if the uniform fallback was taken. */
+ * used, -1 if the uniform fallback was taken.  alpha_body (n_bodies entries)
+ * and passes_body, if not NULL, receive the same for the grouping by
+ * connected body that the energy check falls back to. */
 int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha,
-                 int* passes, void* stream);
+                 int* passes, double* alpha_body, int* passes_body, void* stream);
 
 const char* ipc_last_error(void);
 

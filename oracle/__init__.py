@@ -95,7 +95,8 @@ def _lib_handle():
             "o_ltight_pt": (C.c_double, [_D]),
             "o_ltight_ee": (C.c_double, [_D]),
             "o_loriginal_pt": (C.c_double, [_D]),
-            "o_ccd": (C.c_int, [C.c_void_p, _D, _D, _D]),
+            "o_ccd": (C.c_int, [C.c_void_p, _D, _D, _D, _D, _I]),
+            "o_bodies": (C.c_int, [C.c_void_p, _I]),
             "o_solve2x2": (None, [C.c_double] * 7 + [_D, _D]),
             "o_step": (C.c_int, [C.c_void_p, _D, _D, C.POINTER(OStepStats)]),
             "o_trace": (C.c_int, [C.c_void_p, C.POINTER(OIterRecord), C.c_int]),
@@ -243,15 +244,26 @@ class Scene:
         self.lib.o_hess_forms(self.h, xbp, xcp, zp, pp, out.ctypes.data_as(_D))
         return out
 
-    def ccd(self, x, p):
+    def bodies(self):
+        b = np.zeros(self.nv, np.int32)
+        n = self.lib.o_bodies(self.h, b.ctypes.data_as(_I))
+        return n, b
+
+    def ccd(self, x, p, per_body=False):
         x, xp = _d(x)
         p, pp = _d(p)
         n = C.c_int()
         g = C.c_int()
         self.lib.o_level_info(self.h, 0, C.byref(n), C.byref(g))
         a = np.zeros(g.value)
-        passes = self.lib.o_ccd(self.h, xp, pp, a.ctypes.data_as(_D))
-        return a, passes
+        if not per_body:
+            passes = self.lib.o_ccd(self.h, xp, pp, a.ctypes.data_as(_D), None, None)
+            return a, passes
+        nb, _ = self.bodies()
+        ab = np.zeros(nb)
+        pb = C.c_int()
+        passes = self.lib.o_ccd(self.h, xp, pp, a.ctypes.data_as(_D), ab.ctypes.data_as(_D), C.byref(pb))
+        return a, passes, ab, pb.value
 
     def step(self, x, v):
         x = np.array(x, dtype=np.float64, copy=True)

@@ -22,12 +22,17 @@
  *  - alpha_d = min(1, min over candidate pairs with a vertex in d).
  *  - Reading for pairs straddling subdomains (the paper is silent): the
  *    actual motion q_v = alpha_d(v) p_v is re-checked with the same cubic
- *    analysis on t in [0, 1]; a pair with safe fraction rho < 1 scales every
- *    subdomain it touches by rho (the smallest rho per subdomain).  At most
- *    4 passes; if the 4th pass still finds a violation, every subdomain takes
- *    the uniform step min_d alpha_d, which is safe by construction.
+ *    analysis on t in [0, 1]; every subdomain touched by a pair whose safe
+ *    fraction rho < 1 takes the smallest alpha among that pair's subdomains
+ *    (the pair then moves uniformly along a segment already checked).  A
+ *    pass sees the alphas of the previous pass.  At most O_CCD_PASSES
+ *    passes; if the last still finds a violation, every subdomain takes the
+ *    uniform step min_d alpha_d, which is safe by construction.  Neither
+ *    outcome is ever below that uniform step.
  */
 #include "o_internal.h"
+
+#define O_CCD_PASSES 8
 
 static double sgn(double v) { return (v > 0.0) - (v < 0.0); }
 
@@ -225,10 +230,66 @@ typedef struct Cand {
     int v[4];
 } Cand;
 
-int o_ccd(OScene* s, const double* x, const double* p, double* alpha) {
-    int ng = s->ngroups[0];
-    const int* grp = s->group_of[0];
+/* Step sizes for one grouping of the vertices (level-0 subdomains or bodies):
+ * alpha_g = min(1, min over candidate pairs and point-ground pairs touching
+ * g), then verification of the pairs straddling groups with the actual motion
+ * alpha_g(v) p_v.  Returns the number of passes, -1 for the uniform fallback. */
+static int group_steps(OScene* s, const double* x, const double* p, const Cand* cand, int nc, const double* apair,
+                       const double* apg, const int* grp, int ng, double* alpha) {
     for (int g = 0; g < ng; ++g) alpha[g] = 1.0;
+    for (int k = 0; k < nc; ++k)
+        for (int j = 0; j < 4; ++j) {
+            int g = grp[cand[k].v[j]];
+            if (apair[k] < alpha[g]) alpha[g] = apair[k];
+        }
+    for (int i = 0; i < s->nsv; ++i) {
+        int g = grp[s->sv[i]];
+        if (apg[i] < alpha[g]) alpha[g] = apg[i];
+    }
+    double* q = (double*)malloc(sizeof(double) * 3 * (size_t)s->nv);
+    double* shrink = (double*)malloc(sizeof(double) * ng);
+    double amin = 1.0;
+    for (int g = 0; g < ng; ++g)
+        if (alpha[g] < amin) amin = alpha[g];
+    int passes = 0, ok = 0;
+    for (int pass = 0; pass < O_CCD_PASSES; ++pass) {
+        ++passes;
+        for (int v = 0; v < s->nv; ++v)
+            for (int r = 0; r < 3; ++r) q[3 * v + r] = alpha[grp[v]] * p[3 * v + r];
+        for (int g = 0; g < ng; ++g) shrink[g] = alpha[g];
+        int viol = 0;
+        for (int k = 0; k < nc; ++k) {
+            const int* v = cand[k].v;
+            int g0 = grp[v[0]];
+            if (grp[v[1]] == g0 && grp[v[2]] == g0 && grp[v[3]] == g0) continue;
+            double rho = pair_safe(s, cand[k].kind, v, x, q);
+            if (rho < 1.0) {
+                /* equalise: every group of the pair takes the pair's smallest
+                 * alpha, so the pair moves uniformly */
+                viol = 1;
+                double m = alpha[grp[v[0]]];
+                for (int j = 1; j < 4; ++j)
+                    if (alpha[grp[v[j]]] < m) m = alpha[grp[v[j]]];
+                for (int j = 0; j < 4; ++j)
+                    if (m < shrink[grp[v[j]]]) shrink[grp[v[j]]] = m;
+            }
+        }
+        if (!viol) {
+            ok = 1;
+            break;
+        }
+        for (int g = 0; g < ng; ++g) alpha[g] = shrink[g];
+    }
+    if (!ok) {
+        for (int g = 0; g < ng; ++g) alpha[g] = amin;
+        passes = -1;
+    }
+    free(q);
+    free(shrink);
+    return passes;
+}
+
+int o_ccd(OScene* s, const double* x, const double* p, double* alpha, double* alpha_body, int* passes_body) {
     Cand* cand = NULL;
     int nc = 0, cc = 0;
     /* swept boxes of surface points, triangles and edges over [x, x + p] */
@@ -314,62 +375,29 @@ int o_ccd(OScene* s, const double* x, const double* p, double* alpha) {
     free(pb);
     free(tb);
     free(eb);
-    /* per-pair steps */
-    for (int k = 0; k < nc; ++k) {
-        double a = pair_safe(s, cand[k].kind, cand[k].v, x, p);
-        for (int j = 0; j < 4; ++j) {
-            int g = grp[cand[k].v[j]];
-            if (a < alpha[g]) alpha[g] = a;
-        }
+    /* per-pair steps, computed once for both groupings */
+    double* apair = (double*)malloc(sizeof(double) * (nc + 1));
+    for (int k = 0; k < nc; ++k) apair[k] = pair_safe(s, cand[k].kind, cand[k].v, x, p);
+    double* apg = (double*)malloc(sizeof(double) * (s->nsv + 1));
+    for (int i = 0; i < s->nsv; ++i) {
+        int v = s->sv[i];
+        apg[i] = 1.0;
+        if (!s->has_ground) continue;
+        double vn = s->gn[0] * p[3 * v] + s->gn[1] * p[3 * v + 1] + s->gn[2] * p[3 * v + 2];
+        if (!(vn < 0.0)) continue;
+        double d0 = s->gn[0] * x[3 * v] + s->gn[1] * x[3 * v + 1] + s->gn[2] * x[3 * v + 2] - s->goff;
+        double a = (1.0 - s->prm.ccd_shrink) * d0 / (-vn);
+        if (a > 1.0) a = 1.0;
+        if (!(a > 0.0)) a = 0.0;
+        apg[i] = a;
     }
-    if (s->has_ground) {
-        for (int i = 0; i < s->nsv; ++i) {
-            int v = s->sv[i];
-            double vn = s->gn[0] * p[3 * v] + s->gn[1] * p[3 * v + 1] + s->gn[2] * p[3 * v + 2];
-            if (!(vn < 0.0)) continue;
-            double d0 = s->gn[0] * x[3 * v] + s->gn[1] * x[3 * v + 1] + s->gn[2] * x[3 * v + 2] - s->goff;
-            double a = (1.0 - s->prm.ccd_shrink) * d0 / (-vn);
-            if (a > 1.0) a = 1.0;
-            if (!(a > 0.0)) a = 0.0;
-            if (a < alpha[grp[v]]) alpha[grp[v]] = a;
-        }
+    int passes = group_steps(s, x, p, cand, nc, apair, apg, s->group_of[0], s->ngroups[0], alpha);
+    if (alpha_body) {
+        int pb2 = group_steps(s, x, p, cand, nc, apair, apg, s->body, s->nbody, alpha_body);
+        if (passes_body) *passes_body = pb2;
     }
-    /* verification of straddling pairs with the actual motion */
-    double* q = (double*)malloc(sizeof(double) * 3 * (size_t)s->nv);
-    double* shrink = (double*)malloc(sizeof(double) * ng);
-    double amin = 1.0;
-    for (int g = 0; g < ng; ++g)
-        if (alpha[g] < amin) amin = alpha[g];
-    int passes = 0, ok = 0;
-    for (int pass = 0; pass < 4; ++pass) {
-        ++passes;
-        for (int v = 0; v < s->nv; ++v)
-            for (int r = 0; r < 3; ++r) q[3 * v + r] = alpha[grp[v]] * p[3 * v + r];
-        for (int g = 0; g < ng; ++g) shrink[g] = 1.0;
-        int viol = 0;
-        for (int k = 0; k < nc; ++k) {
-            const int* v = cand[k].v;
-            int g0 = grp[v[0]];
-            if (grp[v[1]] == g0 && grp[v[2]] == g0 && grp[v[3]] == g0) continue;
-            double rho = pair_safe(s, cand[k].kind, v, x, q);
-            if (rho < 1.0) {
-                viol = 1;
-                for (int j = 0; j < 4; ++j)
-                    if (rho < shrink[grp[v[j]]]) shrink[grp[v[j]]] = rho;
-            }
-        }
-        if (!viol) {
-            ok = 1;
-            break;
-        }
-        for (int g = 0; g < ng; ++g) alpha[g] *= shrink[g];
-    }
-    if (!ok) {
-        for (int g = 0; g < ng; ++g) alpha[g] = amin;
-        passes = -1;
-    }
-    free(q);
-    free(shrink);
+    free(apair);
+    free(apg);
     free(cand);
     return passes;
 }

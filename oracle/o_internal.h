@@ -63,6 +63,9 @@ struct OScene {
 
     /* vertex adjacency from tet edges */
     int *adj_ptr, *adj;
+    /* connected components of the tet mesh, numbered by lowest vertex id */
+    int nbody;
+    int* body;
 
     /* MAS hierarchy: level l nodes, grouped into subdomains of <= subdomain
      * nodes.  node_of_vert[l][v] is the level-l node containing vertex v

@@ -310,6 +310,33 @@ static void bfs_order(int n, const int* ptr, const int* nb, int* order) {
     free(seen);
 }
 
+/* bodies: connected components over tet edges, numbered in order of their
+ * lowest vertex id */
+static void build_bodies(OScene* s) {
+    s->body = (int*)malloc(sizeof(int) * s->nv);
+    for (int v = 0; v < s->nv; ++v) s->body[v] = -1;
+    int* stack = (int*)malloc(sizeof(int) * s->nv);
+    s->nbody = 0;
+    for (int v0 = 0; v0 < s->nv; ++v0) {
+        if (s->body[v0] >= 0) continue;
+        int top = 0;
+        stack[top++] = v0;
+        s->body[v0] = s->nbody;
+        while (top > 0) {
+            int u = stack[--top];
+            for (int k = s->adj_ptr[u]; k < s->adj_ptr[u + 1]; ++k) {
+                int w = s->adj[k];
+                if (s->body[w] < 0) {
+                    s->body[w] = s->nbody;
+                    stack[top++] = w;
+                }
+            }
+        }
+        s->nbody++;
+    }
+    free(stack);
+}
+
 int o_build_hierarchy(OScene* s) {
     int S = s->prm.subdomain;
     int n = s->nv;
@@ -436,6 +463,7 @@ OScene* o_scene_create(int nv, const double* x_rest, int nt, const int* tets,
                    (hi[2] - lo[2]) * (hi[2] - lo[2]));
     build_surface(s);
     build_adjacency(s);
+    build_bodies(s);
     o_build_hierarchy(s);
     return s;
 }
@@ -455,6 +483,7 @@ void o_scene_destroy(OScene* s) {
     free(s->on_surface);
     free(s->adj_ptr);
     free(s->adj);
+    free(s->body);
     for (int l = 0; l < s->nlev; ++l) {
         free(s->group_of[l]);
         free(s->slot_of[l]);
@@ -497,6 +526,11 @@ void o_surface_get(const OScene* s, int* verts, int* tris, int* edges) {
 void o_mass_get(const OScene* s, double* mass) { memcpy(mass, s->mass, sizeof(double) * s->nv); }
 
 double o_bbox_diag(const OScene* s) { return s->bbox; }
+
+int o_bodies(const OScene* s, int* body_of_vertex) {
+    if (body_of_vertex) memcpy(body_of_vertex, s->body, sizeof(int) * s->nv);
+    return s->nbody;
+}
 
 int o_levels(const OScene* s) { return s->nlev; }
 

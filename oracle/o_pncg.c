@@ -19,11 +19,13 @@
  *    per-subdomain step x + sum_d alpha_d S_d p; it is accepted if
  *    E(x_{k+1}) <= E(x_k).  Per-subdomain scaling of p is not in general a
  *    descent direction (it can stretch a body whose lower subdomains are
- *    clamped), so a rejected first trial switches to the uniform step
- *    beta = min_d alpha_d (safe by construction) and halves beta until the
- *    energy does not increase, ls_max trials in all.  If none is accepted,
- *    x does not move and the next iteration restarts; a rejection on a
- *    restart iteration ends the step unconverged.
+ *    clamped), so a rejected first trial falls back to per-body steps (each
+ *    connected body moves uniformly by its own verified alpha_b) scaled by
+ *    1, 1/2, 1/4, 1/8 -- skipped when no body exceeds the uniform step --
+ *    then to the uniform step beta = min_d alpha_d (safe by construction)
+ *    halved until the energy does not increase, ls_max + 1 trials in all.
+ *    If none is accepted, x does not move and the next iteration restarts; a
+ *    rejection on a restart iteration ends the step unconverged.
  *  - Velocity update v = (x^{t+1} - x^t) / h; x~ = x + h v + h^2 gravity.
  */
 #include "o_internal.h"
@@ -141,6 +143,7 @@ int o_step(OScene* s, double* x, double* v, OStepStats* st) {
     double* q = (double*)malloc(sizeof(double) * n3);
     double* xtry = (double*)malloc(sizeof(double) * n3);
     double* alpha = (double*)malloc(sizeof(double) * s->ngroups[0]);
+    double* alpha_b = (double*)malloc(sizeof(double) * s->nbody);
     memcpy(xstart, x, sizeof(double) * n3);
     memcpy(xk, x, sizeof(double) * n3);
     for (int i = 0; i < nv; ++i)
@@ -190,28 +193,36 @@ int o_step(OScene* s, double* x, double* v, OStepStats* st) {
         }
         rec.znorm = zn;
         S.znorm = zn;
-        /* step sizes */
-        o_ccd(s, xk, p, alpha);
+        /* step sizes per level-0 subdomain and per body */
+        o_ccd(s, xk, p, alpha, alpha_b, NULL);
         rec.alpha_min = 1.0;
         rec.alpha_max = 0.0;
         for (int gi = 0; gi < s->ngroups[0]; ++gi) {
             if (alpha[gi] < rec.alpha_min) rec.alpha_min = alpha[gi];
             if (alpha[gi] > rec.alpha_max) rec.alpha_max = alpha[gi];
         }
-        for (int i = 0; i < nv; ++i) {
-            double a = alpha[s->group_of[0][i]];
-            for (int r = 0; r < 3; ++r) q[3 * i + r] = a * p[3 * i + r];
-        }
-        /* energy check: per-subdomain trial, then uniform halving */
+        double bmax = 0.0;
+        for (int b = 0; b < s->nbody; ++b)
+            if (alpha_b[b] > bmax) bmax = alpha_b[b];
+        /* energy check over the trial list: per-subdomain step; per-body
+         * steps scaled by 1, 1/2, 1/4, 1/8; uniform steps alpha_min / 2^j */
         rec.energy_before = Ek;
         int accepted = 0, halv = 0;
-        double beta = rec.alpha_min;
-        int uniform_first = rec.alpha_max > rec.alpha_min;
+        int body_tier = bmax > rec.alpha_min;
+        int j0 = (rec.alpha_max > rec.alpha_min || body_tier) ? 0 : 1;
         for (int ls = 0; ls <= s->prm.ls_max; ++ls) {
             if (ls == 0) {
-                for (int i = 0; i < n3; ++i) xtry[i] = xk[i] + q[i];
+                for (int i = 0; i < nv; ++i)
+                    for (int r = 0; r < 3; ++r)
+                        xtry[3 * i + r] = xk[3 * i + r] + alpha[s->group_of[0][i]] * p[3 * i + r];
+            } else if (body_tier && ls <= 4) {
+                double c = ldexp(1.0, -(ls - 1));
+                for (int i = 0; i < nv; ++i)
+                    for (int r = 0; r < 3; ++r)
+                        xtry[3 * i + r] = xk[3 * i + r] + c * alpha_b[s->body[i]] * p[3 * i + r];
             } else {
-                if (ls > 1 || !uniform_first) beta *= 0.5;
+                int j = j0 + (ls - 1 - (body_tier ? 4 : 0));
+                double beta = ldexp(rec.alpha_min, -j);
                 for (int i = 0; i < n3; ++i) xtry[i] = xk[i] + beta * p[i];
             }
             o_find_contacts(s, xtry, &Ctry);
@@ -276,5 +287,6 @@ int o_step(OScene* s, double* x, double* v, OStepStats* st) {
     free(q);
     free(xtry);
     free(alpha);
+    free(alpha_b);
     return S.converged ? 0 : 1;
 }

@@ -147,8 +147,11 @@ double o_ltight_ee(const double* p4);
 double o_loriginal_pt(const double* p4);
 /* per-subdomain step sizes for direction p at x; alpha has one entry per
  * level-0 subdomain; returns number of verification passes (-1 = uniform
- * fallback was taken). */
-int o_ccd(OScene* s, const double* x, const double* p, double* alpha);
+ * fallback was taken).  If alpha_body is not NULL it receives the same for
+ * the grouping by connected body (one entry per body), with its passes in
+ * *passes_body. */
+int o_ccd(OScene* s, const double* x, const double* p, double* alpha, double* alpha_body, int* passes_body);
+int o_bodies(const OScene* s, int* body_of_vertex);
 
 /* ---- 2x2 subspace ----------------------------------------------------- */
 void o_solve2x2(double A11, double A12, double A22, double b1, double b2,

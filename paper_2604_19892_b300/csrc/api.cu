@@ -296,6 +296,11 @@ int setup_dev(ipc_scene* s) {
     D.topk = A.arr<int>((size_t)m.ngroups[0] * std::max(1, D.K));
     D.alpha = A.arr<double>(m.ngroups[0]);
     D.shrink = A.arr<double>(m.ngroups[0]);
+    D.nbody = m.nbody;
+    int* d_body = A.arr<int>(m.nv);
+    D.body = d_body;
+    D.alpha_b = A.arr<double>(m.nbody);
+    D.shrink_b = A.arr<double>(m.nbody);
     D.str_v = A.arr<int4>(D.straddle_cap);
     D.str_t = A.arr<int>(D.straddle_cap);
     int nprim = std::max(std::max(D.nsf, D.nse), 1);
@@ -346,6 +351,7 @@ int setup_dev(ipc_scene* s) {
     if (D.nse) CUDA_TRY(cudaMemcpy(d_se, m.se.data(), sizeof(int) * m.se.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_grp0, m.group_of[0].data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_slot0, m.slot_of[0].data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_body, m.body.data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice));
     for (int l = 0; l < m.nlev; ++l) {
         if (l >= 1) CUDA_TRY(cudaMemcpy(d_nov[l], m.node_of_vert[l].data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(d_gon[l], m.group_of[l].data(), sizeof(int) * m.nnodes[l], cudaMemcpyHostToDevice));
@@ -399,8 +405,8 @@ void eval_current(const Dev<R>& D, cudaStream_t st) {
 }
 
 template <class R>
-void eval_trial(const Dev<R>& D, double beta, cudaStream_t st) {
-    launch_trial_positions(D, beta, st);
+void eval_trial(const Dev<R>& D, int mode, double c, cudaStream_t st) {
+    launch_trial_positions(D, mode, c, st);
     launch_detect(D, D.xtry, D.Ct, st);
     launch_energy_grad(D, D.xtry, D.Ct, D.gtry, &D.S->E_try, st);
     launch_accept(D, st);
@@ -422,7 +428,7 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
     }
     if (int e = read_view(s, D, st)) return e;
     if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
-    if (s->hv->nC > 0 && !(s->hv->S.min_dist > 0.0))
+    if (s->hv->S.nonpos)
         return fail(IPC_ERR_INTERSECTING, "a contact has non-positive distance");
     s->trace.clear();
     double Ek = s->hv->S.E_k;
@@ -469,7 +475,7 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         }
         {
             Stage t(s, 6, st);
-            eval_trial(D, 0.0, st);
+            eval_trial(D, 0, 0.0, st);
         }
         if (int e = read_view(s, D, st)) return e;
         Scalars S = s->hv->S;
@@ -487,14 +493,19 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         int accepted = S.accepted;
         int halv = 0;
         if (!accepted) {
+            // trial list after the per-subdomain step: per-body steps scaled
+            // by 1, 1/2, 1/4, 1/8 (when some body exceeds the uniform step),
+            // then the uniform step alpha_min / 2^j
             halv = 1;
-            double beta = S.alpha_min;
-            bool uniform_first = S.alpha_max > S.alpha_min;
+            bool body_tier = S.alpha_bmax > S.alpha_min;
+            int j0 = (S.alpha_max > S.alpha_min || body_tier) ? 0 : 1;
             for (int ls = 1; ls <= P.ls_max; ++ls) {
-                if (ls > 1 || !uniform_first) beta *= 0.5;
                 {
                     Stage t(s, 6, st);
-                    eval_trial(D, beta, st);
+                    if (body_tier && ls <= 4)
+                        eval_trial(D, 1, std::ldexp(1.0, -(ls - 1)), st);
+                    else
+                        eval_trial(D, 2, std::ldexp(S.alpha_min, -(j0 + ls - 1 - (body_tier ? 4 : 0))), st);
                 }
                 if (int e = read_view(s, D, st)) return e;
                 if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
@@ -702,7 +713,8 @@ int eval_forms_impl(ipc_scene* s, const double* xb, const double* xc, const doub
 }
 
 template <class R>
-int eval_ccd_impl(ipc_scene* s, const double* x, const double* p, double* alpha, int* passes, cudaStream_t st) {
+int eval_ccd_impl(ipc_scene* s, const double* x, const double* p, double* alpha, int* passes, double* alpha_body,
+                  int* passes_body, cudaStream_t st) {
     Dev<R>& D = dev_of<R>(s);
     size_t n3 = 3 * (size_t)D.nv;
     Dev<R> E = D;
@@ -722,6 +734,8 @@ int eval_ccd_impl(ipc_scene* s, const double* x, const double* p, double* alpha,
     int ng = D.ngroups[0];
     CUDA_TRY(cudaMemcpy(alpha, D.alpha, sizeof(double) * ng, cudaMemcpyDeviceToHost));
     if (passes) *passes = s->hv->S.ccd_passes;
+    if (alpha_body) CUDA_TRY(cudaMemcpy(alpha_body, D.alpha_b, sizeof(double) * D.nbody, cudaMemcpyDeviceToHost));
+    if (passes_body) *passes_body = s->hv->S.ccd_passes_b;
     return IPC_OK;
 }
 
@@ -793,7 +807,7 @@ int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params, const
         ipc_scene_destroy(s);
         return fail(r, msg);
     }
-    if (nc > 0 && !(s->hv->S.min_dist > 0.0)) {
+    if (s->hv->S.nonpos) {
         ipc_scene_destroy(s);
         return fail(IPC_ERR_INTERSECTING, "initial state has a contact at distance <= 0");
     }
@@ -889,6 +903,10 @@ int ipc_query(ipc_scene* s, int what, void* dst, size_t bytes, void* stream) {
             o[2] = (int)(s->hm.se.size() / 2);
             return IPC_OK;
         }
+        case IPC_Q_N_BODIES:
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            *(int*)dst = s->hm.nbody;
+            return IPC_OK;
         case IPC_Q_BBOX_DIAG:
             if (!need(sizeof(double))) return fail(IPC_ERR_INVALID, "destination too small");
             *(double*)dst = s->hm.bbox_diag;
@@ -973,11 +991,12 @@ int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr, con
                                     : eval_forms_impl<float>(s, x_base, x_curr, z, p, out, st);
 }
 
-int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha, int* passes, void* stream) {
+int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha, int* passes, double* alpha_body,
+                 int* passes_body, void* stream) {
     if (!checked(s) || !x || !p || !alpha) return fail(IPC_ERR_INVALID, "null argument");
     cudaStream_t st = (cudaStream_t)stream;
-    return s->prec == IPC_PREC_FP64 ? eval_ccd_impl<double>(s, x, p, alpha, passes, st)
-                                    : eval_ccd_impl<float>(s, x, p, alpha, passes, st);
+    return s->prec == IPC_PREC_FP64 ? eval_ccd_impl<double>(s, x, p, alpha, passes, alpha_body, passes_body, st)
+                                    : eval_ccd_impl<float>(s, x, p, alpha, passes, alpha_body, passes_body, st);
 }
 
 }  // extern "C"

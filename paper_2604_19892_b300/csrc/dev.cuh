@@ -46,10 +46,13 @@ struct Scalars {
     int ccd_viol;                  // verification found a violation
     int ccd_uniform;               // 2 verified, 1 fell back to uniform alpha
     int ccd_passes;                // verification passes run
+    int ccd_viol_b, ccd_uniform_b, ccd_passes_b;  // the same for the body grouping
+    double alpha_bmin, alpha_bmax; // smallest / largest per-body step
     int n_upd;                     // classified updates
     int n_straddle;                // straddling CCD candidates
     int overflow;                  // bit flags: 1 contacts, 2 straddle, 4 upd
     int nan_flag;
+    int nonpos;                    // a contact of the last detection has d <= 0
     double alpha_min, alpha_max;
     double beta;                   // uniform step of the current trial (0 = per-subdomain)
 };
@@ -123,6 +126,10 @@ struct Dev {
     // CCD
     double* alpha;                         // per level-0 group
     double* shrink;
+    int nbody;
+    const int* body;                       // connected body of each vertex
+    double* alpha_b;                       // per body
+    double* shrink_b;
     int4* str_v;                           // straddling candidates: vertices
     int* str_t;                            // 0 PT (p, t0, t1, t2), 1 EE (a0, a1, b0, b1)
     // broad-phase grid (shared by proximity and CCD queries)

@@ -190,6 +190,30 @@ int build_host_mesh(const ipc_scene_desc* d, int levels_max, HostMesh* m, std::s
                 if (a != b) pr.emplace_back(m->tets[4 * t + a], m->tets[4 * t + b]);
     pairs_to_csr(nv, pr, m->vert_adj_ptr, m->vert_adj);
 
+    // bodies: components over tet edges, numbered in order of lowest vertex
+    m->body.assign(nv, -1);
+    m->nbody = 0;
+    {
+        std::vector<int> stack;
+        for (int v0 = 0; v0 < nv; ++v0) {
+            if (m->body[v0] >= 0) continue;
+            m->body[v0] = m->nbody;
+            stack.push_back(v0);
+            while (!stack.empty()) {
+                int u = stack.back();
+                stack.pop_back();
+                for (int k = m->vert_adj_ptr[u]; k < m->vert_adj_ptr[u + 1]; ++k) {
+                    int w = m->vert_adj[k];
+                    if (m->body[w] < 0) {
+                        m->body[w] = m->nbody;
+                        stack.push_back(w);
+                    }
+                }
+            }
+            ++m->nbody;
+        }
+    }
+
     // hierarchy
     std::vector<int> ptr = m->vert_adj_ptr, nb = m->vert_adj;
     int n = nv;

@@ -20,6 +20,9 @@ struct HostMesh {
     // boundary surface in lexicographic order of sorted vertex ids
     std::vector<int> sv, sf, se;
     std::vector<int> vert_adj_ptr, vert_adj;
+    // connected components of the tet mesh, numbered by their lowest vertex id
+    int nbody = 0;
+    std::vector<int> body;
     // hierarchy: level l has nnodes[l] nodes in ngroups[l] groups of <= 32
     int nlev = 0;
     std::vector<int> nnodes, ngroups;

@@ -17,9 +17,9 @@
 // alpha_l = (1 - s) d0 / l_tight (supplement Eq. 29 / 31); point-ground takes
 // min(1, (1 - s) d0 / (-n.p)).  alpha_d is the minimum over candidate pairs
 // touching subdomain d; pairs straddling subdomains are re-checked with the
-// actual motion alpha_d(v) p_v, shrinking the subdomains of a pair whose safe
-// fraction rho < 1 by rho, for at most 4 passes, then the uniform step
-// min_d alpha_d is taken.
+// actual motion alpha_d(v) p_v; the subdomains of a pair whose safe fraction
+// rho < 1 all take the pair's smallest alpha; after at most 8 passes with a
+// violation the uniform step min_d alpha_d is taken (never below it).
 #include "geom.cuh"
 #include "kernels.h"
 
@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kT = 128;
 constexpr int kMaxCells = 64;
+constexpr int kCcdPasses = 8;   // verification passes before the uniform fallback
 
 inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
 
@@ -168,7 +169,10 @@ __device__ __forceinline__ void put_contact(const ContactBuf& C, int cap, int ty
     C.r[3 * i + 1] = r.y;
     C.r[3 * i + 2] = r.z;
     for (int j = 0; j < 4; ++j) C.w[4 * i + j] = w[j];
-    atomicMinPos(&S->min_dist, d);
+    if (d > 0.0)
+        atomicMinPos(&S->min_dist, d);
+    else
+        S->nonpos = 1;  // touching or penetrating (bit-pattern min is only valid for d > 0)
 }
 
 template <class R>
@@ -296,16 +300,18 @@ template <class R>
 __global__ void k_reset_detect(Dev<R> D, ContactBuf C) {
     *C.count = 0;
     D.S->min_dist = __longlong_as_double(0x7ff0000000000000ULL);
+    D.S->nonpos = 0;
 }
 
 // ------------------------------------------------------------------- CCD
 
 template <class R>
-__device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const double* x, const R* p, const double* scale) {
+__device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const double* x, const R* p, const double* scale,
+                             const int* grp = nullptr) {
     d3 X[4], Q[4];
     for (int j = 0; j < 4; ++j) {
         X[j] = ld3(x + 3 * v[j]);
-        double s = scale ? scale[D.grp0[v[j]]] : 1.0;
+        double s = scale ? scale[grp[v[j]]] : 1.0;
         Q[j] = mk(s * (double)p[3 * v[j]], s * (double)p[3 * v[j] + 1], s * (double)p[3 * v[j] + 2]);
     }
     double d0, l = 0.0, c[4];
@@ -335,13 +341,19 @@ template <class R>
 __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
     double a = pair_alpha(D, kind, v, D.x, D.p, nullptr);
     int g0 = D.grp0[v[0]], g1 = D.grp0[v[1]], g2 = D.grp0[v[2]], g3 = D.grp0[v[3]];
+    int b0 = D.body[v[0]], b1 = D.body[v[1]], b2 = D.body[v[2]], b3 = D.body[v[3]];
     if (a < 1.0) {
         atomicMinPos(&D.alpha[g0], a);
         if (g1 != g0) atomicMinPos(&D.alpha[g1], a);
         if (g2 != g0 && g2 != g1) atomicMinPos(&D.alpha[g2], a);
         if (g3 != g0 && g3 != g1 && g3 != g2) atomicMinPos(&D.alpha[g3], a);
+        atomicMinPos(&D.alpha_b[b0], a);
+        if (b1 != b0) atomicMinPos(&D.alpha_b[b1], a);
+        if (b2 != b0 && b2 != b1) atomicMinPos(&D.alpha_b[b2], a);
+        if (b3 != b0 && b3 != b1 && b3 != b2) atomicMinPos(&D.alpha_b[b3], a);
     }
-    if (!(g1 == g0 && g2 == g0 && g3 == g0)) {
+    // keep every pair that straddles subdomains or bodies for verification
+    if (!(g1 == g0 && g2 == g0 && g3 == g0) || !(b1 == b0 && b2 == b0 && b3 == b0)) {
         int k = atomicAdd(&D.S->n_straddle, 1);
         if (k < D.straddle_cap) {
             D.str_v[k] = make_int4(v[0], v[1], v[2], v[3]);
@@ -462,7 +474,10 @@ __global__ void k_ccd_pg(Dev<R> D) {
     double d0 = dot(n, ld3(D.x + 3 * pv)) - D.goff;
     double a = fmin(1.0, (1.0 - D.ccd_shrink) * d0 / (-vn));
     if (!(a > 0.0)) a = 0.0;
-    if (a < 1.0) atomicMinPos(&D.alpha[D.grp0[pv]], a);
+    if (a < 1.0) {
+        atomicMinPos(&D.alpha[D.grp0[pv]], a);
+        atomicMinPos(&D.alpha_b[D.body[pv]], a);
+    }
 }
 
 template <class R>
@@ -475,20 +490,32 @@ template <class R>
 __global__ void k_ccd_begin(Dev<R> D) {
     Scalars* S = D.S;
     S->n_straddle = 0;
-    S->ccd_viol = 0;
-    S->ccd_uniform = 0;
-    S->ccd_passes = 0;
+    S->ccd_viol = S->ccd_viol_b = 0;
+    S->ccd_uniform = S->ccd_uniform_b = 0;
+    S->ccd_passes = S->ccd_passes_b = 0;
 }
 
-// one block: min / max of alpha over subdomains; which = 0 stores alpha_min
-// for the fallback, 1 stores the final min / max
-template <class R>
-__global__ void k_alpha_minmax(Dev<R> D, int which) {
+// One grouping of the vertices (level-0 subdomains or bodies) with its step
+// sizes, verification scratch and status words.
+struct Grouping {
+    const int* of;        // group of each vertex
+    double* alpha;
+    double* shrink;
+    int n;
+    int* viol;
+    int* state;           // 0 running, 1 uniform fallback, 2 verified
+    int* passes;
+    double* amin;         // minimum before verification (the uniform step)
+    double* amax;
+};
+
+// one block: min / max of a[0..n)
+__global__ void k_minmax(const double* a, int n, double* out_min, double* out_max) {
     __shared__ double smin[32], smax[32];
     double mn = 1.0, mx = 0.0;
-    for (int g = threadIdx.x; g < D.ngroups[0]; g += blockDim.x) {
-        mn = fmin(mn, D.alpha[g]);
-        mx = fmax(mx, D.alpha[g]);
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        mn = fmin(mn, a[g]);
+        mx = fmax(mx, a[g]);
     }
     for (int o = 16; o > 0; o >>= 1) {
         mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -504,66 +531,77 @@ __global__ void k_alpha_minmax(Dev<R> D, int which) {
             mn = fmin(mn, smin[w]);
             mx = fmax(mx, smax[w]);
         }
-        if (which == 0) {
-            D.S->alpha_min = mn;  // pre-verification minimum for the uniform fallback
-        } else {
-            D.S->alpha_min = mn;
-            D.S->alpha_max = mx;
-        }
+        if (out_min) *out_min = mn;
+        if (out_max) *out_max = mx;
     }
 }
 
-// verification pass: re-check straddling pairs with the actual motion
+// verification pass: re-check pairs straddling groups with the actual motion
+// alpha_g(v) p_v; a violating pair lowers every group it touches to the
+// pair's smallest alpha (the pair then moves uniformly on a segment already
+// checked)
+__global__ void k_verify_prep(Grouping G) {
+    if (*G.state == 2) return;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.shrink[g] = G.alpha[g];
+}
+
 template <class R>
-__global__ void k_verify(Dev<R> D) {
-    Scalars* S = D.S;
-    if (S->ccd_uniform == 2) return;  // finished
-    int n = min(S->n_straddle, D.straddle_cap);
+__global__ void k_verify(Dev<R> D, Grouping G) {
+    if (*G.state == 2) return;  // finished
+    int n = min(D.S->n_straddle, D.straddle_cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         int4 q = D.str_v[k];
         int v[4] = {q.x, q.y, q.z, q.w};
-        double rho = pair_alpha(D, D.str_t[k], v, D.x, D.p, D.alpha);
+        int g0 = G.of[v[0]];
+        if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) continue;
+        double rho = pair_alpha(D, D.str_t[k], v, D.x, D.p, G.alpha, G.of);
         if (rho < 1.0) {
-            S->ccd_viol = 1;
-            for (int j = 0; j < 4; ++j) atomicMinPos(&D.shrink[D.grp0[v[j]]], rho);
+            *G.viol = 1;
+            double m = G.alpha[g0];
+            for (int j = 1; j < 4; ++j) m = fmin(m, G.alpha[G.of[v[j]]]);
+            for (int j = 0; j < 4; ++j) atomicMinPos(&G.shrink[G.of[v[j]]], m);
         }
     }
 }
 
-template <class R>
-__global__ void k_verify_apply(Dev<R> D) {
-    Scalars* S = D.S;
-    if (S->ccd_uniform == 2 || !S->ccd_viol) return;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < D.ngroups[0]; g += gridDim.x * blockDim.x) {
-        D.alpha[g] *= D.shrink[g];
-        D.shrink[g] = 1.0;
-    }
+__global__ void k_verify_apply(Grouping G) {
+    if (*G.state == 2 || !*G.viol) return;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.alpha[g] = G.shrink[g];
 }
 
 // after pass `pass`: stop if clean; after the last pass with a violation
 // mark the uniform fallback
-template <class R>
-__global__ void k_verify_flag(Dev<R> D, int pass, int last) {
-    Scalars* S = D.S;
-    if (S->ccd_uniform == 2) return;
-    if (!S->ccd_viol) {
-        S->ccd_uniform = 2;  // verified
-        S->ccd_passes = pass + 1;
+__global__ void k_verify_flag(Grouping G, int pass, int last) {
+    if (*G.state == 2) return;
+    if (!*G.viol) {
+        *G.state = 2;
+        *G.passes = pass + 1;
         return;
     }
-    S->ccd_viol = 0;
+    *G.viol = 0;
     if (last) {
-        S->ccd_uniform = 1;
-        S->ccd_passes = -1;
+        *G.state = 1;
+        *G.passes = -1;
     }
 }
 
+__global__ void k_uniform(Grouping G) {
+    if (*G.state != 1) return;
+    double a = *G.amin;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.alpha[g] = a;
+}
+
 template <class R>
-__global__ void k_uniform(Dev<R> D, double amin_dummy) {
-    Scalars* S = D.S;
-    if (S->ccd_uniform != 1) return;
-    double a = S->alpha_min;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < D.ngroups[0]; g += gridDim.x * blockDim.x) D.alpha[g] = a;
+void verify_grouping(const Dev<R>& D, const Grouping& G, cudaStream_t st) {
+    KL(k_minmax<<<1, 1024, 0, st>>>(G.alpha, G.n, G.amin, nullptr));
+    for (int pass = 0; pass < kCcdPasses; ++pass) {
+        KL(k_verify_prep<<<nblk(G.n), kT, 0, st>>>(G));
+        KL(k_verify<R><<<592, kT, 0, st>>>(D, G));
+        KL(k_verify_apply<<<nblk(G.n), kT, 0, st>>>(G));
+        KL(k_verify_flag<<<1, 1, 0, st>>>(G, pass, pass == kCcdPasses - 1 ? 1 : 0));
+    }
+    KL(k_uniform<<<nblk(G.n), kT, 0, st>>>(G));
+    KL(k_minmax<<<1, 1024, 0, st>>>(G.alpha, G.n, G.amin, G.amax));
 }
 
 }  // namespace
@@ -584,21 +622,20 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     int ng = D.ngroups[0];
     KL(k_ccd_begin<R><<<1, 1, 0, st>>>(D));
     KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
-    KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.shrink, ng, 1.0));
+    KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
     int* gin = D.gin;
     build_grid<R>(D, D.sf, 3, D.nsf, D.x, D.p, 0.0, gin, true, st);
     if (D.nsv) KL(k_ccd_pt<R><<<nblk(D.nsv), kT, 0, st>>>(D, gin));
     build_grid<R>(D, D.se, 2, D.nse, D.x, D.p, 0.0, gin, true, st);
     if (D.nse) KL(k_ccd_ee<R><<<nblk(D.nse), kT, 0, st>>>(D, gin));
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
-    KL(k_alpha_minmax<R><<<1, 1024, 0, st>>>(D, 0));
-    for (int pass = 0; pass < 4; ++pass) {
-        KL(k_verify<R><<<592, kT, 0, st>>>(D));
-        KL(k_verify_apply<R><<<nblk(ng), kT, 0, st>>>(D));
-        KL(k_verify_flag<R><<<1, 1, 0, st>>>(D, pass, pass == 3 ? 1 : 0));
-    }
-    KL(k_uniform<R><<<nblk(ng), kT, 0, st>>>(D, 0.0));
-    KL(k_alpha_minmax<R><<<1, 1024, 0, st>>>(D, 1));
+    Scalars* S = D.S;
+    Grouping sub{D.grp0, D.alpha, D.shrink, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes, &S->alpha_min,
+                 &S->alpha_max};
+    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b, &S->ccd_passes_b,
+                 &S->alpha_bmin, &S->alpha_bmax};
+    verify_grouping(D, sub, st);
+    verify_grouping(D, bod, st);
 }
 
 #define INST(R)                                                                               \

@@ -26,10 +26,10 @@ __global__ void k_predict(Dev<R> D) {
 }
 
 template <class R>
-__global__ void k_trial(Dev<R> D, double beta) {
+__global__ void k_trial(Dev<R> D, int mode, double c) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * D.nv) return;
-    double a = beta > 0.0 ? beta : D.alpha[D.grp0[i / 3]];
+    double a = mode == 0 ? D.alpha[D.grp0[i / 3]] : (mode == 1 ? c * D.alpha_b[D.body[i / 3]] : c);
     D.xtry[i] = D.x[i] + a * (double)D.p[i];
 }
 
@@ -247,8 +247,8 @@ void launch_predict(const Dev<R>& D, cudaStream_t st) {
 }
 
 template <class R>
-void launch_trial_positions(const Dev<R>& D, double beta, cudaStream_t st) {
-    KL(k_trial<R><<<nblk(3LL * D.nv), kT, 0, st>>>(D, beta));
+void launch_trial_positions(const Dev<R>& D, int mode, double c, cudaStream_t st) {
+    KL(k_trial<R><<<nblk(3LL * D.nv), kT, 0, st>>>(D, mode, c));
 }
 
 template <class R>
@@ -271,7 +271,7 @@ void launch_zero_scalars(const Dev<R>& D, cudaStream_t st) {
 
 #define INST(R)                                                                                              \
     template void launch_predict<R>(const Dev<R>&, cudaStream_t);                                            \
-    template void launch_trial_positions<R>(const Dev<R>&, double, cudaStream_t);                            \
+    template void launch_trial_positions<R>(const Dev<R>&, int, double, cudaStream_t);                       \
     template void launch_energy_grad<R>(const Dev<R>&, const double*, const ContactBuf&, R*, double*,        \
                                         cudaStream_t);                                                       \
     template void launch_accept<R>(const Dev<R>&, cudaStream_t);                                             \

@@ -11,8 +11,9 @@ void scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st);
 
 // predictor x~ = x + h v + h^2 g_ext and x_start = x (Algorithm 1 input)
 template <class R> void launch_predict(const Dev<R>& D, cudaStream_t st);
-// x_try = x + (beta > 0 ? beta : alpha_{d(v)}) p
-template <class R> void launch_trial_positions(const Dev<R>& D, double beta, cudaStream_t st);
+// x_try = x + a_v p with a_v = alpha_{d(v)} (mode 0), c * alpha_{b(v)}
+// (mode 1, per body) or c (mode 2, uniform)
+template <class R> void launch_trial_positions(const Dev<R>& D, int mode, double c, cudaStream_t st);
 // E(x) and grad E(x) with the contact set C of x (Eq. 1); E accumulates into *E
 template <class R> void launch_energy_grad(const Dev<R>& D, const double* x, const ContactBuf& C, R* g,
                                            double* E, cudaStream_t st);

@@ -70,7 +70,7 @@ class Profile(C.Structure):
 STAGES = ["restart", "classify", "mas_blocks", "forms", "direction", "ccd", "trial_eval", "other"]
 
 Q_POSITIONS, Q_VELOCITIES, Q_N_VERTS, Q_N_CONTACTS, Q_SUBDOMAIN_ALPHA, Q_N_SUBDOMAINS, Q_TRACE_LEN, Q_TRACE, \
-    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG = range(11)
+    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG, Q_N_BODIES = range(12)
 
 _lib = None
 
@@ -87,7 +87,7 @@ EXPORTS = {
     "ipc_eval_contacts": (C.c_int, [C.c_void_p, _D, C.c_int, _I, _I, _I, _I, _D, _D, _D, C.c_void_p]),
     "ipc_eval_precond": (C.c_int, [C.c_void_p, _D, _D, _D, _D, C.c_void_p]),
     "ipc_eval_forms": (C.c_int, [C.c_void_p, _D, _D, _D, _D, _D, C.c_void_p]),
-    "ipc_eval_ccd": (C.c_int, [C.c_void_p, _D, _D, _D, _I, C.c_void_p]),
+    "ipc_eval_ccd": (C.c_int, [C.c_void_p, _D, _D, _D, _I, _D, _I, C.c_void_p]),
     "ipc_last_error": (C.c_char_p, []),
     "ipc_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ipc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
@@ -360,9 +360,19 @@ class Scene:
                                        _dp(out), _stream_handle(self.stream)))
         return out
 
-    def ccd(self, x, p):
+    def n_bodies(self):
+        return int(self._query_array(Q_N_BODIES, 1, np.int32)[0])
+
+    def ccd(self, x, p, per_body=False):
         x, p = _f64(x), _f64(p)
         a = np.zeros(self.n_subdomains())
         passes = C.c_int()
-        _check(self.lib.ipc_eval_ccd(self.h, _dp(x), _dp(p), _dp(a), C.byref(passes), _stream_handle(self.stream)))
-        return a, passes.value
+        if not per_body:
+            _check(self.lib.ipc_eval_ccd(self.h, _dp(x), _dp(p), _dp(a), C.byref(passes), None, None,
+                                         _stream_handle(self.stream)))
+            return a, passes.value
+        ab = np.zeros(self.n_bodies())
+        pb = C.c_int()
+        _check(self.lib.ipc_eval_ccd(self.h, _dp(x), _dp(p), _dp(a), C.byref(passes), _dp(ab), C.byref(pb),
+                                     _stream_handle(self.stream)))
+        return a, passes.value, ab, pb.value
