@@ -169,7 +169,7 @@ void o_restart(OScene* s, const double* x, const OContactList* C) {
         s->fac[l] = level_blocks(s, l);
         for (int g = 0; g < s->ngroups[l]; ++g) {
             int m = 3 * s->gsize[l][g];
-            if (o_chol(m, s->fac[l][g]) != 0) o_set_error("coarse block %d/%d not SPD", l, g);
+            if (o_chol(m, s->fac[l][g]) != 0) o_set_error("coarse block %d/%d: pivots floored", l, g);
         }
     }
     s->nupd = 0;
@@ -291,7 +291,7 @@ void o_apply_P(OScene* s, const double* g, double* z) {
                 for (int b = 0; b < m; ++b) A[a * m + b] += ud[a] * ud[b];
         }
         free(ud);
-        if (o_chol(m, A) != 0) o_set_error("level-0 block %d not SPD", gi);
+        if (o_chol(m, A) != 0) o_set_error("level-0 block %d: pivots floored", gi);
         double* rhs = (double*)calloc(m, sizeof(double));
         const int* mem = s->members[0] + (size_t)gi * S;
         for (int a = 0; a < cnt; ++a)

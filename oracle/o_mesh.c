@@ -31,11 +31,22 @@ const char* o_last_error(void) { return g_err; }
 
 /* ---------------------------------------------------------------- dense */
 
+/* Cholesky A = L L^T in place (lower).  Reading for numerically singular SPD
+ * blocks (stiff rank-1 contact terms): each pivot (Schur-complement diagonal)
+ * is floored at 1e-12 of the original diagonal entry, i.e. A plus a tiny
+ * non-negative diagonal shift is factorised.  Returns the number of floored
+ * pivots. */
 int o_chol(int n, double* A) {
+    int floored = 0;
     for (int j = 0; j < n; ++j) {
-        double s = A[j * n + j];
+        double a0 = A[j * n + j];
+        double s = a0;
         for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
-        if (!(s > 0.0)) return -1;
+        double fl = 1e-12 * a0;
+        if (!(s > fl)) {
+            s = fl > 0.0 ? fl : 1.0;
+            ++floored;
+        }
         double l = sqrt(s);
         A[j * n + j] = l;
         for (int i = j + 1; i < n; ++i) {
@@ -45,7 +56,7 @@ int o_chol(int n, double* A) {
         }
         for (int i = 0; i < j; ++i) A[i * n + j] = 0.0;
     }
-    return 0;
+    return floored;
 }
 
 void o_chol_solve(int n, const double* L, double* b) {

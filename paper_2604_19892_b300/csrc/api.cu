@@ -379,6 +379,45 @@ int read_view(ipc_scene* s, const Dev<R>& D, cudaStream_t st) {
     return 0;
 }
 
+template <class T>
+__global__ void k_count_nonfinite(const T* a, size_t n, unsigned long long* out) {
+    unsigned long long c = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double v = (double)a[i];
+        if (!(v == v) || v - v != 0.0) ++c;
+    }
+    if (c) atomicAdd(out, c);
+}
+
+// Describe where non-finite values sit (for the error message of a NaN stop).
+template <class R>
+std::string nonfinite_report(const Dev<R>& D, const Scalars& S, cudaStream_t st) {
+    unsigned long long* cnt = nullptr;
+    if (cudaMalloc(&cnt, 8 * sizeof(unsigned long long)) != cudaSuccess) return "";
+    cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), st);
+    size_t n3 = 3 * (size_t)D.nv;
+    size_t nb = (size_t)D.blk_off[D.nlev] * kBlk * kBlk;
+    KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.g, n3, cnt + 0));
+    KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.z, n3, cnt + 1));
+    KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.p, n3, cnt + 2));
+    KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.blocks, nb, cnt + 3));
+    KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.hess, (size_t)D.ntp * kH * kPack, cnt + 4));
+    KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.x, n3, cnt + 5));
+    KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.asmb, nb, cnt + 6));
+    unsigned long long h[8] = {0};
+    cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    cudaFree(cnt);
+    char buf[512];
+    snprintf(buf, sizeof buf,
+             " (non-finite: g %llu, z %llu, p %llu, blocks %llu, tet Hessians %llu, x %llu, assembled %llu; "
+             "gz %g zHz %g zHp %g pHp %g gp %g mu %g nu %g; first non-finite block %d with %d updates: "
+             "max|rhs| %g max|Y| %g max|lambda| %g max dS %g)",
+             h[0], h[1], h[2], h[3], h[4], h[5], h[6], S.gz, S.zHz, S.zHp, S.pHp, S.gp, S.mu, S.nu, S.dbg_block,
+             S.dbg_ns, S.dbg_rhs, S.dbg_y, S.dbg_lam, S.dbg_ds);
+    return buf;
+}
+
 template <class R>
 __global__ void k_velocity(Dev<R> D) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -395,6 +434,7 @@ template <class R>
 __global__ void k_reset_flags(Dev<R> D) {
     D.S->overflow = 0;
     D.S->nan_flag = 0;
+    D.S->dbg_block = -1;
 }
 
 // contacts, energy and gradient at D.x into C / g / E_k
@@ -479,7 +519,9 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         }
         if (int e = read_view(s, D, st)) return e;
         Scalars S = s->hv->S;
-        if (S.nan_flag || !(S.gz == S.gz)) return fail(IPC_ERR_NUMERIC, "NaN in the PNCG iteration");
+        if (S.nan_flag || !(S.gz == S.gz))
+            return fail(IPC_ERR_NUMERIC, "NaN in the PNCG iteration at iteration " + std::to_string(k) +
+                                             (restart ? " (restart)" : "") + nonfinite_report(D, S, st));
         if (S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
         if (S.ccd_passes < 0) ++fallbacks;
         rec.n_update = S.n_upd;

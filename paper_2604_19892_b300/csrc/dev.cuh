@@ -53,6 +53,10 @@ struct Scalars {
     int overflow;                  // bit flags: 1 contacts, 2 straddle, 4 upd
     int nan_flag;
     int nonpos;                    // a contact of the last detection has d <= 0
+    // first block apply with a non-finite result: block, updates used,
+    // max |rhs| (g and U columns), max |Y|, max |lambda|, max dS
+    int dbg_block, dbg_ns;
+    double dbg_rhs, dbg_y, dbg_lam, dbg_ds;
     double alpha_min, alpha_max;
     double beta;                   // uniform step of the current trial (0 = per-subdomain)
 };

@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(256) k_invert(Dev<R> D) {
     T* A = reinterpret_cast<T*>(smem_raw);
     T* rowk = A + kBlk * kBlk;
     T* colk = rowk + kBlk;
+    T* diag0 = colk + kBlk;  // original diagonal: pivot floor reference
     int b = blockIdx.x;
     int l = 0;
     while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
@@ -270,10 +271,18 @@ __global__ void __launch_bounds__(256) k_invert(Dev<R> D) {
         T v = (T)src[i];
         if (mem[r / 3] < 0 || mem[c / 3] < 0) v = (r == c) ? (T)1 : (T)0;
         A[i] = v;
+        if (r == c) diag0[r] = v;
     }
     __syncthreads();
     for (int k = 0; k < kBlk; ++k) {
+        // the pivot is the Schur-complement diagonal; a numerically singular
+        // SPD block (stiff rank-1 contact terms) is floored at 1e-12 of the
+        // original diagonal (1e-7 when the inverse is stored in FP32, whose
+        // range and precision cannot carry a larger condition number), i.e.
+        // A + a tiny non-negative shift is inverted
         T piv = A[k * kBlk + k];
+        T floor_k = (T)(sizeof(R) == 8 ? 1e-12 : 1e-7) * diag0[k];
+        if (!(piv > floor_k)) piv = floor_k > (T)0 ? floor_k : (T)1;
         T ip = (T)1 / piv;
         for (int j = threadIdx.x; j < kBlk; j += blockDim.x) {
             rowk[j] = (j == k) ? ip : A[k * kBlk + j] * ip;
@@ -570,11 +579,16 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
         __syncthreads();
         if (tid == 0) {
             // Cholesky solve of the SPD capacitance system
+            // C = I + U^T B U is >= I in exact arithmetic, so every pivot is
+            // >= 1; a pivot below 1/2 means B's rounding swamped a stiff
+            // update direction and the correction is dropped (z_d = B g_d)
             double L[kMaxK][kMaxK];
+            bool good = true;
             for (int j = 0; j < ns; ++j) {
                 double d = cap[j][j];
                 for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-                d = sqrt(fmax(d, 1e-300));
+                good = good && (d >= 0.5);
+                d = sqrt(fmax(d, 0.5));
                 L[j][j] = d;
                 for (int i = j + 1; i < ns; ++i) {
                     double t = cap[i][j];
@@ -593,6 +607,12 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
                 for (int k = i + 1; k < ns; ++k) t -= L[k][i] * lam[k];
                 lam[i] = t / L[i][i];
             }
+            // a non-finite capacitance solution (overflowing contact
+            // stiffness) drops this subdomain's correction: z_d = B g_d
+            bool ok = good;
+            for (int i = 0; i < ns; ++i) ok = ok && (lam[i] - lam[i] == 0.0);
+            if (!ok)
+                for (int i = 0; i < ns; ++i) lam[i] = 0.0;
         }
         __syncthreads();
         double o = (double)out;
@@ -604,6 +624,25 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
             z[3 * node + comp] = out;
         else
             D.coarse_y[D.coarse_off[l] + 3 * node + comp] = out;
+    }
+    // diagnostics: record the first block whose output is not finite
+    double od = (double)out;
+    if (!(od - od == 0.0) && atomicCAS(&D.S->dbg_block, -1, b) == -1) {
+        double rm = 0, ym = 0, lm = 0, dm = 0;
+        for (int a = 0; a <= ns; ++a)
+            for (int i = 0; i < kBlk; ++i) {
+                rm = fmax(rm, fabs((double)rhs[a][i]));
+                ym = fmax(ym, fabs((double)Y[a][i]));
+            }
+        for (int a = 0; a < ns; ++a) {
+            lm = fmax(lm, fabs(lam[a]));
+            dm = fmax(dm, D.upd_dS[sel[a]]);
+        }
+        D.S->dbg_ns = ns;
+        D.S->dbg_rhs = rm;
+        D.S->dbg_y = ym;
+        D.S->dbg_lam = lm;
+        D.S->dbg_ds = dm;
     }
 }
 
@@ -640,7 +679,7 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
     KL(k_assemble_mass<R><<<nblk(D.nv), kT, 0, st>>>(D));
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
     using T = double;  // blocks are assembled and inverted in FP64, stored in R
-    size_t smem = sizeof(T) * ((size_t)kBlk * kBlk + 2 * kBlk);
+    size_t smem = sizeof(T) * ((size_t)kBlk * kBlk + 3 * kBlk);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_invert<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -139,7 +139,7 @@ def default_params(bbox_diag, h, E_max):
     return {
         "h": h,
         "dhat": dhat,
-        "kappa": 100.0 * h * h * E_max * dhat,
+        "kappa": 10.0 * h * h * E_max * dhat,
         "tol": 1e-3,
         "iter_max": 10000,
         "delta": 0.3,
