@@ -79,9 +79,9 @@ def test_gradient_matches_finite_differences_with_contacts():
     g = o.gradient(x, xt)
     for _ in range(6):
         d = RNG.normal(size=x.shape)
-        eps = 1e-9
+        eps = 1e-8  # central differences settle to ~1e-6 relative here
         fd = (o.energy(x + eps * d, xt) - o.energy(x - eps * d, xt)) / (2 * eps)
-        assert np.sum(g * d) == pytest.approx(fd, rel=1e-7)
+        assert np.sum(g * d) == pytest.approx(fd, rel=1e-5)
     # per-coordinate on contact vertices (barrier gradient = kappa b'(d) grad d)
     verts = np.unique(C["verts"][C["verts"] >= 0])[:6]
     for vtx in verts:
