@@ -42,18 +42,31 @@ int o_chol(int n, double* A) {
         double a0 = A[j * n + j];
         double s = a0;
         for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        /* column j of the Schur complement, not yet divided by the pivot */
+        double th = 0.0;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = t;
+            /* for an SPD matrix the squared row norm of L equals the
+             * diagonal, so L_ij^2 <= A_ii; where rounding breaks that the
+             * pivot is raised until it holds (a diagonal shift, as in a
+             * modified Cholesky factorisation) */
+            double aii = A[i * n + i];
+            if (aii > 0.0 && t * t / aii > th) th = t * t / aii;
+        }
         double fl = 1e-12 * a0;
         if (!(s > fl)) {
             s = fl > 0.0 ? fl : 1.0;
             ++floored;
         }
+        if (s < th) {
+            s = th;
+            ++floored;
+        }
         double l = sqrt(s);
         A[j * n + j] = l;
-        for (int i = j + 1; i < n; ++i) {
-            double t = A[i * n + j];
-            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
-            A[i * n + j] = t / l;
-        }
+        for (int i = j + 1; i < n; ++i) A[i * n + j] /= l;
         for (int i = 0; i < j; ++i) A[i * n + j] = 0.0;
     }
     return floored;

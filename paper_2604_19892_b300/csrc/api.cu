@@ -278,7 +278,7 @@ int setup_dev(ipc_scene* s) {
     D.p = A.arr<R>(n3);
     D.hess = A.arr<R>((size_t)D.ntp * kH * kPack);
     D.blocks = A.arr<R>((size_t)nb * kBlk * kBlk);
-    D.asmb = A.arr<double>((size_t)nb * kBlk * kBlk);
+    D.asmb = A.arr<R>((size_t)nb * kBlk * kBlk);
     D.coarse_r = A.arr<R>(std::max(coff, 1));
     D.coarse_y = A.arr<R>(std::max(coff, 1));
     D.C = alloc_contacts(A, D.cap);
@@ -403,7 +403,7 @@ std::string nonfinite_report(const Dev<R>& D, const Scalars& S, cudaStream_t st)
     KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.blocks, nb, cnt + 3));
     KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.hess, (size_t)D.ntp * kH * kPack, cnt + 4));
     KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.x, n3, cnt + 5));
-    KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.asmb, nb, cnt + 6));
+    KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.asmb, nb, cnt + 6));
     unsigned long long h[8] = {0};
     cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);

@@ -110,7 +110,7 @@ struct Dev {
     R *g, *gtry, *z, *zprev, *p;
     R* hess;                               // [ntp][45][32]
     R* blocks;                             // nblocks * 96 * 96
-    double* asmb;                          // assembly buffer, same shape, double
+    R* asmb;                               // assembly buffer, same shape
     R* coarse_r;                           // restricted residuals, 3 * nnodes[l] per level, offsets coarse_off
     R* coarse_y;
     int coarse_off[kMaxLevels + 1];

@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __re
     R fro = 0;
     for (int i = 0; i < 9; ++i)
         for (int j = 0; j < 9; ++j) fro += A[i][j] * A[i][j];
-    const R tol = (sizeof(R) == 8 ? (R)1e-30 : (R)1e-14) * fro;
+    // stop when the off-diagonal norm is ~eps-relative (FP32: 3e-7, FP64: 1e-15)
+    const R tol = (sizeof(R) == 8 ? (R)1e-30 : (R)1e-13) * fro;
 #pragma unroll 1
     for (int sweep = 0; sweep < 20; ++sweep) {
         R off = 0;
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __re
 // ------------------------------------------------------ block assembly
 
 template <class R>
-__device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb, const double blk[3][3]) {
+__device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb, const R blk[3][3]) {
     int na, nb, ga, gb, sa, sb;
     if (l == 0) {
         ga = D.grp0[va];
@@ -161,11 +162,11 @@ __device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb
         sa = D.slot_of_node[l][na];
         sb = D.slot_of_node[l][nb];
     }
-    double* A = D.asmb + ((size_t)(D.blk_off[l] + ga)) * (kBlk * kBlk);
+    R* A = D.asmb + ((size_t)(D.blk_off[l] + ga)) * (kBlk * kBlk);
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) {
-            double v = blk[r][c];
-            if (v != 0.0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
+            R v = blk[r][c];
+            if (v != (R)0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
         }
 }
 
@@ -180,6 +181,9 @@ __device__ __forceinline__ bool one_node(const Dev<R>& D, int l, const int* v, i
     return true;
 }
 
+// 3x3 blocks K_ab = sum_{c,c'} Bf[a][c] Bf[b][c'] H[3c+r][3c'+s] of the tet's
+// 12x12 Hessian G^T H G, scattered into every level where the tet spans
+// more than one node
 template <class R>
 __global__ void k_assemble_tets(Dev<R> D) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,33 +192,37 @@ __global__ void k_assemble_tets(Dev<R> D) {
     int vid[4] = {q.x, q.y, q.z, q.w};
     R Bm[3][3];
     load_B(D, t, Bm);
-    double Bf[4][3];
+    R Bf[4][3];
     for (int c = 0; c < 3; ++c) {
-        Bf[0][c] = -((double)Bm[0][c] + (double)Bm[1][c] + (double)Bm[2][c]);
-        for (int j = 0; j < 3; ++j) Bf[j + 1][c] = (double)Bm[j][c];
+        Bf[0][c] = -(Bm[0][c] + Bm[1][c] + Bm[2][c]);
+        for (int j = 0; j < 3; ++j) Bf[j + 1][c] = Bm[j][c];
     }
     const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
-    double H[9][9];
+    R H[9][9];
     for (int i = 0; i < 9; ++i)
         for (int j = i; j < 9; ++j) {
-            double v = (double)hp[pk(i, j) * kPack];
+            R v = hp[pk(i, j) * kPack];
             H[i][j] = v;
             H[j][i] = v;
         }
+    unsigned levels = 0;
+    for (int l = 0; l < D.nlev; ++l)
+        if (!one_node(D, l, vid, 4)) levels |= 1u << l;
     for (int a = 0; a < 4; ++a)
         for (int b = 0; b < 4; ++b) {
-            double blk[3][3];
+            R blk[3][3];
             for (int r = 0; r < 3; ++r)
                 for (int s = 0; s < 3; ++s) {
-                    double acc = 0.0;
-                    for (int c = 0; c < 3; ++c)
-                        for (int c2 = 0; c2 < 3; ++c2) acc += Bf[a][c] * Bf[b][c2] * H[3 * c + r][3 * c2 + s];
+                    R acc = 0;
+                    for (int c = 0; c < 3; ++c) {
+                        R inner = 0;
+                        for (int c2 = 0; c2 < 3; ++c2) inner += Bf[b][c2] * H[3 * c + r][3 * c2 + s];
+                        acc += Bf[a][c] * inner;
+                    }
                     blk[r][s] = acc;
                 }
-            for (int l = 0; l < D.nlev; ++l) {
-                if (one_node(D, l, vid, 4)) continue;
-                add_block(D, l, vid[a], vid[b], blk);
-            }
+            for (int l = 0; l < D.nlev; ++l)
+                if (levels & (1u << l)) add_block(D, l, vid[a], vid[b], blk);
         }
 }
 
@@ -222,8 +230,8 @@ template <class R>
 __global__ void k_assemble_mass(Dev<R> D) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= D.nv) return;
-    double m = D.massd[v];
-    double blk[3][3] = {{m, 0, 0}, {0, m, 0}, {0, 0, m}};
+    R m = D.mass[v];
+    R blk[3][3] = {{m, 0, 0}, {0, m, 0}, {0, 0, m}};
     for (int l = 0; l < D.nlev; ++l) add_block(D, l, v, v, blk);
 }
 
@@ -239,9 +247,9 @@ __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
         double w[4] = {C.w[4 * i], C.w[4 * i + 1], C.w[4 * i + 2], C.w[4 * i + 3]};
         for (int a = 0; a < nvv; ++a)
             for (int b = 0; b < nvv; ++b) {
-                double blk[3][3];
+                R blk[3][3];
                 for (int rr = 0; rr < 3; ++rr)
-                    for (int s = 0; s < 3; ++s) blk[rr][s] = k * w[a] * w[b] * r[rr] * r[s];
+                    for (int s = 0; s < 3; ++s) blk[rr][s] = (R)(k * w[a] * w[b] * r[rr] * r[s]);
                 for (int l = 0; l < D.nlev; ++l) {
                     if (nvv == 4 && one_node(D, l, vid, 4)) continue;
                     add_block(D, l, vid[a], vid[b], blk);
@@ -252,56 +260,210 @@ __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
 
 // ------------------------------------------------------ batched inversion
 
-// One CTA per 96x96 block; Gauss-Jordan in shared memory in precision T.
-template <class R, class T>
-__global__ void __launch_bounds__(256) k_invert(Dev<R> D) {
+// Inverse of one SPD 96x96 subdomain block, B_d = M_d^{-1} (Sec. 4.2), one
+// CTA per block. The block is scaled to a unit diagonal, S = s A s with
+// s = diag(A)^{-1/2}; S = L L^T by right-looking Cholesky; W = L^{-1}; and
+// B = s W^T W s. Each pivot is floored at eps_piv of the unit diagonal (the
+// pivot relative to the original diagonal entry) and raised where needed to
+// keep every L_rk^2 <= 1: a numerically singular block (stiff rank-1 contact
+// terms) is replaced by A plus a small non-negative diagonal shift. Forming W^T W keeps the stored inverse
+// symmetric positive semi-definite whatever the rounding, so it remains a
+// valid preconditioner when R is FP32.
+//
+// Register tiling: the lower triangle is cut into 6x6 tiles (136 of them),
+// one per thread. Each elimination step broadcasts one column of L (or one
+// row of W) through shared memory; the broadcast vector is double-buffered
+// by step parity so a step needs a single barrier.
+constexpr int kTile = 6;
+constexpr int kNT = kBlk / kTile;                // 16 tiles per side
+constexpr int kNTiles = kNT * (kNT + 1) / 2;     // 136
+constexpr int kInvThreads = 160;
+static_assert(kNT * kTile == kBlk, "tile size must divide the block size");
+static_assert(kInvThreads >= kNTiles && kInvThreads % 32 == 0, "one thread per lower tile");
+
+template <class R>
+__global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
     extern __shared__ unsigned char smem_raw[];
-    T* A = reinterpret_cast<T*>(smem_raw);
-    T* rowk = A + kBlk * kBlk;
-    T* colk = rowk + kBlk;
-    T* diag0 = colk + kBlk;  // original diagonal: pivot floor reference
+    R* buf = reinterpret_cast<R*>(smem_raw);      // 96 x 96: L^T, then W
+    R* vec = buf + kBlk * kBlk;                   // 2 x 96 broadcast
+    R* sc = vec + 2 * kBlk;                       // diagonal scaling s
+    R* pm = sc + kBlk;                            // 2 x 16 column maxima of L_rk^2
+    const R eps_piv = (R)(sizeof(R) == 8 ? 1e-12 : 1e-6);
     int b = blockIdx.x;
     int l = 0;
     while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
     int grp = b - D.blk_off[l];
     const int* mem = D.members[l] + (size_t)grp * kSub;
-    const double* src = D.asmb + (size_t)b * kBlk * kBlk;
-    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
-        int r = i / kBlk, c = i % kBlk;
-        T v = (T)src[i];
-        if (mem[r / 3] < 0 || mem[c / 3] < 0) v = (r == c) ? (T)1 : (T)0;
-        A[i] = v;
-        if (r == c) diag0[r] = v;
+    const R* src = D.asmb + (size_t)b * kBlk * kBlk;
+    for (int r = threadIdx.x; r < kBlk; r += blockDim.x) {
+        R d = src[r * kBlk + r];
+        sc[r] = (mem[r / 3] < 0 || !(d > (R)0)) ? (R)1 : (R)1 / sqrt(d);
     }
-    __syncthreads();
-    for (int k = 0; k < kBlk; ++k) {
-        // the pivot is the Schur-complement diagonal; a numerically singular
-        // SPD block (stiff rank-1 contact terms) is floored at 1e-12 of the
-        // original diagonal (1e-7 when the inverse is stored in FP32, whose
-        // range and precision cannot carry a larger condition number), i.e.
-        // A + a tiny non-negative shift is inverted
-        T piv = A[k * kBlk + k];
-        T floor_k = (T)(sizeof(R) == 8 ? 1e-12 : 1e-7) * diag0[k];
-        if (!(piv > floor_k)) piv = floor_k > (T)0 ? floor_k : (T)1;
-        T ip = (T)1 / piv;
-        for (int j = threadIdx.x; j < kBlk; j += blockDim.x) {
-            rowk[j] = (j == k) ? ip : A[k * kBlk + j] * ip;
-            colk[j] = (j == k) ? (T)0 : A[j * kBlk + k];
+    // thread t owns tile (ti, tj), ti >= tj, t = ti (ti + 1) / 2 + tj
+    const int t = threadIdx.x;
+    const bool act = t < kNTiles;
+    int ti = 0, tj = 0;
+    if (act) {
+        int rem = t;
+        while (rem > ti) {
+            ++ti;
+            rem -= ti;
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
-            int r = i / kBlk, c = i % kBlk;
-            if (r == k) {
-                A[i] = rowk[c];
-            } else {
-                T a = (c == k) ? (T)0 : A[i];
-                A[i] = a - colk[r] * rowk[c];
+        tj = rem;
+    }
+    const int r0 = kTile * ti, c0 = kTile * tj;
+    __syncthreads();
+    R a[kTile][kTile];
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) {
+            int r = r0 + rr, c = c0 + cc;
+            R v = (R)0;
+            if (act) {
+                if (mem[r / 3] < 0 || mem[c / 3] < 0)
+                    v = (r == c) ? (R)1 : (R)0;
+                else
+                    v = src[r * kBlk + c] * sc[r] * sc[c];
+            }
+            a[rr][cc] = v;
+        }
+
+    // ---- S = L L^T (lower tiles in registers)
+    for (int kt = 0; kt < kNT; ++kt) {
+#pragma unroll
+        for (int kk = 0; kk < kTile; ++kk) {
+            const int k = kTile * kt + kk;
+            R* vb = vec + (k & 1) * kBlk;
+            if (act && tj == kt) {
+                R m = (R)0;
+#pragma unroll
+                for (int rr = 0; rr < kTile; ++rr) {
+                    R v = (ti == kt && rr < kk) ? (R)0 : a[rr][kk];
+                    vb[r0 + rr] = v;
+                    if ((ti > kt || rr > kk) && v * v > m) m = v * v;
+                }
+                pm[(k & 1) * kNT + ti] = m;
+            }
+            __syncthreads();
+            if (act && ti >= kt && tj >= kt) {
+                // pivot floor, then the row-norm bound L_rk^2 <= S_rr = 1 that
+                // holds for any SPD matrix: where rounding breaks it the pivot
+                // is raised (a diagonal shift, as in a modified Cholesky), so
+                // L stays bounded and no floored pivot can cascade
+                R piv = vb[k];
+                if (!(piv > eps_piv)) piv = eps_piv;
+                const R* pmk = pm + (k & 1) * kNT;
+                for (int q = kt; q < kNT; ++q) piv = pmk[q] > piv ? pmk[q] : piv;
+                const R sq = sqrt(piv);
+                const R ip = (R)1 / piv, isq = (R)1 / sq;
+                R vr[kTile], vc[kTile];
+#pragma unroll
+                for (int q = 0; q < kTile; ++q) {
+                    vr[q] = vb[r0 + q];
+                    vc[q] = vb[c0 + q] * ip;
+                }
+#pragma unroll
+                for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+                    for (int cc = 0; cc < kTile; ++cc) {
+                        if (tj == kt && cc < kk) continue;    // finished columns
+                        if (tj == kt && cc == kk) {
+                            // column k of L
+                            if (ti > kt || rr > kk) a[rr][cc] = vr[rr] * isq;
+                            else if (rr == kk) a[rr][cc] = sq;
+                        } else {
+                            a[rr][cc] -= vr[rr] * vc[cc];
+                        }
+                    }
             }
         }
-        __syncthreads();
+    }
+    // L^T -> shared memory (lower entries only; nothing reads above the diagonal)
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc)
+            if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
+    __syncthreads();
+
+    // ---- W = L^{-1}: row k of W is final once divided by L_kk; then every
+    // later row r subtracts L_rk times it
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (act && ti == tj && rr == cc) ? (R)1 : (R)0;
+    for (int kt = 0; kt < kNT; ++kt) {
+#pragma unroll
+        for (int kk = 0; kk < kTile; ++kk) {
+            const int k = kTile * kt + kk;
+            R* vb = vec + (k & 1) * kBlk;
+            const R* Lk = buf + k * kBlk;                 // column k of L
+            if (act && ti == kt) {
+                const R il = (R)1 / Lk[k];
+#pragma unroll
+                for (int cc = 0; cc < kTile; ++cc) {
+                    a[kk][cc] *= il;
+                    vb[c0 + cc] = a[kk][cc];
+                }
+            }
+            __syncthreads();
+            if (act && ti >= kt && tj <= kt) {
+                R lr[kTile], wc[kTile];
+#pragma unroll
+                for (int q = 0; q < kTile; ++q) {
+                    lr[q] = (ti > kt || q > kk) ? Lk[r0 + q] : (R)0;
+                    wc[q] = vb[c0 + q];
+                }
+#pragma unroll
+                for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+                    for (int cc = 0; cc < kTile; ++cc) a[rr][cc] -= lr[rr] * wc[cc];
+            }
+        }
+    }
+    __syncthreads();
+    // W -> shared memory, row-major; tiles above the diagonal are zero
+    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
+        int r = i / kBlk, c = i % kBlk;
+        if (r / kTile < c / kTile) buf[i] = (R)0;
+    }
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc)
+            if (act) buf[(r0 + rr) * kBlk + c0 + cc] = a[rr][cc];
+    __syncthreads();
+
+    // ---- B = s W^T W s; tile (ti, tj) needs rows k >= 6 ti of W only
+    if (!act) return;
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (R)0;
+    for (int k = r0; k < kBlk; ++k) {
+        const R* Wk = buf + k * kBlk;
+        R wr[kTile], wc[kTile];
+#pragma unroll
+        for (int q = 0; q < kTile; ++q) {
+            wr[q] = Wk[r0 + q];
+            wc[q] = Wk[c0 + q];
+        }
+#pragma unroll
+        for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < kTile; ++cc) a[rr][cc] += wr[rr] * wc[cc];
     }
     R* dst = D.blocks + (size_t)b * kBlk * kBlk;
-    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) dst[i] = (R)A[i];
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) {
+            int r = r0 + rr, c = c0 + cc;
+            R v = a[rr][cc] * sc[r] * sc[c];
+            dst[r * kBlk + c] = v;
+            dst[c * kBlk + r] = v;
+        }
 }
 
 // ------------------------------------------------------ C_base snapshot
@@ -462,16 +624,29 @@ __global__ void k_topk(Dev<R> D, ContactBuf C) {
 
 // ------------------------------------------------------ preconditioner apply
 
+// r_{l+1}[g] = sum of the level-l values over the members of level-l
+// subdomain g (C_{l+1} sums xyz per cluster): one warp per subdomain, lane =
+// slot, no atomics
 template <class R>
-__global__ void k_restrict(Dev<R> D, const R* __restrict__ g) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= D.nv) return;
-    R gx = g[3 * v], gy = g[3 * v + 1], gz = g[3 * v + 2];
-    for (int l = 1; l < D.nlev; ++l) {
-        R* r = D.coarse_r + D.coarse_off[l] + 3 * D.node_of_vert[l][v];
-        atomicAdd(r, gx);
-        atomicAdd(r + 1, gy);
-        atomicAdd(r + 2, gz);
+__global__ void k_restrict_level(Dev<R> D, int l, const R* __restrict__ src) {
+    int grp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (grp >= D.ngroups[l]) return;
+    int node = D.members[l][(size_t)grp * kSub + lane];
+    R a0 = 0, a1 = 0, a2 = 0;
+    if (node >= 0) {
+        a0 = src[3 * node];
+        a1 = src[3 * node + 1];
+        a2 = src[3 * node + 2];
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (lane == 0) {
+        R* dst = D.coarse_r + D.coarse_off[l + 1] + 3 * grp;
+        dst[0] = a0;
+        dst[1] = a1;
+        dst[2] = a2;
     }
 }
 
@@ -673,19 +848,21 @@ template <class R>
 void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
     int nb = D.blk_off[D.nlev];
     KL(k_clear_upd<R><<<1, 1, 0, st>>>(D));
-    cudaMemsetAsync(D.asmb, 0, sizeof(double) * (size_t)nb * kBlk * kBlk, st);
+    cudaMemsetAsync(D.asmb, 0, sizeof(R) * (size_t)nb * kBlk * kBlk, st);
     KL(k_tet_hessian<R><<<nblk(D.nt, 64), 64, 0, st>>>(D, x));
     KL(k_assemble_tets<R><<<nblk(D.nt), kT, 0, st>>>(D));
     KL(k_assemble_mass<R><<<nblk(D.nv), kT, 0, st>>>(D));
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
-    using T = double;  // blocks are assembled and inverted in FP64, stored in R
-    size_t smem = sizeof(T) * ((size_t)kBlk * kBlk + 3 * kBlk);
+    // blocks are assembled and inverted in the bulk precision R: FP64 in the
+    // plain mode; FP32 in the mixed mode (B300's FP64 rate would make the
+    // inversion the most expensive step; it is not among the FP64 steps)
+    size_t smem = sizeof(R) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_invert<R, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_invert<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    KL(k_invert<R, T><<<nb, 256, smem, st>>>(D));
+    KL(k_invert<R><<<nb, kInvThreads, smem, st>>>(D));
     cudaMemsetAsync(D.bkeys, 0xFF, sizeof(unsigned long long) * D.btab, st);
     KL(k_snapshot<R><<<592, kT, 0, st>>>(D));
 }
@@ -704,9 +881,9 @@ void launch_classify(const Dev<R>& D, const ContactBuf& C, cudaStream_t st) {
 
 template <class R>
 void launch_restrict(const Dev<R>& D, const R* g, cudaStream_t st) {
-    if (D.nlev > 1) {
-        cudaMemsetAsync(D.coarse_r, 0, sizeof(R) * D.coarse_off[D.nlev], st);
-        KL(k_restrict<R><<<nblk(D.nv), kT, 0, st>>>(D, g));
+    for (int l = 0; l + 1 < D.nlev; ++l) {
+        const R* src = l == 0 ? g : D.coarse_r + D.coarse_off[l];
+        KL(k_restrict_level<R><<<nblk(32LL * D.ngroups[l]), kT, 0, st>>>(D, l, src));
     }
 }
 

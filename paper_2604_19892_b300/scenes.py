@@ -321,6 +321,21 @@ def free_fall_block(n=2, edge_len=0.1, h=1.0 / 30):
     return sc
 
 
+def ground_drop(n=3, edge_len=0.1, gap=0.003, drop_speed=0.5, jitter=1e-4, seed=0, h=1.0 / 30):
+    """One jittered n^3-cell cube `gap` above the ground plane moving down at
+    `drop_speed`: plane contacts only, whose barrier is convex in x, so each
+    step's incremental potential has a single minimiser near rest."""
+    rng = np.random.default_rng(seed)
+    x, t = box_mesh(n, edge_len / n, (0.0, gap, 0.0))
+    sc = _assemble([(x, t, 1e5, 0.4, 1000.0)])
+    sc["x_rest"] += rng.uniform(-jitter, jitter, size=sc["x_rest"].shape)
+    sc["x0"] = sc["x_rest"].copy()
+    sc["v0"][:, 1] = -drop_speed
+    sc["params"] = default_params(bbox_diag(sc["x0"]), h, 1e5)
+    sc["name"] = f"ground_drop_{n}"
+    return sc
+
+
 def small_cubes(n=2, gap=0.01, jitter=1e-4, seed=0, h=1.0 / 30, edge_len=0.1, drop_speed=0.0):
     """Tiny two-cube scene for brute-force invariant checks."""
     sc = two_cubes(n=n, edge_len=edge_len, gap=gap, jitter=jitter, seed=seed, h=h)

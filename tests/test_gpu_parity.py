@@ -125,6 +125,25 @@ def test_preconditioner_parity(lib, name):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
+def test_preconditioner_fp32(lib, name):
+    """FP32 bulk mode: blocks assembled, inverted (scaled Cholesky, B = W^T W)
+    and applied in FP32. The result follows the FP64 oracle to FP32 rounding
+    times the block conditioning, and P stays positive definite: g.z > 0."""
+    sc = SCENES[name]
+    g, o = _pair(lib, sc, precision=1)
+    xb = contact_state(sc, 0.9)
+    xc = contact_state(sc, 0.4) + 1e-6 * RNG.normal(size=xb.shape)
+    for trial in range(3):
+        grad = RNG.normal(size=xb.shape)
+        for cur in (None, xc):
+            zg = g.precond_apply(xb, grad, cur)
+            zo = o.precond_apply(xb, grad, cur)
+            rel = np.linalg.norm(zg - zo) / np.linalg.norm(zo)
+            assert rel <= 1e-3, rel
+            assert float(np.sum(zg * grad)) > 0
+
+
+@pytest.mark.parametrize("name", list(SCENES))
 def test_forms_parity(lib, name):
     sc = SCENES[name]
     g, o = _pair(lib, sc)
@@ -165,23 +184,70 @@ def _step_pair(lib, sc, x, v, tol):
     return g, o, st, so, xo, vo
 
 
-def test_step_parity_at_the_minimiser(lib):
-    """Per timestep, GPU and oracle start from the same (x, v) and both solve
-    to tol 1e-8, so a rounding-level flip of a discrete decision (restart,
-    contact membership, CCD bisection) cannot move the answer: positions
-    agree within 1e-6 of the bounding-box diagonal, through the impact, and
-    the GPU state stays intersection-free."""
+def test_step_parity_unique_minimiser(lib):
+    """A cube dropped onto the ground plane: plane contacts only, so each
+    step's incremental potential has one minimiser. Per timestep GPU and
+    oracle start from the same (x, v), both converge at tol 1e-7, and their
+    positions agree within 1e-6 of the bounding-box diagonal through the
+    impact."""
     from paper_2604_19892_b300 import scenes as S
-    from tests.geometry import any_intersection
-    sc = S.small_cubes(n=3, gap=0.003, drop_speed=0.5)
+    sc = S.ground_drop(n=3, gap=0.003, drop_speed=0.5)
     x, v = sc["x0"].copy(), sc["v0"].copy()
     saw = 0
     for step in range(3):
-        g, o, st, so, xo, vo = _step_pair(lib, sc, x, v, 1e-8)
+        g, o, st, so, xo, vo = _step_pair(lib, sc, x, v, 1e-7)
+        assert st["converged"] == 1 and so["converged"] == 1, (step, st, so)
         xg, vg = g.positions(), g.velocities()
         err = np.abs(xg - xo).max() / o.bbox_diag()
         assert err <= 1e-6, (step, err, st, so)
-        sv, sf, se = o.surface()
+        assert st["n_contacts"] == so["n_contacts"]
+        saw += st["n_contacts"] > 0
+        x, v = xg, vg
+    assert saw > 0
+
+
+def _oracle_stationarity(o, sc, x, x_prev, v_prev):
+    """max_v |z_v| of the oracle's preconditioned gradient of the incremental
+    potential at x (predictor from x_prev, v_prev; P rebuilt at x)."""
+    p = sc["params"]
+    h = p["h"]
+    xt = x_prev + h * v_prev + h * h * np.asarray(sc["gravity"])[None, :]
+    grad = o.gradient(x, xt)
+    z = o.precond_apply(x, grad)
+    return np.linalg.norm(z, axis=1).max(), o.energy(x, xt)
+
+
+def test_step_reaches_a_stationary_point_of_the_oracle_potential(lib):
+    """Three stacked cubes landing face to face: the barrier between faces is
+    not convex, the step problem has several local minima, and which one a
+    solver reaches depends on rounding-level decisions (GPU atomics reorder
+    sums). What is unique is the definition of a solution, so per timestep
+    the GPU result is checked against the oracle's potential: the oracle's
+    preconditioned gradient at the GPU positions meets the convergence test
+    (max_v |z_v| <= tol h bbox, with a factor 10 for the oracle's fresh P and
+    rounding; the oracle's own result measures 0.5), the GPU's energy equals the oracle's energy there, and the
+    state is intersection-free."""
+    from paper_2604_19892_b300 import scenes as S
+    from tests.geometry import any_intersection
+    import oracle as O
+    sc = S.small_cubes(n=3, gap=0.003, drop_speed=0.5)
+    tol = 1e-7
+    o = O.Scene(sc, params={"tol": tol})
+    thr = tol * sc["params"]["h"] * o.bbox_diag()
+    x, v = sc["x0"].copy(), sc["v0"].copy()
+    z0, _ = _oracle_stationarity(o, sc, x, x, v)
+    assert z0 > 1e4 * thr          # the start is far from stationary
+    sv, sf, se = o.surface()
+    saw = 0
+    for step in range(3):
+        g = lib.Scene(sc, params={"tol": tol})
+        g.set_state(x, v)
+        st = g.step(1)
+        assert st["converged"] == 1, (step, st)
+        xg, vg = g.positions(), g.velocities()
+        zmax, E = _oracle_stationarity(o, sc, xg, x, v)
+        assert zmax <= 10 * thr, (step, zmax / thr, st)
+        assert st["energy"] == pytest.approx(E, rel=1e-10, abs=0)
         assert not any_intersection(xg, sf, se)
         saw += st["n_contacts"] > 0
         x, v = xg, vg
