@@ -241,6 +241,37 @@ int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr,
 int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha,
                  int* passes, double* alpha_body, int* passes_body, void* stream);
 
+/* ---- allocation-free preconditioner apply --------------------------------
+ * No counterpart in the paper: a library entry point for callers that must
+ * not allocate device memory during the call (a solver loop beside other
+ * busy streams, where cudaMalloc / cudaFree can synchronise the device; a
+ * process whose device memory belongs to another allocator).
+ *
+ * z = P_base g: the additive multilevel Schwarz preconditioner (Sec. 3.3)
+ * as the scene's last RebuildMAS left it (its last restart inside ipc_step,
+ * or the last ipc_eval_precond / ipc_eval_forms call), without the Woodbury
+ * patch, on caller-owned DEVICE arrays.
+ *  - g_dev, z_dev: 3 n_verts values each in the scene's bulk precision
+ *    (double for IPC_PREC_FP64, float for IPC_PREC_FP32), on the scene's
+ *    device, which must be current; they must not overlap.  z need not be
+ *    initialised.  The call only reads g and the scene and writes z.
+ *  - Work is enqueued on `stream` and the call returns without waiting.
+ *  - Scratch: the coarse residuals and solutions (levels >= 1) live in one
+ *    static 256 KiB device array per device (2 x align256(3 x coarse nodes x
+ *    sizeof(value)) bytes are used); nothing in it needs to start at zero.
+ *    Calls that overlap in time on one device race on that array: order
+ *    them on one stream or synchronise between them.
+ *  - The first call on each device resolves the array's address
+ *    (cudaGetSymbolAddress), which may load the library's device code on
+ *    that device; make that first call before any stream capture begins.
+ *  - Errors: IPC_ERR_INVALID for a null argument, host or foreign-device
+ *    arrays, overlapping g and z, or another device current;
+ *    IPC_ERR_CAPACITY when the coarse levels need more than the static
+ *    array (above roughly 1.7e5 vertices in FP64, twice that in FP32);
+ *    IPC_ERR_CUDA if a launch fails.  Only error paths allocate (host
+ *    memory for the message). */
+int ipc_precond_apply_noalloc(ipc_scene* s, const void* g_dev, void* z_dev, void* stream);
+
 const char* ipc_last_error(void);
 
 #ifdef __cplusplus

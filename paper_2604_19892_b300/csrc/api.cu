@@ -781,6 +781,74 @@ int eval_ccd_impl(ipc_scene* s, const double* x, const double* p, double* alpha,
     return IPC_OK;
 }
 
+// ---- allocation-free preconditioner apply (no counterpart in the paper)
+//
+// For callers that must not allocate device memory while they run: a solver
+// loop that shares the device with other busy streams, where cudaMalloc /
+// cudaFree can synchronise the whole device, and processes whose device
+// memory is owned by another allocator (a framework's caching pool), where
+// one more allocation can fail. The MAS apply (Sec. 3.3, additive over
+// levels) needs scratch only for the restricted residuals r_l and coarse
+// solutions y_l of levels l >= 1; here they live in one static device array
+// per device instead of the scene's arena. Nothing in it has to start at
+// zero: within a call every coarse residual and every coarse solution is
+// written before it is read. Calls that overlap in time on one device
+// (any scene, any stream) share this array and race.
+constexpr size_t kNoAllocScratchBytes = 256 * 1024;
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::atomic<void*> g_noalloc_addr[kNoAllocMaxDevices];
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+bool device_array_on(const void* p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
+template <class R>
+int precond_noalloc_impl(ipc_scene* s, const void* g_dev, void* z_dev, cudaStream_t st) {
+    const Dev<R>& D = dev_of<R>(s);
+    int dev = -1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (!device_array_on(D.blocks, dev))
+        return fail(IPC_ERR_INVALID, "ipc_precond_apply_noalloc: the current device is not the scene's device");
+    if (!device_array_on(g_dev, dev) || !device_array_on(z_dev, dev))
+        return fail(IPC_ERR_INVALID, "ipc_precond_apply_noalloc: g and z must be device arrays on the scene's device");
+    const size_t bytes = sizeof(R) * 3 * (size_t)D.nv;
+    const char* gb = static_cast<const char*>(g_dev);
+    const char* zb = static_cast<const char*>(z_dev);
+    if (gb < zb + bytes && zb < gb + bytes) return fail(IPC_ERR_INVALID, "ipc_precond_apply_noalloc: g and z overlap");
+    const size_t n_coarse = (size_t)D.coarse_off[D.nlev];
+    const size_t need = 2 * align256(sizeof(R) * n_coarse);
+    if (need > kNoAllocScratchBytes) {
+        char msg[256];
+        snprintf(msg, sizeof msg,
+                 "ipc_precond_apply_noalloc: the coarse levels need %zu bytes of scratch, above the %zu-byte "
+                 "static limit; use ipc_eval_precond",
+                 need, kNoAllocScratchBytes);
+        return fail(IPC_ERR_CAPACITY, msg);
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(IPC_ERR_INVALID, "ipc_precond_apply_noalloc: device ordinal above 63");
+    void* base = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!base) {
+        // first call on this device: resolve the array's address (the
+        // current device is the scene's, checked above)
+        CUDA_TRY(cudaGetSymbolAddress(&base, g_noalloc_scratch));
+        g_noalloc_addr[dev].store(base, std::memory_order_release);
+    }
+    Dev<R> E = D;
+    E.coarse_r = static_cast<R*>(base);
+    E.coarse_y = reinterpret_cast<R*>(static_cast<unsigned char*>(base) + align256(sizeof(R) * n_coarse));
+    launch_precond(E, static_cast<const R*>(g_dev), static_cast<R*>(z_dev), E.C, false, st);
+    CUDA_TRY(cudaGetLastError());
+    return IPC_OK;
+}
+
 ipc_scene* checked(ipc_scene* s) {
     if (!s) g_err = "null scene";
     return s;
@@ -1031,6 +1099,13 @@ int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr, con
     cudaStream_t st = (cudaStream_t)stream;
     return s->prec == IPC_PREC_FP64 ? eval_forms_impl<double>(s, x_base, x_curr, z, p, out, st)
                                     : eval_forms_impl<float>(s, x_base, x_curr, z, p, out, st);
+}
+
+int ipc_precond_apply_noalloc(ipc_scene* s, const void* g_dev, void* z_dev, void* stream) {
+    if (!checked(s) || !g_dev || !z_dev) return fail(IPC_ERR_INVALID, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? precond_noalloc_impl<double>(s, g_dev, z_dev, st)
+                                    : precond_noalloc_impl<float>(s, g_dev, z_dev, st);
 }
 
 int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha, int* passes, double* alpha_body,

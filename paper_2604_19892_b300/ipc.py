@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libipc_b300.so")
 
 IPC_OK = 0
 IPC_NOT_CONVERGED = 1
+IPC_ERR_INVALID = -1
+IPC_ERR_CAPACITY = -7
 IPC_PREC_FP64 = 0
 IPC_PREC_FP32 = 1
 
@@ -88,6 +90,7 @@ EXPORTS = {
     "ipc_eval_precond": (C.c_int, [C.c_void_p, _D, _D, _D, _D, C.c_void_p]),
     "ipc_eval_forms": (C.c_int, [C.c_void_p, _D, _D, _D, _D, _D, C.c_void_p]),
     "ipc_eval_ccd": (C.c_int, [C.c_void_p, _D, _D, _D, _I, _D, _I, C.c_void_p]),
+    "ipc_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ipc_last_error": (C.c_char_p, []),
     "ipc_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ipc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
@@ -351,6 +354,18 @@ class Scene:
         _check(self.lib.ipc_eval_precond(self.h, _dp(xb), _dp(xc) if xc is not None else None, _dp(g), _dp(z),
                                          _stream_handle(self.stream)))
         return z
+
+    def precond_apply_noalloc(self, g_dev, z_dev, stream=None):
+        """z = P_base g on device tensors of shape (nv, 3) in the scene's bulk
+        precision, through the allocation-free entry point; enqueued on the
+        stream, not waited for."""
+        import torch
+        want = torch.float64 if self.precision == IPC_PREC_FP64 else torch.float32
+        for t in (g_dev, z_dev):
+            if not (t.is_cuda and t.dtype == want and t.is_contiguous() and t.numel() == 3 * self.nv):
+                raise ValueError(f"expected a contiguous CUDA {want} tensor of {3 * self.nv} values")
+        _check(self.lib.ipc_precond_apply_noalloc(self.h, C.c_void_p(g_dev.data_ptr()), C.c_void_p(z_dev.data_ptr()),
+                                                  _stream_handle(stream or self.stream)))
 
     def hess_forms(self, x_base, z, p, x_curr=None):
         xb, z, p = _f64(x_base), _f64(z), _f64(p)

@@ -1,0 +1,71 @@
+"""Allocation-free preconditioner apply (ipc_precond_apply_noalloc) against
+the allocating evaluation entry point ipc_eval_precond: same scene, same
+P_base, two calls in a row on caller-owned device tensors. Named to be
+collected last, so it also runs after every other GPU test in one session."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_19892_b300 import build, ipc
+    build.build()
+    ipc.load()
+    return ipc
+
+
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-12), (1, 1e-6)])
+def test_noalloc_apply_matches_eval_precond(lib, precision, rtol):
+    import torch
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.two_cubes(n=8)                      # 1458 vertices, three levels
+    g = lib.Scene(sc, precision=precision)
+    assert len(g.levels()) >= 2                # the coarse scratch is used
+    rng = np.random.default_rng(11)
+    xb = sc["x0"] + 1e-4 * rng.normal(size=sc["x0"].shape)
+    dtype = torch.float64 if precision == 0 else torch.float32
+    for call in range(2):
+        grad = rng.normal(size=sc["x0"].shape)
+        z_ref = g.precond_apply(xb, grad)      # rebuilds P_base at xb, applies it
+        gd = torch.tensor(grad, dtype=dtype, device="cuda")
+        zd = torch.full_like(gd, float("nan"))  # every entry must be overwritten
+        g.precond_apply_noalloc(gd, zd)
+        torch.cuda.synchronize()
+        z = zd.double().cpu().numpy()
+        assert np.all(np.isfinite(z))
+        err = np.linalg.norm(z - z_ref) / np.linalg.norm(z_ref)
+        assert err <= rtol, (call, err)
+
+
+def test_noalloc_rejects_bad_arguments(lib):
+    import torch
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.two_cubes(n=3, gap=0.004)
+    g = lib.Scene(sc)
+    n3 = 3 * g.nv
+    gd = torch.zeros(n3, dtype=torch.float64, device="cuda")
+    zd = torch.zeros(n3, dtype=torch.float64, device="cuda")
+    host = np.zeros(n3)
+    L = lib.load()
+    import ctypes as C
+    code = L.ipc_precond_apply_noalloc(g.h, C.c_void_p(host.ctypes.data), C.c_void_p(zd.data_ptr()), None)
+    assert code == lib.IPC_ERR_INVALID and b"device arrays" in L.ipc_last_error()
+    code = L.ipc_precond_apply_noalloc(g.h, C.c_void_p(gd.data_ptr()), C.c_void_p(gd.data_ptr()), None)
+    assert code == lib.IPC_ERR_INVALID and b"overlap" in L.ipc_last_error()
+
+
+def test_noalloc_rejects_scenes_above_the_static_limit(lib):
+    import torch
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.free_fall_block(n=56)               # 185,193 vertices: 5,975 coarse nodes in FP64
+    g = lib.Scene(sc)
+    gd = torch.zeros(3 * g.nv, dtype=torch.float64, device="cuda")
+    zd = torch.zeros_like(gd)
+    with pytest.raises(lib.IPCError) as e:
+        g.precond_apply_noalloc(gd, zd)
+    assert e.value.code == lib.IPC_ERR_CAPACITY and "static limit" in str(e.value)
