@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-from-step", type=int, default=-1,
+                    help="call cudaProfilerStart before this timed step (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -227,6 +229,9 @@ def main():
     iters = 0
     status = []
     for k in range(args.steps):
+        if k == args.profile_from_step:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
         flush.fill_(float(k))
         ev0[k].record(stream)
         st = scene.step(1)
@@ -234,6 +239,8 @@ def main():
         iters += st["iters"]
         status.append(st)
     torch.cuda.synchronize()
+    if args.profile_from_step >= 0:
+        torch.cuda.profiler.stop()
     launches = ipc.kernel_launches() - launches0
     prof = scene.profile_read()
     scene.profile(False)

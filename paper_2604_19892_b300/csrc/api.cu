@@ -217,7 +217,7 @@ int setup_dev(ipc_scene* s) {
     D.coarse_off[m.nlev] = coff;
     D.cap = p.contact_capacity > 0 ? p.contact_capacity : std::max(4096, 16 * D.nsv + 16 * D.nse / 8);
     D.upd_cap = D.cap;
-    D.straddle_cap = 8 * (D.nsf + D.nse) + 4096;
+    D.straddle_cap = 32 * (D.nsf + D.nse) + 4096;  // 20 bytes per candidate
     D.h = p.h;
     D.dhat = p.dhat;
     D.kappa = p.kappa;

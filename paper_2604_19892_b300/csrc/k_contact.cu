@@ -490,6 +490,7 @@ template <class R>
 __global__ void k_ccd_begin(Dev<R> D) {
     Scalars* S = D.S;
     S->n_straddle = 0;
+    S->overflow &= ~2;
     S->ccd_viol = S->ccd_viol_b = 0;
     S->ccd_uniform = S->ccd_uniform_b = 0;
     S->ccd_passes = S->ccd_passes_b = 0;
@@ -541,13 +542,13 @@ __global__ void k_minmax(const double* a, int n, double* out_min, double* out_ma
 // pair's smallest alpha (the pair then moves uniformly on a segment already
 // checked)
 __global__ void k_verify_prep(Grouping G) {
-    if (*G.state == 2) return;
+    if (*G.state != 0) return;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.shrink[g] = G.alpha[g];
 }
 
 template <class R>
 __global__ void k_verify(Dev<R> D, Grouping G) {
-    if (*G.state == 2) return;  // finished
+    if (*G.state != 0) return;  // verified, or falling back to the uniform step
     int n = min(D.S->n_straddle, D.straddle_cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         int4 q = D.str_v[k];
@@ -565,14 +566,14 @@ __global__ void k_verify(Dev<R> D, Grouping G) {
 }
 
 __global__ void k_verify_apply(Grouping G) {
-    if (*G.state == 2 || !*G.viol) return;
+    if (*G.state != 0 || !*G.viol) return;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.alpha[g] = G.shrink[g];
 }
 
 // after pass `pass`: stop if clean; after the last pass with a violation
 // mark the uniform fallback
 __global__ void k_verify_flag(Grouping G, int pass, int last) {
-    if (*G.state == 2) return;
+    if (*G.state != 0) return;
     if (!*G.viol) {
         *G.state = 2;
         *G.passes = pass + 1;
@@ -591,9 +592,19 @@ __global__ void k_uniform(Grouping G) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.alpha[g] = a;
 }
 
+// a straddling-candidate list that overflowed cannot be verified: the
+// grouping takes the uniform step alpha_min, which needs no verification
+__global__ void k_verify_begin(Grouping G, const Scalars* S) {
+    if (S->overflow & 2) {
+        *G.state = 1;
+        *G.passes = -1;
+    }
+}
+
 template <class R>
 void verify_grouping(const Dev<R>& D, const Grouping& G, cudaStream_t st) {
     KL(k_minmax<<<1, 1024, 0, st>>>(G.alpha, G.n, G.amin, nullptr));
+    KL(k_verify_begin<<<1, 1, 0, st>>>(G, D.S));
     for (int pass = 0; pass < kCcdPasses; ++pass) {
         KL(k_verify_prep<<<nblk(G.n), kT, 0, st>>>(G));
         KL(k_verify<R><<<592, kT, 0, st>>>(D, G));
