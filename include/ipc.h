@@ -95,6 +95,12 @@ typedef struct ipc_params {
     int ls_max;              /* energy-check trials (20) */
     int precision;           /* ipc_precision */
     int contact_capacity;    /* initial contact buffer size, 0 = automatic */
+    int broad_phase;         /* 0 automatic: cached candidate-pair lists while
+                                valid, hashed grid otherwise; 1 hashed grid for
+                                every query; 2 cached lists for every query
+                                (built at the query's own positions where
+                                needed).  All three give the same contact and
+                                CCD candidate sets. */
 } ipc_params;
 
 /* Device allocator used for all scene memory; NULL functions = cudaMalloc. */

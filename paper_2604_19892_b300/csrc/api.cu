@@ -70,6 +70,18 @@ struct Arena {
     T* arr(size_t n) {
         return static_cast<T*>(get(n * sizeof(T)));
     }
+    void put(void* p) {
+        for (size_t i = 0; i < ptrs.size(); ++i)
+            if (ptrs[i] == p) {
+                if (fns.free)
+                    fns.free(p, fns.ctx);
+                else
+                    cudaFree(p);
+                ptrs[i] = ptrs.back();
+                ptrs.pop_back();
+                return;
+            }
+    }
     void release() {
         for (void* p : ptrs) {
             if (fns.free)
@@ -85,6 +97,7 @@ struct Arena {
 struct HostView {
     Scalars S;
     int nC, nCt;
+    int cand_n[2];
 };
 
 }  // namespace
@@ -136,6 +149,11 @@ struct ipc_scene {
     HostView* hv = nullptr;  // pinned
     std::vector<ipc_iter_record> trace;
     StageProf prof;
+    // cached candidate pairs: built with margin cand_delta; cand_bound bounds
+    // max_v |x_v - xref_v| of the current positions
+    bool cand_ok = false;
+    double cand_delta = 0.0;
+    double cand_bound = 0.0;
 };
 
 namespace {
@@ -318,6 +336,11 @@ int setup_dev(ipc_scene* s) {
     D.gtmp = A.arr<int>(std::max(D.nbuckets, m.ngroups[0]) / 1024 + 16);
     D.pbox = A.arr<double>(6 * (size_t)nprim);
     D.cellsz = A.arr<double>(1);
+    D.cand_cap = 48 * (D.nsv + D.nse) + 4096;
+    D.xref = A.arr<double>(3 * (size_t)m.nv);
+    D.cand_pt = A.arr<int2>(D.cand_cap);
+    D.cand_ee = A.arr<int2>(D.cand_cap);
+    D.cand_n = A.arr<int>(2);
     D.S = A.arr<Scalars>(1);
     if (!A.ok) return fail(IPC_ERR_OOM, "scene: device allocation failed");
 
@@ -439,17 +462,88 @@ __global__ void k_reset_flags(Dev<R> D) {
 
 // contacts, energy and gradient at D.x into C / g / E_k
 template <class R>
-void eval_current(const Dev<R>& D, cudaStream_t st) {
-    launch_detect(D, D.x, D.C, st);
+void eval_current(const Dev<R>& D, cudaStream_t st, bool list = false) {
+    if (list)
+        launch_detect_list(D, D.x, D.C, st);
+    else
+        launch_detect(D, D.x, D.C, st);
     launch_energy_grad(D, D.x, D.C, D.g, &D.S->E_k, st);
 }
 
 template <class R>
-void eval_trial(const Dev<R>& D, int mode, double c, cudaStream_t st) {
+void eval_trial(const Dev<R>& D, int mode, double c, cudaStream_t st, bool list = false) {
     launch_trial_positions(D, mode, c, st);
-    launch_detect(D, D.xtry, D.Ct, st);
+    if (list)
+        launch_detect_list(D, D.xtry, D.Ct, st);
+    else
+        launch_detect(D, D.xtry, D.Ct, st);
     launch_energy_grad(D, D.xtry, D.Ct, D.gtry, &D.S->E_try, st);
     launch_accept(D, st);
+}
+
+// Builds the candidate lists at x with margin delta; grows them (up to
+// max_pairs entries each) when they overflow. Returns 1 when the lists hold
+// every candidate, 0 when they would need more than max_pairs, < 0 on error.
+template <class R>
+int build_lists(ipc_scene* s, Dev<R>& D, const double* x, double delta, long long max_pairs, cudaStream_t st) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        launch_cand_build(D, x, delta, st);
+        CUDA_TRY(cudaMemcpyAsync(s->hv->cand_n, D.cand_n, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        long long need = std::max(s->hv->cand_n[0], s->hv->cand_n[1]);
+        if (need <= D.cand_cap) return 1;
+        if (need > max_pairs || attempt == 1) return 0;
+        long long cap = std::min(max_pairs, need + need / 4 + 4096);
+        int2* a = s->arena.arr<int2>(cap);
+        int2* b = s->arena.arr<int2>(cap);
+        if (!a || !b) {
+            if (a) s->arena.put(a);
+            if (b) s->arena.put(b);
+            s->arena.ok = true;
+            return 0;
+        }
+        s->arena.put(D.cand_pt);
+        s->arena.put(D.cand_ee);
+        D.cand_pt = a;
+        D.cand_ee = b;
+        D.cand_cap = (int)cap;
+    }
+    return 0;
+}
+
+// Broad phase of this iteration. The cached candidate lists serve while
+// every position of the CCD segment stays within cand_delta of the build
+// positions: max_v |x_v - xref_v| + max_v |p_v| <= delta. Otherwise they
+// are rebuilt here at x_k with delta = max(2 dhat, 2 max|p|) when the
+// direction is short (max|p| <= 2 dhat); long directions (the first
+// iterations of a timestep) use the per-call hashed grid.
+template <class R>
+int choose_broad_phase(ipc_scene* s, Dev<R>& D, cudaStream_t st, bool* use_list, double* bound_after) {
+    CUDA_TRY(cudaMemcpyAsync(&s->hv->S.pmax, &D.S->pmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    const double pm = s->hv->S.pmax, md = s->hv->S.maxdisp;
+    const int mode = s->prm.broad_phase;
+    *use_list = false;
+    *bound_after = INFINITY;
+    if (mode == 1) return IPC_OK;
+    if (s->cand_ok && md + pm <= s->cand_delta) {
+        *use_list = true;
+        *bound_after = md + pm;
+        return IPC_OK;
+    }
+    if (pm <= 2.0 * D.dhat || mode == 2) {
+        const double delta = std::max(2.0 * D.dhat, 2.0 * pm);
+        const long long lim = mode == 2 ? (1LL << 30) : 256LL * (D.nsv + D.nse) + 4096;
+        int r = build_lists(s, D, D.x, delta, lim, st);
+        if (r < 0) return r;
+        s->cand_ok = r == 1;
+        if (s->cand_ok) {
+            s->cand_delta = delta;
+            *use_list = true;
+            *bound_after = pm;
+        }
+    }
+    return IPC_OK;
 }
 
 // Algorithm 1 for one timestep.
@@ -464,7 +558,7 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         launch_predict(D, st);
         CUDA_TRY(cudaMemsetAsync(D.zprev, 0, sizeof(R) * n3, st));
         CUDA_TRY(cudaMemsetAsync(D.p, 0, sizeof(R) * n3, st));
-        eval_current(D, st);
+        eval_current(D, st, s->prm.broad_phase != 1 && s->cand_ok && s->cand_bound <= s->cand_delta);
     }
     if (int e = read_view(s, D, st)) return e;
     if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
@@ -509,13 +603,19 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
             Stage t(s, 4, st);
             launch_direction(D, restart, st);
         }
+        bool use_list = false;
+        double bound_after = INFINITY;
         {
             Stage t(s, 5, st);
-            launch_ccd(D, st);
+            if (int e = choose_broad_phase(s, D, st, &use_list, &bound_after)) return e;
+            if (use_list)
+                launch_ccd_list(D, st);
+            else
+                launch_ccd(D, st);
         }
         {
             Stage t(s, 6, st);
-            eval_trial(D, 0, 0.0, st);
+            eval_trial(D, 0, 0.0, st, use_list);
         }
         if (int e = read_view(s, D, st)) return e;
         Scalars S = s->hv->S;
@@ -545,9 +645,10 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
                 {
                     Stage t(s, 6, st);
                     if (body_tier && ls <= 4)
-                        eval_trial(D, 1, std::ldexp(1.0, -(ls - 1)), st);
+                        eval_trial(D, 1, std::ldexp(1.0, -(ls - 1)), st, use_list);
                     else
-                        eval_trial(D, 2, std::ldexp(S.alpha_min, -(j0 + ls - 1 - (body_tier ? 4 : 0))), st);
+                        eval_trial(D, 2, std::ldexp(S.alpha_min, -(j0 + ls - 1 - (body_tier ? 4 : 0))), st,
+                                   use_list);
                 }
                 if (int e = read_view(s, D, st)) return e;
                 if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
@@ -560,6 +661,11 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         }
         rec.ls_halvings = halv;
         halvings += halv;
+        // bound on max_v |x_v - xref_v| for the next iteration or timestep
+        if (use_list)
+            s->cand_bound = accepted ? bound_after : bound_after - s->hv->S.pmax;
+        else
+            s->cand_bound = INFINITY;
         if (accepted) {
             std::swap(D.x, D.xtry);
             std::swap(D.C, D.Ct);
@@ -655,7 +761,16 @@ int eval_contacts_impl(ipc_scene* s, const double* x, int cap, int* n, int* type
     size_t n3 = 3 * (size_t)D.nv;
     CUDA_TRY(cudaMemcpyAsync(D.xtry, x, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
     KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
-    launch_detect(D, D.xtry, D.Ct, st);
+    if (s->prm.broad_phase == 2) {
+        // candidate lists built at x itself (margin 2 dhat)
+        s->cand_ok = false;
+        int r = build_lists(s, D, D.xtry, 2.0 * D.dhat, 1LL << 30, st);
+        if (r < 0) return r;
+        if (r == 0) return fail(IPC_ERR_CAPACITY, "candidate list overflow");
+        launch_detect_list(D, D.xtry, D.Ct, st);
+    } else {
+        launch_detect(D, D.xtry, D.Ct, st);
+    }
     if (int e = read_view(s, D, st)) return e;
     if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
     int nc = std::min(s->hv->nCt, D.cap);
@@ -771,7 +886,19 @@ int eval_ccd_impl(ipc_scene* s, const double* x, const double* p, double* alpha,
     }
     KL(k_set_scalar_double<R><<<1, 1, 0, st>>>(&D.S->pmax, pm));
     KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
-    launch_ccd(E, st);
+    if (s->prm.broad_phase == 2) {
+        // candidate lists built at x with a margin covering the segment
+        s->cand_ok = false;
+        int r = build_lists(s, D, D.xtry, std::max(2.0 * D.dhat, 2.0 * pm), 1LL << 30, st);
+        if (r < 0) return r;
+        if (r == 0) return fail(IPC_ERR_CAPACITY, "candidate list overflow");
+        E.cand_pt = D.cand_pt;
+        E.cand_ee = D.cand_ee;
+        E.cand_cap = D.cand_cap;
+        launch_ccd_list(E, st);
+    } else {
+        launch_ccd(E, st);
+    }
     if (int e = read_view(s, D, st)) return e;
     int ng = D.ngroups[0];
     CUDA_TRY(cudaMemcpy(alpha, D.alpha, sizeof(double) * ng, cudaMemcpyDeviceToHost));
@@ -875,6 +1002,7 @@ void ipc_default_params(ipc_params* p) {
     p->ls_max = 20;
     p->precision = IPC_PREC_FP64;
     p->contact_capacity = 0;
+    p->broad_phase = 0;
 }
 
 const char* ipc_last_error(void) { return g_err.c_str(); }
@@ -884,7 +1012,8 @@ int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params, const
     *out = nullptr;
     if (!(params->h > 0) || !(params->dhat > 0) || !(params->kappa > 0) || params->K < 0 || params->K > kMaxK ||
         params->iter_max <= 0 || params->levels_max < 1 || params->ls_max < 0 ||
-        (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_FP32))
+        (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_FP32) || params->broad_phase < 0 ||
+        params->broad_phase > 2)
         return fail(IPC_ERR_INVALID, "invalid parameters");
     ipc_scene* s = new ipc_scene();
     s->prm = *params;
@@ -948,6 +1077,7 @@ int ipc_set_state(ipc_scene* s, const double* x, const double* v, int on_device,
     double* dv = s->prec == IPC_PREC_FP64 ? s->dd.v : s->df.v;
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CUDA_TRY(cudaMemcpyAsync(dx, x, sizeof(double) * n3, kind, st));
+    s->cand_ok = false;
     if (v)
         CUDA_TRY(cudaMemcpyAsync(dv, v, sizeof(double) * n3, kind, st));
     else

@@ -37,6 +37,7 @@ struct Scalars {
     double zHz, zHp, pHp;          // quadratic forms of H~ (Eq. 13-15)
     double znorm;                  // max_v |z_v| (as double bits, atomicMax)
     double pmax;                   // max_v |p_v|
+    double maxdisp;                // max_v |x_v - xref_v|
     double mu, nu;
     // energies
     double E_k, E_try;
@@ -151,6 +152,14 @@ struct Dev {
     int* gtmp;                             // scan temporaries
     double* pbox;                          // per stored primitive: lo(3) hi(3)
     double* cellsz;                        // scalar: cell size of the current build
+    // cached candidate pairs (built at xref with margin delta): every PT / EE
+    // pair whose query box at xref overlaps the stored box inflated by
+    // dhat + 2 delta; valid while every vertex stays within delta of xref
+    double* xref;                          // 3 nv
+    int2* cand_pt;                         // (surface vertex id, surface tri)
+    int2* cand_ee;                         // (edge i, edge j), i < j
+    int* cand_n;                           // device: [0] PT count, [1] EE count
+    int cand_cap;                          // capacity of each list
     // scalars
     Scalars* S;
 };

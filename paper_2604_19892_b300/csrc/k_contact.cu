@@ -480,6 +480,156 @@ __global__ void k_ccd_pg(Dev<R> D) {
     }
 }
 
+// ------------------------------------------------------ cached candidates
+//
+// Built at xref with margin delta: the stored boxes are inflated by
+// infl = dhat + 2 delta, the query boxes are plain, so for positions y with
+// max_v |y_v - xref_v| <= delta the list holds every pair with d(y) < dhat
+// (proximity) and every pair whose swept boxes over a segment inside that
+// ball overlap (CCD). The per-iteration kernels then apply the exact tests of
+// the grid path to the listed pairs, giving the same contact and CCD
+// candidate sets.
+
+// append one int2 per calling thread with one atomic per warp
+__device__ __forceinline__ void append_pair(int2* list, int* count, int cap, int a, int b) {
+    unsigned m = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int rank = __popc(m & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    int k = base + rank;
+    if (k < cap) list[k] = make_int2(a, b);
+}
+
+template <class R>
+__global__ void k_cand_pt(Dev<R> D, const double* __restrict__ x) {
+    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= D.nsv) return;
+    int pv = D.sv[qi];
+    double px = x[3 * pv], py = x[3 * pv + 1], pz = x[3 * pv + 2];
+    double inv = 1.0 / *D.cellsz;
+    unsigned long long cc = pack_cell(cellc(px, inv), cellc(py, inv), cellc(pz, inv));
+    int bk = bucket_of(cc, D.nbuckets);
+    for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+        if (D.gcell[e] != cc) continue;
+        int f = D.gentry[e];
+        const double* b = D.pbox + 6 * (size_t)f;
+        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
+        if (pv == D.sf[3 * f] || pv == D.sf[3 * f + 1] || pv == D.sf[3 * f + 2]) continue;
+        append_pair(D.cand_pt, &D.cand_n[0], D.cand_cap, pv, f);
+    }
+    int nl = *D.gnlarge;
+    for (int k = 0; k < nl; ++k) {
+        int f = D.glarge[k];
+        const double* b = D.pbox + 6 * (size_t)f;
+        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
+        if (pv == D.sf[3 * f] || pv == D.sf[3 * f + 1] || pv == D.sf[3 * f + 2]) continue;
+        append_pair(D.cand_pt, &D.cand_n[0], D.cand_cap, pv, f);
+    }
+}
+
+template <class R>
+__device__ __forceinline__ bool edges_adjacent(const Dev<R>& D, int i, int j) {
+    int a0 = D.se[2 * i], a1 = D.se[2 * i + 1], b0 = D.se[2 * j], b1 = D.se[2 * j + 1];
+    return a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1;
+}
+
+template <class R>
+__global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.nse) return;
+    int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+    double lo[3], hi[3];
+    prim_box<R>(x, nullptr, vid, 2, 0.0, lo, hi);
+    double inv = 1.0 / *D.cellsz;
+    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
+    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
+    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
+    if (!(nc > 0)) nc = kMaxCells + 1;
+    if (nc > kMaxCells) {
+        for (int j = i + 1; j < D.nse; ++j) {
+            const double* b = D.pbox + 6 * (size_t)j;
+            if (overlap(lo, hi, b, b + 3) && !edges_adjacent(D, i, j))
+                append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
+        }
+        return;
+    }
+    for (int a = i0; a <= i1; ++a)
+        for (int bb = j0; bb <= j1; ++bb)
+            for (int c = k0; c <= k1; ++c) {
+                unsigned long long cc = pack_cell(a, bb, c);
+                int bk = bucket_of(cc, D.nbuckets);
+                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                    if (D.gcell[e] != cc) continue;
+                    int j = D.gentry[e];
+                    if (j <= i) continue;
+                    const double* b = D.pbox + 6 * (size_t)j;
+                    if (!overlap(lo, hi, b, b + 3)) continue;
+                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
+                        cellc(fmax(lo[2], b[2]), inv) != c)
+                        continue;
+                    if (edges_adjacent(D, i, j)) continue;
+                    append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
+                }
+            }
+    int nl = *D.gnlarge;
+    for (int k = 0; k < nl; ++k) {
+        int j = D.glarge[k];
+        if (j <= i) continue;
+        const double* b = D.pbox + 6 * (size_t)j;
+        if (overlap(lo, hi, b, b + 3) && !edges_adjacent(D, i, j)) append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
+    }
+}
+
+template <class R>
+__global__ void k_set_cell_cand(Dev<R> D, double infl) { *D.cellsz = fmax(D.cell, 2.0 * infl); }
+
+template <class R>
+__global__ void k_prox_pt_list(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
+    int n = min(D.cand_n[0], D.cand_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int2 q = D.cand_pt[k];
+        pt_try(D, x, C, q.x, q.y);
+    }
+}
+
+template <class R>
+__global__ void k_prox_ee_list(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
+    int n = min(D.cand_n[1], D.cand_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int2 q = D.cand_ee[k];
+        ee_try(D, x, C, q.x, q.y);
+    }
+}
+
+template <class R>
+__global__ void k_ccd_pt_list(Dev<R> D) {
+    int n = min(D.cand_n[0], D.cand_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int2 q = D.cand_pt[k];
+        int v[4] = {q.x, D.sf[3 * q.y], D.sf[3 * q.y + 1], D.sf[3 * q.y + 2]};
+        double lo[3], hi[3], tlo[3], thi[3];
+        prim_box(D.x, D.p, v, 1, 0.0, lo, hi);
+        prim_box(D.x, D.p, v + 1, 3, 0.0, tlo, thi);
+        if (overlap(lo, hi, tlo, thi)) ccd_pair(D, 0, v);
+    }
+}
+
+template <class R>
+__global__ void k_ccd_ee_list(Dev<R> D) {
+    int n = min(D.cand_n[1], D.cand_cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int2 q = D.cand_ee[k];
+        int v[4] = {D.se[2 * q.x], D.se[2 * q.x + 1], D.se[2 * q.y], D.se[2 * q.y + 1]};
+        double lo[3], hi[3], blo[3], bhi[3];
+        prim_box(D.x, D.p, v, 2, 0.0, lo, hi);
+        prim_box(D.x, D.p, v + 2, 2, 0.0, blo, bhi);
+        if (overlap(lo, hi, blo, bhi)) ccd_pair(D, 1, v);
+    }
+}
+
 template <class R>
 __global__ void k_fill(Dev<R> D, double* a, int n, double v) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -649,9 +799,60 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     verify_grouping(D, bod, st);
 }
 
+template <class R>
+void launch_cand_build(const Dev<R>& D, const double* x, double delta, cudaStream_t st) {
+    const double infl = D.dhat + 2.001 * delta;
+    cudaMemsetAsync(D.cand_n, 0, 2 * sizeof(int), st);
+    int* gin = D.gin;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int* prims = pass == 0 ? D.sf : D.se;
+        int nper = pass == 0 ? 3 : 2, nprim = pass == 0 ? D.nsf : D.nse;
+        cudaMemsetAsync(D.gcount, 0, sizeof(int) * (D.nbuckets + 1), st);
+        cudaMemsetAsync(D.gfill, 0, sizeof(int) * D.nbuckets, st);
+        cudaMemsetAsync(D.gtotal, 0, sizeof(int), st);
+        cudaMemsetAsync(D.gnlarge, 0, sizeof(int), st);
+        KL(k_set_cell_cand<R><<<1, 1, 0, st>>>(D, infl));
+        if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, x, (const R*)nullptr, infl, gin));
+        scan_exclusive(D.gcount, D.gstart, D.nbuckets, D.gtmp, st);
+        if (nprim > 0) KL(k_grid_fill<R><<<nblk(nprim), kT, 0, st>>>(D, nprim, gin));
+        if (pass == 0 && D.nsv) KL(k_cand_pt<R><<<nblk(D.nsv), kT, 0, st>>>(D, x));
+        if (pass == 1 && D.nse) KL(k_cand_ee<R><<<nblk(D.nse), kT, 0, st>>>(D, x));
+    }
+    cudaMemcpyAsync(D.xref, x, sizeof(double) * 3 * (size_t)D.nv, cudaMemcpyDeviceToDevice, st);
+}
+
+template <class R>
+void launch_detect_list(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
+    KL(k_reset_detect<R><<<1, 1, 0, st>>>(D, C));
+    KL(k_prox_pt_list<R><<<1184, kT, 0, st>>>(D, x, C));
+    KL(k_prox_ee_list<R><<<1184, kT, 0, st>>>(D, x, C));
+    if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
+}
+
+template <class R>
+void launch_ccd_list(const Dev<R>& D, cudaStream_t st) {
+    int ng = D.ngroups[0];
+    KL(k_ccd_begin<R><<<1, 1, 0, st>>>(D));
+    KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
+    KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
+    KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D));
+    KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D));
+    if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
+    Scalars* S = D.S;
+    Grouping sub{D.grp0, D.alpha, D.shrink, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes, &S->alpha_min,
+                 &S->alpha_max};
+    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b, &S->ccd_passes_b,
+                 &S->alpha_bmin, &S->alpha_bmax};
+    verify_grouping(D, sub, st);
+    verify_grouping(D, bod, st);
+}
+
 #define INST(R)                                                                               \
     template void launch_detect<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t); \
-    template void launch_ccd<R>(const Dev<R>&, cudaStream_t);
+    template void launch_ccd<R>(const Dev<R>&, cudaStream_t);                                  \
+    template void launch_cand_build<R>(const Dev<R>&, const double*, double, cudaStream_t);    \
+    template void launch_detect_list<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t); \
+    template void launch_ccd_list<R>(const Dev<R>&, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

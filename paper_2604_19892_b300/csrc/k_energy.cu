@@ -170,6 +170,7 @@ __global__ void k_zero_scalars(Dev<R> D) {
     S->zHz = S->zHp = S->pHp = 0.0;
     S->znorm = 0.0;
     S->pmax = 0.0;
+    S->maxdisp = 0.0;
 }
 
 // ---- scan: block sums, scan of sums, block scan + offset

@@ -190,7 +190,7 @@ __global__ void k_solve2x2(Dev<R> D, int restart) {
 template <class R>
 __global__ void k_direction(Dev<R> D, int restart) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
-    double pm = 0.0;
+    double pm = 0.0, dm = 0.0;
     if (v < D.nv) {
         double mu = D.S->mu, nu = D.S->nu;
         double s = 0.0;
@@ -201,9 +201,20 @@ __global__ void k_direction(Dev<R> D, int restart) {
             s += pn * pn;
         }
         pm = sqrt(s);
+        // drift from the positions the candidate lists were built at
+        if (D.xref) {
+            double q = 0.0;
+            for (int r = 0; r < 3; ++r) {
+                double e = D.x[3 * v + r] - D.xref[3 * v + r];
+                q += e * e;
+            }
+            dm = sqrt(q);
+        }
     }
     pm = warp_max(pm);
+    dm = warp_max(dm);
     if ((threadIdx.x & 31) == 0 && pm > 0.0) atomicMaxPos(&D.S->pmax, pm);
+    if ((threadIdx.x & 31) == 0 && dm > 0.0) atomicMaxPos(&D.S->maxdisp, dm);
 }
 
 }  // namespace

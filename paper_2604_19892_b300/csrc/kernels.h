@@ -39,6 +39,12 @@ template <class R> void launch_forms(const Dev<R>& D, const ContactBuf& C, bool 
 template <class R> void launch_direction(const Dev<R>& D, bool restart, cudaStream_t st);
 // per-subdomain step sizes for p at x with verification (supplement Sec. 3)
 template <class R> void launch_ccd(const Dev<R>& D, cudaStream_t st);
+// cached candidate pairs: build at x with margin delta; proximity and CCD
+// over the listed pairs (same results as launch_detect / launch_ccd while
+// every vertex stays within delta of the build positions)
+template <class R> void launch_cand_build(const Dev<R>& D, const double* x, double delta, cudaStream_t st);
+template <class R> void launch_detect_list(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st);
+template <class R> void launch_ccd_list(const Dev<R>& D, cudaStream_t st);
 // S->accepted = E_try <= E_k
 template <class R> void launch_accept(const Dev<R>& D, cudaStream_t st);
 // H_base-only forms for evaluation entry points

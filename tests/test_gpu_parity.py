@@ -89,10 +89,11 @@ def test_energy_gradient_parity(lib, name, precision, gtol, etol):
     assert err <= gtol, err
 
 
+@pytest.mark.parametrize("bp", [1, 2])  # hashed grid, cached candidate lists
 @pytest.mark.parametrize("name", list(SCENES))
-def test_contact_set_parity(lib, name):
+def test_contact_set_parity(lib, name, bp):
     sc = SCENES[name]
-    g, o = _pair(lib, sc)
+    g, o = _pair(lib, sc, broad_phase=bp)
     x = contact_state(sc) + 2e-6 * RNG.normal(size=sc["x0"].shape)
     cg, co = g.contacts(x), o.contacts(x)
     kg = {(int(t), int(a), int(b)): i for i, (t, (a, b)) in enumerate(zip(cg["type"], cg["ids"]))}
@@ -156,10 +157,11 @@ def test_forms_parity(lib, name):
         np.testing.assert_allclose(fg, fo, rtol=1e-10)
 
 
+@pytest.mark.parametrize("bp", [1, 2])  # hashed grid, cached candidate lists
 @pytest.mark.parametrize("name", list(SCENES))
-def test_ccd_parity(lib, name):
+def test_ccd_parity(lib, name, bp):
     sc = SCENES[name]
-    g, o = _pair(lib, sc)
+    g, o = _pair(lib, sc, broad_phase=bp)
     x = contact_state(sc, 3.0)
     nv = x.shape[0] // 2
     for trial in range(3):
@@ -217,7 +219,8 @@ def _oracle_stationarity(o, sc, x, x_prev, v_prev):
     return np.linalg.norm(z, axis=1).max(), o.energy(x, xt)
 
 
-def test_step_reaches_a_stationary_point_of_the_oracle_potential(lib):
+@pytest.mark.parametrize("bp", [0, 1, 2])  # automatic, hashed grid only, cached lists only
+def test_step_reaches_a_stationary_point_of_the_oracle_potential(lib, bp):
     """Three stacked cubes landing face to face: the barrier between faces is
     not convex, the step problem has several local minima, and which one a
     solver reaches depends on rounding-level decisions (GPU atomics reorder
@@ -240,7 +243,7 @@ def test_step_reaches_a_stationary_point_of_the_oracle_potential(lib):
     sv, sf, se = o.surface()
     saw = 0
     for step in range(3):
-        g = lib.Scene(sc, params={"tol": tol})
+        g = lib.Scene(sc, params={"tol": tol, "broad_phase": bp})
         g.set_state(x, v)
         st = g.step(1)
         assert st["converged"] == 1, (step, st)
