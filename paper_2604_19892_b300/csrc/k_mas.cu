@@ -2,16 +2,18 @@
 // the Sparse-Input Woodbury update of the level-0 inverses (Sec. 4.1, Eq. 7-8).
 //
 // RebuildMAS at x:
-//  1. per tet: dP/dF (9x9) of the SNH density, PSD-projected by cyclic Jacobi
-//     (negative eigenvalues clamped), times h^2 V, stored packed (45 values);
+//  1. per tet: dP/dF (9x9) of the SNH density, PSD-projected through its
+//     closed-form eigensystem (negative eigenvalues clamped), times h^2 V,
+//     stored packed (45 values);
 //  2. level blocks of H_base = M + h^2 sum_t K_t + sum_{c in C} k n n^T:
 //     level 0 takes the 3x3 couplings between vertices of one subdomain;
 //     level l >= 1 takes C_l H C_l^T restricted to one level-l subdomain.
 //     Elastic and PT/EE contact terms annihilate rigid translations, so a
 //     term whose vertices all fall in one level-l node adds nothing to that
 //     level and is skipped; mass and point-ground terms always add;
-//  3. every 96x96 block is inverted by Gauss-Jordan elimination in shared
-//     memory (the blocks are SPD), padded slots carry an identity;
+//  3. every 96x96 block is inverted through a scaled Cholesky factorisation
+//     in register tiles (B = s W^T W s, W = L^{-1}), padded slots carry an
+//     identity;
 //  4. the contact set is snapshot as C_base with a key table.
 // Woodbury (non-restart iterations): each current contact is classified
 // against C_base (new / rotated: dS = k, u = sqrt(k) n; stiffer: dS = k - k_b,
@@ -41,105 +43,215 @@ __device__ __forceinline__ void load_B(const Dev<R>& D, int t, R B[3][3]) {
 
 // ------------------------------------------------------ per-tet projected Hessian
 
+// Cyclic Jacobi on a symmetric 3x3 matrix: eigenvalues on the diagonal of
+// A, eigenvectors in the columns of V.
+template <class R>
+__device__ __forceinline__ void sym3_jacobi(R A[3][3], R V[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? (R)1 : (R)0;
+    R fro = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) fro += A[i][j] * A[i][j];
+    const R tol = (sizeof(R) == 8 ? (R)1e-32 : (R)1e-14) * fro;
+#pragma unroll 1
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        if (A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2] <= tol) break;
+#pragma unroll
+        for (int pq = 0; pq < 3; ++pq) {
+            const int pp = pq == 2 ? 1 : 0, qq = pq == 0 ? 1 : 2;
+            R apq = A[pp][qq];
+            if (apq == (R)0) continue;
+            R th = (A[qq][qq] - A[pp][pp]) / (2 * apq);
+            R tt = (th >= 0 ? (R)1 : (R)-1) / (fabs(th) + sqrt(th * th + (R)1));
+            R c = (R)1 / sqrt(tt * tt + (R)1), sn = tt * c;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                R akp = A[k][pp], akq = A[k][qq];
+                A[k][pp] = c * akp - sn * akq;
+                A[k][qq] = sn * akp + c * akq;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                R apk = A[pp][k], aqk = A[qq][k];
+                A[pp][k] = c * apk - sn * aqk;
+                A[qq][k] = sn * apk + c * aqk;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                R vkp = V[k][pp], vkq = V[k][qq];
+                V[k][pp] = c * vkp - sn * vkq;
+                V[k][qq] = sn * vkp + c * vkq;
+            }
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void add_mode(R acc[kH], R e, const R q[9]) {
+    if (!(e > (R)0)) return;
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        R ei = e * q[i];
+#pragma unroll
+        for (int j = i; j < 9; ++j) acc[k++] += ei * q[j];
+    }
+}
+
+// Per tet: K_t = h^2 V (d^2 Psi / dF^2)^+ in F space (vec column-major),
+// Psi = mu/2 (|F|^2 - 3) - mu (J - 1) + lam/2 (J - 1)^2, so
+// d^2 Psi/dF^2 = mu I + lam g g^T + (lam (J - 1) - mu) d^2 J/dF^2, g = cof F.
+// Its eigensystem is taken in closed form from the rotation-signed SVD
+// F = U diag(s) V^T (the analytic eigensystems of isotropic energies,
+// Smith et al. 2019): in the frame, d^2 J/dF^2 has eigenvalue +s_k on the
+// twist (E_ab - E_ba)/sqrt2 and -s_k on the flip (E_ab + E_ba)/sqrt2 of the
+// index pair {a, b} without k, and acts on the scaling modes diag(w) as
+// [[0, s2, s1], [s2, 0, s0], [s1, s0, 0]]; g lies in the scaling modes as
+// (s1 s2, s0 s2, s0 s1). The projection keeps the positive eigenvalues; it
+// equals the clamped 9x9 eigen-decomposition up to rounding (the projection
+// onto the PSD cone does not depend on the basis chosen within a cluster).
 template <class R>
 __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __restrict__ x) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= D.nt) return;
-    int4 q = D.tets[t];
-    int vid[4] = {q.x, q.y, q.z, q.w};
+    int4 q4 = D.tets[t];
+    int vid[4] = {q4.x, q4.y, q4.z, q4.w};
     R B[3][3];
     load_B(D, t, B);
     R F[3][3];
+#pragma unroll
     for (int r = 0; r < 3; ++r)
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double s = 0.0;
-            for (int j = 0; j < 3; ++j) s += (x[3 * vid[j + 1] + r] - x[3 * vid[0] + r]) * (double)B[j][c];
-            F[r][c] = (R)s;
+            double sacc = 0.0;
+            for (int j = 0; j < 3; ++j) sacc += (x[3 * vid[j + 1] + r] - x[3 * vid[0] + r]) * (double)B[j][c];
+            F[r][c] = (R)sacc;
         }
-    R f[3][3];  // columns
-    for (int c = 0; c < 3; ++c)
-        for (int r = 0; r < 3; ++r) f[c][r] = F[r][c];
-    R g[9];  // vec(cof F), column-major
-    for (int c = 0; c < 3; ++c) {
-        const R* a = f[(c + 1) % 3];
-        const R* b = f[(c + 2) % 3];
-        g[3 * c + 0] = a[1] * b[2] - a[2] * b[1];
-        g[3 * c + 1] = a[2] * b[0] - a[0] * b[2];
-        g[3 * c + 2] = a[0] * b[1] - a[1] * b[0];
-    }
-    R J = f[0][0] * g[0] + f[0][1] * g[1] + f[0][2] * g[2];
-    R mu = (R)D.tet_mu[t], lam = (R)D.tet_lam[t];
-    R s = lam * (J - (R)1) - mu;
-    R A[9][9];
-    for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) A[i][j] = lam * g[i] * g[j] + (i == j ? mu : (R)0);
-    // s * d cof / dF: block (c, c') = s * d(cof_c)/d(f_c'), hat(a) b = a x b
-    auto add_hat = [&](int rb, int cb, const R* a, R sc) {
-        A[3 * rb + 0][3 * cb + 1] += -sc * a[2];
-        A[3 * rb + 0][3 * cb + 2] += sc * a[1];
-        A[3 * rb + 1][3 * cb + 0] += sc * a[2];
-        A[3 * rb + 1][3 * cb + 2] += -sc * a[0];
-        A[3 * rb + 2][3 * cb + 0] += -sc * a[1];
-        A[3 * rb + 2][3 * cb + 1] += sc * a[0];
+    const R J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+    // V, s^2 from F^T F, sorted descending, V a rotation
+    R C[3][3], V[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) C[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+    sym3_jacobi(C, V);
+    R w[3] = {C[0][0], C[1][1], C[2][2]};
+    auto swapc = [&](int a, int b) {
+        R tw = w[a];
+        w[a] = w[b];
+        w[b] = tw;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R tv = V[k][a];
+            V[k][a] = V[k][b];
+            V[k][b] = tv;
+        }
     };
-    add_hat(0, 1, f[2], -s);
-    add_hat(0, 2, f[1], s);
-    add_hat(1, 0, f[2], s);
-    add_hat(1, 2, f[0], -s);
-    add_hat(2, 0, f[1], -s);
-    add_hat(2, 1, f[0], s);
-    // cyclic Jacobi
-    R Q[9][9];
-    for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) Q[i][j] = (i == j) ? (R)1 : (R)0;
-    R fro = 0;
-    for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) fro += A[i][j] * A[i][j];
-    // stop when the off-diagonal norm is ~eps-relative (FP32: 3e-7, FP64: 1e-15)
-    const R tol = (sizeof(R) == 8 ? (R)1e-30 : (R)1e-13) * fro;
-#pragma unroll 1
-    for (int sweep = 0; sweep < 20; ++sweep) {
-        R off = 0;
-        for (int i = 0; i < 9; ++i)
-            for (int j = i + 1; j < 9; ++j) off += A[i][j] * A[i][j];
-        if (off <= tol) break;
-#pragma unroll 1
-        for (int pp = 0; pp < 8; ++pp) {
-#pragma unroll 1
-            for (int qq = pp + 1; qq < 9; ++qq) {
-                R apq = A[pp][qq];
-                if (apq == (R)0) continue;
-                R th = (A[qq][qq] - A[pp][pp]) / (2 * apq);
-                R tt = (th >= 0 ? (R)1 : (R)-1) / (fabs(th) + sqrt(th * th + (R)1));
-                R c = (R)1 / sqrt(tt * tt + (R)1), sn = tt * c;
-                for (int k = 0; k < 9; ++k) {
-                    R akp = A[k][pp], akq = A[k][qq];
-                    A[k][pp] = c * akp - sn * akq;
-                    A[k][qq] = sn * akp + c * akq;
-                }
-                for (int k = 0; k < 9; ++k) {
-                    R apk = A[pp][k], aqk = A[qq][k];
-                    A[pp][k] = c * apk - sn * aqk;
-                    A[qq][k] = sn * apk + c * aqk;
-                }
-                for (int k = 0; k < 9; ++k) {
-                    R qkp = Q[k][pp], qkq = Q[k][qq];
-                    Q[k][pp] = c * qkp - sn * qkq;
-                    Q[k][qq] = sn * qkp + c * qkq;
-                }
-            }
+    if (w[0] < w[1]) swapc(0, 1);
+    if (w[1] < w[2]) swapc(1, 2);
+    if (w[0] < w[1]) swapc(0, 1);
+    R detV = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) - V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
+             V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
+    if (detV < (R)0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) V[k][2] = -V[k][2];
+    // U by Gram-Schmidt on the columns of F V; u2 = u0 x u1 keeps U a rotation
+    R b[3][3];  // b[i] = F v_i
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) b[i][r] = F[r][0] * V[0][i] + F[r][1] * V[1][i] + F[r][2] * V[2][i];
+    R U[3][3], sg[3];
+    R n0 = sqrt(b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2]);
+    R u0[3], u1[3], u2[3];
+    if (n0 > (R)0) {
+        for (int r = 0; r < 3; ++r) u0[r] = b[0][r] / n0;
+    } else {
+        u0[0] = 1;
+        u0[1] = u0[2] = 0;
+    }
+    R d01 = u0[0] * b[1][0] + u0[1] * b[1][1] + u0[2] * b[1][2];
+    for (int r = 0; r < 3; ++r) u1[r] = b[1][r] - d01 * u0[r];
+    R n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    if (n1 > (R)(sizeof(R) == 8 ? 1e-150 : 1e-30)) {
+        for (int r = 0; r < 3; ++r) u1[r] /= n1;
+    } else {
+        // any unit vector orthogonal to u0
+        int ax = fabs(u0[0]) <= fabs(u0[1]) ? (fabs(u0[0]) <= fabs(u0[2]) ? 0 : 2) : (fabs(u0[1]) <= fabs(u0[2]) ? 1 : 2);
+        R e[3] = {0, 0, 0};
+        e[ax] = 1;
+        u1[0] = u0[1] * e[2] - u0[2] * e[1];
+        u1[1] = u0[2] * e[0] - u0[0] * e[2];
+        u1[2] = u0[0] * e[1] - u0[1] * e[0];
+        R m = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+        for (int r = 0; r < 3; ++r) u1[r] /= m;
+        n1 = 0;
+    }
+    u2[0] = u0[1] * u1[2] - u0[2] * u1[1];
+    u2[1] = u0[2] * u1[0] - u0[0] * u1[2];
+    u2[2] = u0[0] * u1[1] - u0[1] * u1[0];
+    sg[0] = n0;
+    sg[1] = n1;
+    sg[2] = u2[0] * b[2][0] + u2[1] * b[2][1] + u2[2] * b[2][2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        U[r][0] = u0[r];
+        U[r][1] = u1[r];
+        U[r][2] = u2[r];
+    }
+    const R mu = (R)D.tet_mu[t], lam = (R)D.tet_lam[t];
+    const R cJ = lam * (J - (R)1) - mu;
+    R acc[kH];
+#pragma unroll
+    for (int k = 0; k < kH; ++k) acc[k] = 0;
+    const R r2 = (R)0.70710678118654752440;
+    R q[9];
+    // twist / flip modes of the index pairs {1,2}, {0,2}, {0,1}
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int a = k == 0 ? 1 : 0, bb = k == 2 ? 1 : 2;
+#pragma unroll
+        for (int flip = 0; flip < 2; ++flip) {
+            const R sgn = flip ? (R)1 : (R)-1;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int r = 0; r < 3; ++r) q[3 * c + r] = r2 * (U[r][a] * V[c][bb] + sgn * U[r][bb] * V[c][a]);
+            add_mode(acc, flip ? mu - cJ * sg[k] : mu + cJ * sg[k], q);
         }
     }
-    R lamv[9];
-    for (int i = 0; i < 9; ++i) lamv[i] = A[i][i] > (R)0 ? A[i][i] : (R)0;
-    R sc = (R)(D.h * D.h * D.tet_vol[t]);
+    // scaling modes: mu I + lam gh gh^T + cJ S on diag(w)
+    R As[3][3], Ws[3][3];
+    const R gh[3] = {sg[1] * sg[2], sg[0] * sg[2], sg[0] * sg[1]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) As[i][j] = lam * gh[i] * gh[j] + (i == j ? mu : (R)0);
+    As[0][1] += cJ * sg[2];
+    As[1][0] += cJ * sg[2];
+    As[0][2] += cJ * sg[1];
+    As[2][0] += cJ * sg[1];
+    As[1][2] += cJ * sg[0];
+    As[2][1] += cJ * sg[0];
+    sym3_jacobi(As, Ws);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                q[3 * c + r] = U[r][0] * Ws[0][m] * V[c][0] + U[r][1] * Ws[1][m] * V[c][1] + U[r][2] * Ws[2][m] * V[c][2];
+        add_mode(acc, As[m][m], q);
+    }
+    const R scl = (R)(D.h * D.h * D.tet_vol[t]);
     R* out = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
-    for (int i = 0; i < 9; ++i)
-        for (int j = i; j < 9; ++j) {
-            R acc = 0;
-            for (int k = 0; k < 9; ++k) acc += Q[i][k] * lamv[k] * Q[j][k];
-            out[pk(i, j) * kPack] = sc * acc;
-        }
+#pragma unroll
+    for (int k = 0; k < kH; ++k) out[k * kPack] = scl * acc[k];
 }
 
 // ------------------------------------------------------ block assembly
