@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=12,
+                    help="timesteps of the plain FP64 form timed for the comparison (0 = skip)")
+    ap.add_argument("--replays", type=int, default=30, help="L2-flushed replays per stage for the roofline")
+    ap.add_argument("--profile-replays", action="store_true",
+                    help="call cudaProfilerStart/Stop around the roofline replays (ncu --profile-from-start off)")
     ap.add_argument("--profile-from-step", type=int, default=-1,
                     help="call cudaProfilerStart before this timed step (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -126,6 +131,14 @@ def stage_bytes(nv, nt, nblocks, rsize):
     mas = nblocks * 96 * 96 * rsize + 2 * 3 * nv * rsize
     forms = nt * (54 * rsize + 16) + 2 * 3 * nv * rsize + nv * 8
     return {"mas_blocks": mas, "forms": forms}
+
+
+# DRAM bytes per launch from ncu captures of the same kernels (unchanged
+# since), scaled by the units a launch processes: profiles/ holds the
+# summaries and commands
+TRAFFIC = {
+    ("mas_blocks", "fp32"): {"bytes_per_block": 56.39e6 / 1507},
+}
 
 
 def run_cpu_baseline(sc, gpu_iters_per_step):
@@ -256,19 +269,34 @@ def main():
     steps_per_s = world * args.steps / (total_ms / 1e3)
     iters_per_s = world * iters / (total_ms / 1e3)
 
-    # roofline of the dominant HBM-bound stage
+    # roofline of the two per-iteration HBM-bound stages (MAS block apply,
+    # H~ quadratic forms): their kernels replayed on the final state of the
+    # timed run, 256 MB written before each replay to evict L2, a CUDA event
+    # pair on the launch stream around the stage's launches only (the
+    # in-loop stage events also catch host launch gaps; reported beside)
     peak, peak_kind = load_peaks()
     by = stage_bytes(nv, nt, nblocks, rsize)
     roof = {}
-    for stg in ("mas_blocks", "forms"):
+    if args.profile_replays:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+    for stg, sid in (("mas_blocks", 2), ("forms", 3)):
+        avg_ms = scene.profile_replay(sid, args.replays, flush=flush, stream=stream)
+        ach = by[stg] / (avg_ms / 1e3) / 1e9
         n = prof[stg]["launches"]
-        if n:
-            avg_s = prof[stg]["ms"] / n / 1e3
-            ach = by[stg] / avg_s / 1e9
-            roof[stg] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "traffic": None, "bytes_per_launch": by[stg], "avg_us": avg_s * 1e6, "launches": n,
-                         "peak_source": peak_kind}
-    dominant = max(roof, key=lambda s: prof[s]["ms"]) if roof else None
+        in_loop_us = 1e3 * prof[stg]["ms"] / n if n else None
+        tr = TRAFFIC.get((stg, args.precision))
+        traffic = tr["bytes_per_block"] * nblocks if tr and stg == "mas_blocks" else (
+            tr["bytes_per_tet"] * nt if tr else None)
+        roof[stg] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": traffic, "bytes_per_launch": by[stg], "avg_us": avg_ms * 1e3,
+                     "timing": f"{args.replays} replays on the final state, 256 MB read before each (L2 evicted), CUDA events",
+                     "in_loop_avg_us": in_loop_us, "in_loop_launches": n,
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    if args.profile_replays:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    dominant = "mas_blocks"
 
     # end-to-end through the C ABI with host buffers: per step the state goes
     # host -> device, the step runs, positions come back device -> host
@@ -290,6 +318,34 @@ def main():
         dt = time.perf_counter() - t0
         e2e = {"value": world * n_e2e / dt, "unit": "timesteps/s", "h2d_bytes_per_step": 2 * 3 * nv * 8,
                "d2h_bytes_per_step": 2 * 3 * nv * 8, "steps": n_e2e}
+
+    # plain form: the same timesteps in FP64 on the GPU (the method without
+    # mixed precision), compared over the first plain_steps timesteps
+    plain = None
+    if args.plain_steps > 0 and prec == ipc.IPC_PREC_FP32:
+        m = min(args.plain_steps, args.steps)
+        s64 = ipc.Scene(sc, precision=ipc.IPC_PREC_FP64)
+        for _ in range(args.warmup):
+            s64.step(1)
+        s64.set_state(sc["x0"], sc["v0"])
+        q0 = [torch.cuda.Event(enable_timing=True) for _ in range(m)]
+        q1 = [torch.cuda.Event(enable_timing=True) for _ in range(m)]
+        it64 = 0
+        torch.cuda.synchronize()
+        for k in range(m):
+            flush.fill_(float(k))
+            q0[k].record(stream)
+            it64 += s64.step(1)["iters"]
+            q1[k].record(stream)
+        torch.cuda.synchronize()
+        ms64 = sum(a.elapsed_time(b) for a, b in zip(q0, q1))
+        ms32 = sum(step_ms[:m])
+        it32 = sum(st["iters"] for st in status[:m])
+        plain = {"precision": "fp64", "timesteps": f"0..{m - 1}",
+                 "timesteps_per_s": m / (ms64 / 1e3), "iters_per_s": it64 / (ms64 / 1e3), "iters": it64,
+                 "mixed_timesteps_per_s": m / (ms32 / 1e3), "mixed_iters_per_s": it32 / (ms32 / 1e3),
+                 "mixed_iters": it32, "speedup_timesteps": (m / (ms32 / 1e3)) / (m / (ms64 / 1e3))}
+        del s64
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -321,6 +377,7 @@ def main():
         "p50_ms": p50,
         "p99_ms": p99,
         "converged_steps": sum(s["converged"] for s in status),
+        "vs_plain_fp64": plain,
         "roofline": roof.get(dominant) if dominant else None,
         "roofline_stages": roof,
         "stage_ms": {k: v["ms"] for k, v in prof.items()},

@@ -182,10 +182,13 @@ int ipc_query_surface(ipc_scene* s, int* verts, int* tris, int* edges);
 
 /* Per-stage device time of the scene's ipc_step calls, measured with CUDA
  * events recorded on the step's stream around each stage, accumulated until
- * reset.  Stages: 0 restart (RebuildMAS), 1 classify + top-K, 2 MAS apply
- * (restriction, block apply with Woodbury, prolongation), 3 quadratic forms
- * and dots, 4 direction, 5 CCD, 6 trial evaluation (contacts, energy,
- * gradient), 7 other.  ms[8] in milliseconds, launches[8] stage executions. */
+ * reset.  Stages: 0 restart (RebuildMAS), 1 classify + top-K, 2 MAS block
+ * apply with Woodbury (Eq. 7), 3 quadratic forms and dots, 4 direction, 5
+ * broad-phase choice and CCD, 6 trial evaluation (contacts, energy,
+ * gradient), 7 other (predictor, restriction, prolongation).  ms[8] in
+ * milliseconds, launches[8] stage executions.  Event pairs around short
+ * stages also catch host launch gaps; ipc_profile_replay times a stage's
+ * kernels alone. */
 typedef struct ipc_profile {
     double ms[8];
     long long launches[8];
@@ -194,6 +197,19 @@ typedef struct ipc_profile {
 /* enable != 0 starts timing (and resets the counters); 0 stops it. */
 int ipc_profile_enable(ipc_scene* s, int enable);
 int ipc_profile_read(ipc_scene* s, ipc_profile* out);
+
+/* Replays the kernels of one stage on the scene's current state `reps`
+ * times and returns their mean device time in *ms_mean: stage 2 = MAS block
+ * apply of level-0 and coarse blocks to the scene's gradient (no Woodbury
+ * patch), stage 3 = the H~ quadratic forms (Eq. 6) of the scene's z and p.
+ * Before each replay, if flush != NULL, flush_bytes of that caller-owned
+ * device buffer (16-byte aligned) are read, which evicts the stage's data
+ * from L2 without leaving dirty lines; the timed region is a CUDA
+ * event pair on `stream` around the stage's launches only.  Overwrites the
+ * scene's z (stage 2) and its dot-product scalars; meant for use between
+ * timesteps.  IPC_ERR_INVALID for another stage or reps < 1. */
+int ipc_profile_replay(ipc_scene* s, int stage, int reps, void* flush, size_t flush_bytes, void* stream,
+                       double* ms_mean);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (all scenes, all calls). */
@@ -210,6 +226,9 @@ typedef struct ipc_iter_record {
     double energy_before, energy_after;
     double alpha_min, alpha_max;
     double r;
+    double pmax;             /* max_v |p_v| of the direction */
+    int ccd_passes;          /* verification passes, -1 = uniform fallback */
+    int cached_pairs;        /* 1 if the broad phase used the cached candidate lists */
 } ipc_iter_record;
 
 /* ---- evaluation entry points (host arrays in and out) -------------------

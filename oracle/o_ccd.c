@@ -174,6 +174,13 @@ double o_loriginal_pt(const double* p4) {
     return a + b;
 }
 
+/* distance of the pair at X + t Q (PT: p, t0, t1, t2; EE: a0, a1, b0, b1) */
+static double dist_at(int kind, const double* X, const double* Q, double t) {
+    double Y[12], w[3], st[2];
+    for (int i = 0; i < 12; ++i) Y[i] = X[i] + t * Q[i];
+    return kind == 0 ? o_pt_distance(Y, Y + 3, Y + 6, Y + 9, w) : o_ee_distance(Y, Y + 3, Y + 6, Y + 9, st);
+}
+
 /* safe fraction of the motion x + t q, t in [0,1], for a PT (kind 0) or
  * EE (kind 1) pair on vertices v[4] (PT: p, t0, t1, t2). */
 static double pair_safe(const OScene* s, int kind, const int* v, const double* x, const double* q) {
@@ -202,7 +209,27 @@ static double pair_safe(const OScene* s, int kind, const int* v, const double* x
         o_ee_cubic(X, Q, coef);
     }
     double al = l > 0.0 ? (1.0 - s->prm.ccd_shrink) * d0 / l : INFINITY;
-    return o_cubic_safe(coef, al);
+    double a = o_cubic_safe(coef, al);
+    /* The coplanarity walk only rules out crossing: a grazing motion may end
+     * arbitrarily close to contact.  Reading: when the end of the step lies
+     * closer than s * min(d0, dhat), the step is cut back by bisection between
+     * the conservative bound alpha_l (where d >= s d0 holds) and the walk's
+     * result, 12 halvings. */
+    if (a > al) {
+        double thr = s->prm.ccd_shrink * (d0 < s->prm.dhat ? d0 : s->prm.dhat);
+        if (dist_at(kind, X, Q, a) < thr) {
+            double lo = al > 0.0 ? al : 0.0, hi = a;
+            for (int it = 0; it < 12; ++it) {
+                double mid = 0.5 * (lo + hi);
+                if (dist_at(kind, X, Q, mid) >= thr)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            a = lo;
+        }
+    }
+    return a;
 }
 
 static void swept_box(const double* x, const double* p, const int* v, int n, double* lo, double* hi) {

@@ -296,7 +296,10 @@ int setup_dev(ipc_scene* s) {
     D.p = A.arr<R>(n3);
     D.hess = A.arr<R>((size_t)D.ntp * kH * kPack);
     D.blocks = A.arr<R>((size_t)nb * kBlk * kBlk);
-    D.asmb = A.arr<R>((size_t)nb * kBlk * kBlk);
+    const int nb0 = m.nlev > 1 ? D.blk_off[1] : nb;
+    D.asmb = A.arr<double>((size_t)nb0 * kBlk * kBlk);
+    D.invflag = A.arr<int>(std::max(nb0, 1));
+    D.asmbc = A.arr<double>((size_t)std::max(nb - nb0, 1) * kBlk * kBlk);
     D.coarse_r = A.arr<R>(std::max(coff, 1));
     D.coarse_y = A.arr<R>(std::max(coff, 1));
     D.C = alloc_contacts(A, D.cap);
@@ -319,6 +322,7 @@ int setup_dev(ipc_scene* s) {
     D.body = d_body;
     D.alpha_b = A.arr<double>(m.nbody);
     D.shrink_b = A.arr<double>(m.nbody);
+    D.vflags = A.arr<int>(32);
     D.str_v = A.arr<int4>(D.straddle_cap);
     D.str_t = A.arr<int>(D.straddle_cap);
     int nprim = std::max(std::max(D.nsf, D.nse), 1);
@@ -426,7 +430,9 @@ std::string nonfinite_report(const Dev<R>& D, const Scalars& S, cudaStream_t st)
     KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.blocks, nb, cnt + 3));
     KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.hess, (size_t)D.ntp * kH * kPack, cnt + 4));
     KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.x, n3, cnt + 5));
-    KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.asmb, nb, cnt + 6));
+    const size_t nb0 = (size_t)(D.nlev > 1 ? D.blk_off[1] : D.blk_off[D.nlev]) * kBlk * kBlk;
+    KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.asmb, nb0, cnt + 6));
+    if (nb > nb0) KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.asmbc, nb - nb0, cnt + 7));
     unsigned long long h[8] = {0};
     cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -482,18 +488,19 @@ void eval_trial(const Dev<R>& D, int mode, double c, cudaStream_t st, bool list 
 }
 
 // Builds the candidate lists at x with margin delta; grows them (up to
-// max_pairs entries each) when they overflow. Returns 1 when the lists hold
+// max_pairs entries each) when they fill up. Returns 1 when the lists hold
 // every candidate, 0 when they would need more than max_pairs, < 0 on error.
 template <class R>
 int build_lists(ipc_scene* s, Dev<R>& D, const double* x, double delta, long long max_pairs, cudaStream_t st) {
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
         launch_cand_build(D, x, delta, st);
         CUDA_TRY(cudaMemcpyAsync(s->hv->cand_n, D.cand_n, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        long long need = std::max(s->hv->cand_n[0], s->hv->cand_n[1]);
-        if (need <= D.cand_cap) return 1;
-        if (need > max_pairs || attempt == 1) return 0;
-        long long cap = std::min(max_pairs, need + need / 4 + 4096);
+        // the append counters stop at the capacity, so a full list may have
+        // dropped pairs: grow 4x and rebuild
+        if (std::max(s->hv->cand_n[0], s->hv->cand_n[1]) < D.cand_cap) return 1;
+        if (D.cand_cap >= max_pairs) return 0;
+        long long cap = std::min(max_pairs, 4LL * D.cand_cap);
         int2* a = s->arena.arr<int2>(cap);
         int2* b = s->arena.arr<int2>(cap);
         if (!a || !b) {
@@ -519,8 +526,6 @@ int build_lists(ipc_scene* s, Dev<R>& D, const double* x, double delta, long lon
 // iterations of a timestep) use the per-call hashed grid.
 template <class R>
 int choose_broad_phase(ipc_scene* s, Dev<R>& D, cudaStream_t st, bool* use_list, double* bound_after) {
-    CUDA_TRY(cudaMemcpyAsync(&s->hv->S.pmax, &D.S->pmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
     const double pm = s->hv->S.pmax, md = s->hv->S.maxdisp;
     const int mode = s->prm.broad_phase;
     *use_list = false;
@@ -605,6 +610,21 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         }
         bool use_list = false;
         double bound_after = INFINITY;
+        // g.z, max|p| and the list drift of this iteration
+        CUDA_TRY(cudaMemcpyAsync(&s->hv->S.gz, &D.S->gz, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(&s->hv->S.pmax, &D.S->pmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (!restart && !(s->hv->S.gz > 0.0)) {
+            // the Woodbury-patched preconditioner is not positive at g (FP32
+            // inverses of very stiff blocks): no step; the iteration is
+            // redone as a restart with freshly inverted blocks
+            rec.gz = s->hv->S.gz;
+            rec.energy_before = rec.energy_after = Ek;
+            rec.r = INFINITY;
+            s->trace.push_back(rec);
+            restart = true;
+            continue;
+        }
         {
             Stage t(s, 5, st);
             if (int e = choose_broad_phase(s, D, st, &use_list, &bound_after)) return e;
@@ -631,6 +651,9 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         rec.znorm = S.znorm;
         rec.alpha_min = S.alpha_min;
         rec.alpha_max = S.alpha_max;
+        rec.pmax = S.pmax;
+        rec.ccd_passes = S.ccd_passes;
+        rec.cached_pairs = use_list ? 1 : 0;
         rec.energy_before = Ek;
         int accepted = S.accepted;
         int halv = 0;
@@ -906,6 +929,48 @@ int eval_ccd_impl(ipc_scene* s, const double* x, const double* p, double* alpha,
     if (alpha_body) CUDA_TRY(cudaMemcpy(alpha_body, D.alpha_b, sizeof(double) * D.nbody, cudaMemcpyDeviceToHost));
     if (passes_body) *passes_body = s->hv->S.ccd_passes_b;
     return IPC_OK;
+}
+
+// reads n 16-byte words (to fill L2 with clean lines of another buffer)
+__global__ void k_touch(const uint4* __restrict__ p, size_t n, unsigned* sink) {
+    unsigned acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint4 v = p[i];
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x9e3779b9u) *sink = acc;
+}
+
+template <class R>
+int replay_impl(ipc_scene* s, int stage, int reps, void* flush, size_t flush_bytes, cudaStream_t st, double* ms) {
+    Dev<R>& D = dev_of<R>(s);
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(IPC_ERR_CUDA, "cudaEventCreate failed");
+    }
+    double tot = 0.0;
+    int rc = IPC_OK;
+    for (int i = 0; i < reps && rc == IPC_OK; ++i) {
+        if (flush && flush_bytes >= 16)
+            KL(k_touch<<<1184, 256, 0, st>>>(static_cast<const uint4*>(flush), flush_bytes / 16,
+                                             static_cast<unsigned*>(flush)));
+        cudaEventRecord(a, st);
+        if (stage == 2)
+            launch_blocks(D, D.g, D.z, D.C, false, st);
+        else
+            launch_forms(D, D.C, false, st);
+        cudaEventRecord(b, st);
+        float e = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&e, a, b) != cudaSuccess)
+            rc = fail(IPC_ERR_CUDA, std::string("replay: ") + cudaGetErrorString(cudaGetLastError()));
+        tot += e;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc == IPC_OK) *ms = tot / reps;
+    return rc;
 }
 
 // ---- allocation-free preconditioner apply (no counterpart in the paper)
@@ -1229,6 +1294,15 @@ int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr, con
     cudaStream_t st = (cudaStream_t)stream;
     return s->prec == IPC_PREC_FP64 ? eval_forms_impl<double>(s, x_base, x_curr, z, p, out, st)
                                     : eval_forms_impl<float>(s, x_base, x_curr, z, p, out, st);
+}
+
+int ipc_profile_replay(ipc_scene* s, int stage, int reps, void* flush, size_t flush_bytes, void* stream,
+                       double* ms_mean) {
+    if (!checked(s) || !ms_mean) return fail(IPC_ERR_INVALID, "null argument");
+    if ((stage != 2 && stage != 3) || reps < 1) return fail(IPC_ERR_INVALID, "replay: stage must be 2 or 3, reps >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    return s->prec == IPC_PREC_FP64 ? replay_impl<double>(s, stage, reps, flush, flush_bytes, st, ms_mean)
+                                    : replay_impl<float>(s, stage, reps, flush, flush_bytes, st, ms_mean);
 }
 
 int ipc_precond_apply_noalloc(ipc_scene* s, const void* g_dev, void* z_dev, void* stream) {

@@ -111,7 +111,9 @@ struct Dev {
     R *g, *gtry, *z, *zprev, *p;
     R* hess;                               // [ntp][45][32]
     R* blocks;                             // nblocks * 96 * 96
-    R* asmb;                               // assembly buffer, same shape
+    double* asmb;                          // level-0 assembly buffer (FP64)
+    double* asmbc;                         // coarse-level assembly buffer (FP64)
+    int* invflag;                          // level-0 blocks to re-invert in FP64
     R* coarse_r;                           // restricted residuals, 3 * nnodes[l] per level, offsets coarse_off
     R* coarse_y;
     int coarse_off[kMaxLevels + 1];
@@ -135,6 +137,7 @@ struct Dev {
     const int* body;                       // connected body of each vertex
     double* alpha_b;                       // per body
     double* shrink_b;
+    int* vflags;                           // verification: violation flag per grouping and pass
     int4* str_v;                           // straddling candidates: vertices
     int* str_t;                            // 0 PT (p, t0, t1, t2), 1 EE (a0, a1, b0, b1)
     // broad-phase grid (shared by proximity and CCD queries)

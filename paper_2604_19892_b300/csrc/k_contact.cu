@@ -20,10 +20,14 @@
 // actual motion alpha_d(v) p_v; the subdomains of a pair whose safe fraction
 // rho < 1 all take the pair's smallest alpha; after at most 8 passes with a
 // violation the uniform step min_d alpha_d is taken (never below it).
+#include <cooperative_groups.h>
+
 #include "geom.cuh"
 #include "kernels.h"
 
 namespace ipcb {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -70,6 +74,13 @@ __device__ __forceinline__ bool overlap(const double* lo1, const double* hi1, co
              hi2[2] < lo1[2]);
 }
 
+// cell indices of the box fit in int (and the box is finite)
+__device__ __forceinline__ bool box_in_range(const double* lo, const double* hi, double inv) {
+    bool ok = true;
+    for (int r = 0; r < 3; ++r) ok &= fabs(lo[r] * inv) < 1e9 && fabs(hi[r] * inv) < 1e9;
+    return ok;
+}
+
 // ---------------------------------------------------------------- grid build
 
 template <class R>
@@ -86,11 +97,15 @@ __global__ void k_grid_count(Dev<R> D, const int* prims, int nper, int nprim, co
         D.pbox[6 * (size_t)i + 3 + r] = hi[r];
     }
     double inv = 1.0 / *D.cellsz;
-    long long n0 = (long long)cellc(hi[0], inv) - cellc(lo[0], inv) + 1;
-    long long n1 = (long long)cellc(hi[1], inv) - cellc(lo[1], inv) + 1;
-    long long n2 = (long long)cellc(hi[2], inv) - cellc(lo[2], inv) + 1;
+    // a box outside the cell-index range (or not finite) goes to the large list
+    bool finite = true;
+    for (int r = 0; r < 3; ++r) finite &= fabs(lo[r] * inv) < 1e9 && fabs(hi[r] * inv) < 1e9;
+    long long n0 = finite ? (long long)cellc(hi[0], inv) - cellc(lo[0], inv) + 1 : kMaxCells + 1;
+    long long n1 = finite ? (long long)cellc(hi[1], inv) - cellc(lo[1], inv) + 1 : kMaxCells + 1;
+    long long n2 = finite ? (long long)cellc(hi[2], inv) - cellc(lo[2], inv) + 1 : kMaxCells + 1;
     long long nc = n0 * n1 * n2;
-    bool in_grid = nc <= kMaxCells && n0 <= kMaxCells && n1 <= kMaxCells && n2 <= kMaxCells;
+    bool in_grid = finite && n0 >= 1 && n1 >= 1 && n2 >= 1 && nc <= kMaxCells && n0 <= kMaxCells &&
+                   n1 <= kMaxCells && n2 <= kMaxCells;
     if (in_grid) {
         int old = atomicAdd(D.gtotal, (int)nc);
         if (old + nc > D.gcap) in_grid = false;
@@ -152,6 +167,12 @@ void build_grid(const Dev<R>& D, const int* prims, int nper, int nprim, const do
 
 __device__ __forceinline__ void put_contact(const ContactBuf& C, int cap, int type, int4 v, unsigned long long key,
                                             double d, double kap, double dhat, d3 r, const double w[4], Scalars* S) {
+    // counters stop growing once full (checked before the increment), so
+    // they stay far below INT_MAX however many pairs qualify
+    if (*(volatile int*)C.count >= cap) {
+        atomicOr(&S->overflow, 1);
+        return;
+    }
     int i = atomicAdd(C.count, 1);
     if (i >= cap) {
         atomicOr(&S->overflow, 1);
@@ -249,7 +270,7 @@ __global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, 
     int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
     int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
     long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0)) nc = kMaxCells + 1;
+    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
     if (nc > kMaxCells) {
         for (int j = i + 1; j < D.nse; ++j) {
             const double* b = D.pbox + 6 * (size_t)j;
@@ -305,6 +326,18 @@ __global__ void k_reset_detect(Dev<R> D, ContactBuf C) {
 
 // ------------------------------------------------------------------- CCD
 
+// distance of the pair at X + t Q (PT: p, t0, t1, t2; EE: a0, a1, b0, b1)
+__device__ __forceinline__ double pair_dist_at(int kind, const d3 X[4], const d3 Q[4], double t) {
+    d3 Y[4];
+    for (int j = 0; j < 4; ++j) Y[j] = X[j] + t * Q[j];
+    if (kind == 0) {
+        double w[3];
+        return sqrt(pt_closest(Y[0], Y[1], Y[2], Y[3], w));
+    }
+    double s, u;
+    return sqrt(ee_closest(Y[0], Y[1], Y[2], Y[3], s, u));
+}
+
 template <class R>
 __device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const double* x, const R* p, const double* scale,
                              const int* grp = nullptr) {
@@ -334,7 +367,25 @@ __device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const do
         cubic_of(X[2] - X[0], Q[2] - Q[0], X[1] - X[0], Q[1] - Q[0], X[3] - X[0], Q[3] - Q[0], c);
     }
     double al = l > 0.0 ? (1.0 - D.ccd_shrink) * d0 / l : __longlong_as_double(0x7ff0000000000000ULL);
-    return cubic_safe(c, al);
+    double a = cubic_safe(c, al);
+    // the coplanarity walk only rules out crossing; a step ending closer than
+    // s min(d0, dhat) is cut back by 12 bisections between alpha_l (where
+    // d >= s d0 holds) and the walk's result
+    if (a > al) {
+        const double thr = D.ccd_shrink * fmin(d0, D.dhat);
+        if (pair_dist_at(kind, X, Q, a) < thr) {
+            double lo = al > 0.0 ? al : 0.0, hi = a;
+            for (int it = 0; it < 12; ++it) {
+                double mid = 0.5 * (lo + hi);
+                if (pair_dist_at(kind, X, Q, mid) >= thr)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            a = lo;
+        }
+    }
+    return a;
 }
 
 template <class R>
@@ -354,7 +405,7 @@ __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
     }
     // keep every pair that straddles subdomains or bodies for verification
     if (!(g1 == g0 && g2 == g0 && g3 == g0) || !(b1 == b0 && b2 == b0 && b3 == b0)) {
-        int k = atomicAdd(&D.S->n_straddle, 1);
+        int k = *(volatile int*)&D.S->n_straddle < D.straddle_cap ? atomicAdd(&D.S->n_straddle, 1) : D.straddle_cap;
         if (k < D.straddle_cap) {
             D.str_v[k] = make_int4(v[0], v[1], v[2], v[3]);
             D.str_t[k] = kind;
@@ -375,7 +426,7 @@ __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
     int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
     int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
     long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0)) nc = kMaxCells + 1;
+    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
     auto visit = [&](int f) {
         int v[4] = {pv, D.sf[3 * f], D.sf[3 * f + 1], D.sf[3 * f + 2]};
         if (pv == v[1] || pv == v[2] || pv == v[3]) return;
@@ -423,7 +474,7 @@ __global__ void k_ccd_ee(Dev<R> D, const int* gin) {
     int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
     int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
     long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0)) nc = kMaxCells + 1;
+    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
     auto visit = [&](int j) {
         int v[4] = {vid[0], vid[1], D.se[2 * j], D.se[2 * j + 1]};
         if (v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3]) return;
@@ -496,8 +547,8 @@ __device__ __forceinline__ void append_pair(int2* list, int* count, int cap, int
     int lane = threadIdx.x & 31;
     int leader = __ffs(m) - 1;
     int rank = __popc(m & ((1u << lane) - 1u));
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
+    int base = cap;
+    if (lane == leader && *(volatile int*)count < cap) base = atomicAdd(count, __popc(m));
     base = __shfl_sync(m, base, leader);
     int k = base + rank;
     if (k < cap) list[k] = make_int2(a, b);
@@ -547,7 +598,7 @@ __global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
     int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
     int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
     long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0)) nc = kMaxCells + 1;
+    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
     if (nc > kMaxCells) {
         for (int j = i + 1; j < D.nse; ++j) {
             const double* b = D.pbox + 6 * (size_t)j;
@@ -641,6 +692,7 @@ __global__ void k_ccd_begin(Dev<R> D) {
     Scalars* S = D.S;
     S->n_straddle = 0;
     S->overflow &= ~2;
+    for (int i = 0; i < 2 * kCcdPasses; ++i) D.vflags[i] = 0;
     S->ccd_viol = S->ccd_viol_b = 0;
     S->ccd_uniform = S->ccd_uniform_b = 0;
     S->ccd_passes = S->ccd_passes_b = 0;
@@ -660,109 +712,109 @@ struct Grouping {
     double* amax;
 };
 
-// one block: min / max of a[0..n)
-__global__ void k_minmax(const double* a, int n, double* out_min, double* out_max) {
-    __shared__ double smin[32], smax[32];
-    double mn = 1.0, mx = 0.0;
-    for (int g = threadIdx.x; g < n; g += blockDim.x) {
-        mn = fmin(mn, a[g]);
-        mx = fmax(mx, a[g]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        smin[threadIdx.x >> 5] = mn;
-        smax[threadIdx.x >> 5] = mx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            mn = fmin(mn, smin[w]);
-            mx = fmax(mx, smax[w]);
-        }
-        if (out_min) *out_min = mn;
-        if (out_max) *out_max = mx;
-    }
-}
-
-// verification pass: re-check pairs straddling groups with the actual motion
-// alpha_g(v) p_v; a violating pair lowers every group it touches to the
-// pair's smallest alpha (the pair then moves uniformly on a segment already
-// checked)
-__global__ void k_verify_prep(Grouping G) {
-    if (*G.state != 0) return;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.shrink[g] = G.alpha[g];
-}
-
+// Verification of the straddling candidates for both groupings (level-0
+// subdomains, then bodies) in one cooperative launch: per pass, every
+// straddling pair is re-checked with the actual motion alpha_g(v) p_v; a
+// violating pair lowers every group it touches to the pair's smallest alpha
+// (the pair then moves uniformly on a segment already checked). The pass
+// loop stops at the first clean pass; after kCcdPasses passes with a
+// violation, or when the candidate list overflowed, the grouping takes the
+// uniform step min_g alpha_g. Grid-wide barriers are cooperative-groups
+// syncs of a co-resident grid (cudaLaunchCooperativeKernel); every thread
+// executes the same sequence of them.
 template <class R>
-__global__ void k_verify(Dev<R> D, Grouping G) {
-    if (*G.state != 0) return;  // verified, or falling back to the uniform step
-    int n = min(D.S->n_straddle, D.straddle_cap);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int4 q = D.str_v[k];
-        int v[4] = {q.x, q.y, q.z, q.w};
-        int g0 = G.of[v[0]];
-        if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) continue;
-        double rho = pair_alpha(D, D.str_t[k], v, D.x, D.p, G.alpha, G.of);
-        if (rho < 1.0) {
-            *G.viol = 1;
-            double m = G.alpha[g0];
-            for (int j = 1; j < 4; ++j) m = fmin(m, G.alpha[G.of[v[j]]]);
-            for (int j = 0; j < 4; ++j) atomicMinPos(&G.shrink[G.of[v[j]]], m);
+__global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Grouping G1) {
+    cg::grid_group grid = cg::this_grid();
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int nstr = min(D.S->n_straddle, D.straddle_cap);
+    const bool overflow = (D.S->overflow & 2) != 0;
+    for (int gi = 0; gi < 2; ++gi) {
+        const Grouping& G = gi ? G1 : G0;
+        int* vf = D.vflags + gi * kCcdPasses;
+        if (tid == 0) *G.amin = 1.0;
+        grid.sync();
+        double mn = 1.0;
+        for (int g = tid; g < G.n; g += nth) mn = fmin(mn, G.alpha[g]);
+        for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        if (lane == 0 && mn < 1.0) atomicMinPos(G.amin, mn);
+        grid.sync();
+        int state = overflow ? 1 : 0;  // 0 running, 1 uniform fallback, 2 verified
+        int passes = overflow ? -1 : 0;
+        for (int pass = 0; pass < kCcdPasses && state == 0; ++pass) {
+            for (int g = tid; g < G.n; g += nth) G.shrink[g] = G.alpha[g];
+            grid.sync();
+            for (int k = tid; k < nstr; k += nth) {
+                int4 q = D.str_v[k];
+                int v[4] = {q.x, q.y, q.z, q.w};
+                int g0 = G.of[v[0]];
+                if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) continue;
+                double rho = pair_alpha(D, D.str_t[k], v, D.x, D.p, G.alpha, G.of);
+                if (rho < 1.0) {
+                    vf[pass] = 1;
+                    double m = G.alpha[g0];
+                    for (int j = 1; j < 4; ++j) m = fmin(m, G.alpha[G.of[v[j]]]);
+                    for (int j = 0; j < 4; ++j) atomicMinPos(&G.shrink[G.of[v[j]]], m);
+                }
+            }
+            grid.sync();
+            if (__ldcg(&vf[pass]) == 0) {
+                state = 2;
+                passes = pass + 1;
+                break;
+            }
+            for (int g = tid; g < G.n; g += nth) G.alpha[g] = G.shrink[g];
+            grid.sync();
         }
-    }
-}
-
-__global__ void k_verify_apply(Grouping G) {
-    if (*G.state != 0 || !*G.viol) return;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.alpha[g] = G.shrink[g];
-}
-
-// after pass `pass`: stop if clean; after the last pass with a violation
-// mark the uniform fallback
-__global__ void k_verify_flag(Grouping G, int pass, int last) {
-    if (*G.state != 0) return;
-    if (!*G.viol) {
-        *G.state = 2;
-        *G.passes = pass + 1;
-        return;
-    }
-    *G.viol = 0;
-    if (last) {
-        *G.state = 1;
-        *G.passes = -1;
-    }
-}
-
-__global__ void k_uniform(Grouping G) {
-    if (*G.state != 1) return;
-    double a = *G.amin;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G.n; g += gridDim.x * blockDim.x) G.alpha[g] = a;
-}
-
-// a straddling-candidate list that overflowed cannot be verified: the
-// grouping takes the uniform step alpha_min, which needs no verification
-__global__ void k_verify_begin(Grouping G, const Scalars* S) {
-    if (S->overflow & 2) {
-        *G.state = 1;
-        *G.passes = -1;
+        if (state == 0) {
+            state = 1;
+            passes = -1;
+        }
+        if (state == 1) {
+            const double a = __ldcg(G.amin);
+            for (int g = tid; g < G.n; g += nth) G.alpha[g] = a;
+        }
+        if (tid == 0) {
+            *G.state = state;
+            *G.passes = passes;
+            *G.viol = state != 2;
+            *G.amin = 1.0;
+            *G.amax = 0.0;
+        }
+        grid.sync();
+        double lo = 1.0, hi = 0.0;
+        for (int g = tid; g < G.n; g += nth) {
+            lo = fmin(lo, G.alpha[g]);
+            hi = fmax(hi, G.alpha[g]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            if (lo < 1.0) atomicMinPos(G.amin, lo);
+            if (hi > 0.0) atomicMaxPos(G.amax, hi);
+        }
+        grid.sync();
     }
 }
 
 template <class R>
-void verify_grouping(const Dev<R>& D, const Grouping& G, cudaStream_t st) {
-    KL(k_minmax<<<1, 1024, 0, st>>>(G.alpha, G.n, G.amin, nullptr));
-    KL(k_verify_begin<<<1, 1, 0, st>>>(G, D.S));
-    for (int pass = 0; pass < kCcdPasses; ++pass) {
-        KL(k_verify_prep<<<nblk(G.n), kT, 0, st>>>(G));
-        KL(k_verify<R><<<592, kT, 0, st>>>(D, G));
-        KL(k_verify_apply<<<nblk(G.n), kT, 0, st>>>(G));
-        KL(k_verify_flag<<<1, 1, 0, st>>>(G, pass, pass == kCcdPasses - 1 ? 1 : 0));
+void verify_groupings(const Dev<R>& D, const Grouping& sub, const Grouping& bod, cudaStream_t st) {
+    static int nblocks = 0;
+    if (nblocks == 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_verify_all<R>, 256, 0);
+        nblocks = sms * (per < 2 ? per : 2);
+        if (nblocks < 1) nblocks = 1;
     }
-    KL(k_uniform<<<nblk(G.n), kT, 0, st>>>(G));
-    KL(k_minmax<<<1, 1024, 0, st>>>(G.alpha, G.n, G.amin, G.amax));
+    Dev<R> Dc = D;
+    Grouping a = sub, b = bod;
+    void* args[] = {&Dc, &a, &b};
+    KL(cudaLaunchCooperativeKernel((const void*)k_verify_all<R>, dim3(nblocks), dim3(256), args, 0, st));
 }
 
 }  // namespace
@@ -795,8 +847,7 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
                  &S->alpha_max};
     Grouping bod{D.body, D.alpha_b, D.shrink_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b, &S->ccd_passes_b,
                  &S->alpha_bmin, &S->alpha_bmax};
-    verify_grouping(D, sub, st);
-    verify_grouping(D, bod, st);
+    verify_groupings(D, sub, bod, st);
 }
 
 template <class R>
@@ -843,8 +894,7 @@ void launch_ccd_list(const Dev<R>& D, cudaStream_t st) {
                  &S->alpha_max};
     Grouping bod{D.body, D.alpha_b, D.shrink_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b, &S->ccd_passes_b,
                  &S->alpha_bmin, &S->alpha_bmax};
-    verify_grouping(D, sub, st);
-    verify_grouping(D, bod, st);
+    verify_groupings(D, sub, bod, st);
 }
 
 #define INST(R)                                                                               \

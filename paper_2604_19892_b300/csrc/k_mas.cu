@@ -21,6 +21,8 @@
 // largest dS (ties by ascending key) touching it; the block apply reads B_d
 // once for [g_d, U_d], solves the K x K capacitance system in FP64 and
 // corrects z_d = B g_d - W lambda (Eq. 7).  Coarse levels stay frozen (Eq. 8).
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace ipcb {
@@ -256,8 +258,8 @@ __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __re
 
 // ------------------------------------------------------ block assembly
 
-template <class R>
-__device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb, const R blk[3][3]) {
+template <class R, class V>
+__device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb, const V blk[3][3]) {
     int na, nb, ga, gb, sa, sb;
     if (l == 0) {
         ga = D.grp0[va];
@@ -274,12 +276,23 @@ __device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb
         sa = D.slot_of_node[l][na];
         sb = D.slot_of_node[l][nb];
     }
-    R* A = D.asmb + ((size_t)(D.blk_off[l] + ga)) * (kBlk * kBlk);
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            R v = blk[r][c];
-            if (v != (R)0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
-        }
+    // blocks are summed in FP64 (coarse Galerkin blocks add many terms of
+    // both signs, stiff contacts must cancel exactly), inverted in R
+    if (l == 0) {
+        double* A = D.asmb + (size_t)ga * (kBlk * kBlk);
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double v = (double)blk[r][c];
+                if (v != 0.0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
+            }
+    } else {
+        double* A = D.asmbc + ((size_t)(D.blk_off[l] - D.blk_off[1] + ga)) * (kBlk * kBlk);
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double v = (double)blk[r][c];
+                if (v != 0.0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
+            }
+    }
 }
 
 // is every vertex of the term inside one level-l node? (translation-invariant
@@ -359,9 +372,12 @@ __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
         double w[4] = {C.w[4 * i], C.w[4 * i + 1], C.w[4 * i + 2], C.w[4 * i + 3]};
         for (int a = 0; a < nvv; ++a)
             for (int b = 0; b < nvv; ++b) {
-                R blk[3][3];
+                // kept in FP64 until the store: the coarse levels sum these
+                // (weights summing to zero) with FP64 atomics, so a stiff
+                // contact's translation-invariant terms cancel there
+                double blk[3][3];
                 for (int rr = 0; rr < 3; ++rr)
-                    for (int s = 0; s < 3; ++s) blk[rr][s] = (R)(k * w[a] * w[b] * r[rr] * r[s]);
+                    for (int s = 0; s < 3; ++s) blk[rr][s] = k * w[a] * w[b] * r[rr] * r[s];
                 for (int l = 0; l < D.nlev; ++l) {
                     if (nvv == 4 && one_node(D, l, vid, 4)) continue;
                     add_block(D, l, vid[a], vid[b], blk);
@@ -393,23 +409,31 @@ constexpr int kInvThreads = 160;
 static_assert(kNT * kTile == kBlk, "tile size must divide the block size");
 static_assert(kInvThreads >= kNTiles && kInvThreads % 32 == 0, "one thread per lower tile");
 
-template <class R>
-__global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
+// flags (level-0 blocks): pass 0 (T = float) marks a block whose
+// factorisation floored or raised a pivot, i.e. whose conditioning FP32
+// cannot carry (very stiff contacts); pass 1 (T = double) re-inverts only
+// the marked blocks from the same FP64 assembly. flags == nullptr: no marks.
+template <class R, class T>
+__global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, const double* __restrict__ srcbase, int b0,
+                                                       int* flags, int pass) {
     extern __shared__ unsigned char smem_raw[];
-    R* buf = reinterpret_cast<R*>(smem_raw);      // 96 x 96: L^T, then W
-    R* vec = buf + kBlk * kBlk;                   // 2 x 96 broadcast
-    R* sc = vec + 2 * kBlk;                       // diagonal scaling s
-    R* pm = sc + kBlk;                            // 2 x 16 column maxima of L_rk^2
-    const R eps_piv = (R)(sizeof(R) == 8 ? 1e-12 : 1e-6);
-    int b = blockIdx.x;
+    T* buf = reinterpret_cast<T*>(smem_raw);      // 96 x 96: L^T, then W
+    T* vec = buf + kBlk * kBlk;                   // 2 x 96 broadcast
+    T* sc = vec + 2 * kBlk;                       // diagonal scaling s
+    T* pm = sc + kBlk;                            // 2 x 16 column maxima of L_rk^2
+    __shared__ int s_bad;
+    const T eps_piv = (T)(sizeof(T) == 8 ? 1e-12 : 1e-6);
+    int b = b0 + blockIdx.x;
+    if (pass == 1 && !flags[b]) return;  // uniform over the CTA
     int l = 0;
     while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
     int grp = b - D.blk_off[l];
     const int* mem = D.members[l] + (size_t)grp * kSub;
-    const R* src = D.asmb + (size_t)b * kBlk * kBlk;
+    const double* src = srcbase + (size_t)(b - b0) * kBlk * kBlk;
+    if (threadIdx.x == 0) s_bad = 0;
     for (int r = threadIdx.x; r < kBlk; r += blockDim.x) {
-        R d = src[r * kBlk + r];
-        sc[r] = (mem[r / 3] < 0 || !(d > (R)0)) ? (R)1 : (R)1 / sqrt(d);
+        double d = src[r * kBlk + r];
+        sc[r] = (mem[r / 3] < 0 || !(d > 0.0)) ? (T)1 : (T)(1.0 / sqrt(d));
     }
     // thread t owns tile (ti, tj), ti >= tj, t = ti (ti + 1) / 2 + tj
     const int t = threadIdx.x;
@@ -425,18 +449,18 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
     }
     const int r0 = kTile * ti, c0 = kTile * tj;
     __syncthreads();
-    R a[kTile][kTile];
+    T a[kTile][kTile];
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
         for (int cc = 0; cc < kTile; ++cc) {
             int r = r0 + rr, c = c0 + cc;
-            R v = (R)0;
+            T v = (T)0;
             if (act) {
                 if (mem[r / 3] < 0 || mem[c / 3] < 0)
-                    v = (r == c) ? (R)1 : (R)0;
+                    v = (r == c) ? (T)1 : (T)0;
                 else
-                    v = src[r * kBlk + c] * sc[r] * sc[c];
+                    v = (T)(src[r * kBlk + c] * (double)sc[r] * (double)sc[c]);
             }
             a[rr][cc] = v;
         }
@@ -446,12 +470,12 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
 #pragma unroll
         for (int kk = 0; kk < kTile; ++kk) {
             const int k = kTile * kt + kk;
-            R* vb = vec + (k & 1) * kBlk;
+            T* vb = vec + (k & 1) * kBlk;
             if (act && tj == kt) {
-                R m = (R)0;
+                T m = (T)0;
 #pragma unroll
                 for (int rr = 0; rr < kTile; ++rr) {
-                    R v = (ti == kt && rr < kk) ? (R)0 : a[rr][kk];
+                    T v = (ti == kt && rr < kk) ? (T)0 : a[rr][kk];
                     vb[r0 + rr] = v;
                     if ((ti > kt || rr > kk) && v * v > m) m = v * v;
                 }
@@ -463,13 +487,15 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
                 // holds for any SPD matrix: where rounding breaks it the pivot
                 // is raised (a diagonal shift, as in a modified Cholesky), so
                 // L stays bounded and no floored pivot can cascade
-                R piv = vb[k];
+                const T raw = vb[k];
+                T piv = raw;
                 if (!(piv > eps_piv)) piv = eps_piv;
-                const R* pmk = pm + (k & 1) * kNT;
+                const T* pmk = pm + (k & 1) * kNT;
                 for (int q = kt; q < kNT; ++q) piv = pmk[q] > piv ? pmk[q] : piv;
-                const R sq = sqrt(piv);
-                const R ip = (R)1 / piv, isq = (R)1 / sq;
-                R vr[kTile], vc[kTile];
+                if (ti == kt && tj == kt && piv != raw) s_bad = 1;
+                const T sq = sqrt(piv);
+                const T ip = (T)1 / piv, isq = (T)1 / sq;
+                T vr[kTile], vc[kTile];
 #pragma unroll
                 for (int q = 0; q < kTile; ++q) {
                     vr[q] = vb[r0 + q];
@@ -504,15 +530,15 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (act && ti == tj && rr == cc) ? (R)1 : (R)0;
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (act && ti == tj && rr == cc) ? (T)1 : (T)0;
     for (int kt = 0; kt < kNT; ++kt) {
 #pragma unroll
         for (int kk = 0; kk < kTile; ++kk) {
             const int k = kTile * kt + kk;
-            R* vb = vec + (k & 1) * kBlk;
-            const R* Lk = buf + k * kBlk;                 // column k of L
+            T* vb = vec + (k & 1) * kBlk;
+            const T* Lk = buf + k * kBlk;                 // column k of L
             if (act && ti == kt) {
-                const R il = (R)1 / Lk[k];
+                const T il = (T)1 / Lk[k];
 #pragma unroll
                 for (int cc = 0; cc < kTile; ++cc) {
                     a[kk][cc] *= il;
@@ -521,10 +547,10 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
             }
             __syncthreads();
             if (act && ti >= kt && tj <= kt) {
-                R lr[kTile], wc[kTile];
+                T lr[kTile], wc[kTile];
 #pragma unroll
                 for (int q = 0; q < kTile; ++q) {
-                    lr[q] = (ti > kt || q > kk) ? Lk[r0 + q] : (R)0;
+                    lr[q] = (ti > kt || q > kk) ? Lk[r0 + q] : (T)0;
                     wc[q] = vb[c0 + q];
                 }
 #pragma unroll
@@ -538,7 +564,7 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
     // W -> shared memory, row-major; tiles above the diagonal are zero
     for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
         int r = i / kBlk, c = i % kBlk;
-        if (r / kTile < c / kTile) buf[i] = (R)0;
+        if (r / kTile < c / kTile) buf[i] = (T)0;
     }
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
@@ -548,14 +574,15 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
     __syncthreads();
 
     // ---- B = s W^T W s; tile (ti, tj) needs rows k >= 6 ti of W only
+    if (pass == 0 && flags && threadIdx.x == 0) flags[b] = s_bad;
     if (!act) return;
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (R)0;
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (T)0;
     for (int k = r0; k < kBlk; ++k) {
-        const R* Wk = buf + k * kBlk;
-        R wr[kTile], wc[kTile];
+        const T* Wk = buf + k * kBlk;
+        T wr[kTile], wc[kTile];
 #pragma unroll
         for (int q = 0; q < kTile; ++q) {
             wr[q] = Wk[r0 + q];
@@ -572,7 +599,7 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D) {
 #pragma unroll
         for (int cc = 0; cc < kTile; ++cc) {
             int r = r0 + rr, c = c0 + cc;
-            R v = a[rr][cc] * sc[r] * sc[c];
+            R v = (R)(a[rr][cc] * sc[r] * sc[c]);
             dst[r * kBlk + c] = v;
             dst[c * kBlk + r] = v;
         }
@@ -765,6 +792,17 @@ __global__ void k_restrict_level(Dev<R> D, int l, const R* __restrict__ src) {
 // One CTA of 96 threads per block of any level.  Level 0 applies B_d to
 // [g_d, U_d] and the Woodbury correction; coarse levels apply M_l^-1 to the
 // restricted residual.
+__device__ __forceinline__ void unpack16(const float4& v, float e[4]) {
+    e[0] = v.x;
+    e[1] = v.y;
+    e[2] = v.z;
+    e[3] = v.w;
+}
+__device__ __forceinline__ void unpack16(const double2& v, double e[2]) {
+    e[0] = v.x;
+    e[1] = v.y;
+}
+
 template <class R>
 __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z,
                                                     ContactBuf C, int woodbury) {
@@ -815,27 +853,56 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
         }
     }
     __syncthreads();
-    // Y = B [rhs]: B symmetric, thread tid computes row tid reading row j of B
-    const R* Bp = D.blocks + (size_t)b * kBlk * kBlk;
-    R acc[1 + kMaxK];
+    // Y = B [rhs]; B is symmetric, so column c of Y is row c of B times rhs.
+    // 16-byte loads: thread tid owns W = 16 / sizeof(R) consecutive columns
+    // (column group tid % NCG) and the rows j = tid / NCG (mod NRG); the NRG
+    // row-group partial sums are then added in shared memory.
+    constexpr int W = 16 / (int)sizeof(R);
+    constexpr int NCG = kBlk / W, NRG = kBlk / NCG;
+    using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    const int cg = tid % NCG, rg = tid / NCG;
+    const V16* Bv = reinterpret_cast<const V16*>(D.blocks + (size_t)b * kBlk * kBlk) + cg;
+    R acc[1 + kMaxK][W];
 #pragma unroll
-    for (int a = 0; a < 1 + kMaxK; ++a) acc[a] = 0;
+    for (int a = 0; a < 1 + kMaxK; ++a)
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[a][w] = 0;
     if (ns == 0) {
 #pragma unroll 8
-        for (int j = 0; j < kBlk; ++j) acc[0] += Bp[j * kBlk + tid] * rhs[0][j];
+        for (int j = rg; j < kBlk; j += NRG) {
+            R e[W];
+            unpack16(Bv[(size_t)j * NCG], e);
+            const R r0 = rhs[0][j];
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc[0][w] += e[w] * r0;
+        }
     } else {
 #pragma unroll 4
-        for (int j = 0; j < kBlk; ++j) {
-            R bj = Bp[j * kBlk + tid];
+        for (int j = rg; j < kBlk; j += NRG) {
+            R e[W];
+            unpack16(Bv[(size_t)j * NCG], e);
 #pragma unroll
             for (int a = 0; a < 1 + kMaxK; ++a)
-                if (a <= ns) acc[a] += bj * rhs[a][j];
+                if (a <= ns) {
+                    const R ra = rhs[a][j];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) acc[a][w] += e[w] * ra;
+                }
         }
     }
 #pragma unroll
-    for (int a = 0; a < 1 + kMaxK; ++a)
-        if (a <= ns) Y[a][tid] = acc[a];
-    __syncthreads();
+    for (int q = 0; q < NRG; ++q) {
+        if (rg == q)
+#pragma unroll
+            for (int a = 0; a < 1 + kMaxK; ++a)
+                if (a <= ns)
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        R* y = &Y[a][W * cg + w];
+                        *y = q == 0 ? acc[a][w] : *y + acc[a][w];
+                    }
+        __syncthreads();
+    }
     R out = Y[0][tid];
     if (ns > 0) {
         // capacitance I + U^T W and r = U^T z_base, FP64 dot products per warp
@@ -904,7 +971,22 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
         __syncthreads();
         double o = (double)out;
         for (int a = 0; a < ns; ++a) o -= lam[a] * (double)Y[1 + a][tid];
-        out = (R)o;
+        // Adding U U^T can only lower the quadratic form: 0 <= g_d^T B~ g_d
+        // <= g_d^T B g_d. A corrected z_d outside that range (FP32 inverses
+        // of stiff blocks make the capacitance solve unstable) drops this
+        // subdomain's correction.
+        double gi = (double)rhs[0][tid];
+        double qb = warp_sum(gi * (double)Y[0][tid]), qc = warp_sum(gi * o);
+        __shared__ double qsum[2][3];
+        if ((tid & 31) == 0) {
+            qsum[0][tid >> 5] = qb;
+            qsum[1][tid >> 5] = qc;
+        }
+        __syncthreads();
+        qb = qsum[0][0] + qsum[0][1] + qsum[0][2];
+        qc = qsum[1][0] + qsum[1][1] + qsum[1][2];
+        const bool in_range = qc <= qb * (1.0 + 1e-3) && qc >= -1e-3 * qb;
+        out = in_range ? (R)o : Y[0][tid];
     }
     if (node >= 0) {
         if (l == 0)
@@ -960,21 +1042,33 @@ template <class R>
 void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
     int nb = D.blk_off[D.nlev];
     KL(k_clear_upd<R><<<1, 1, 0, st>>>(D));
-    cudaMemsetAsync(D.asmb, 0, sizeof(R) * (size_t)nb * kBlk * kBlk, st);
+    const int nb0 = D.nlev > 1 ? D.blk_off[1] : nb;
+    cudaMemsetAsync(D.asmb, 0, sizeof(double) * (size_t)nb0 * kBlk * kBlk, st);
+    if (nb > nb0) cudaMemsetAsync(D.asmbc, 0, sizeof(double) * (size_t)(nb - nb0) * kBlk * kBlk, st);
     KL(k_tet_hessian<R><<<nblk(D.nt, 64), 64, 0, st>>>(D, x));
     KL(k_assemble_tets<R><<<nblk(D.nt), kT, 0, st>>>(D));
     KL(k_assemble_mass<R><<<nblk(D.nv), kT, 0, st>>>(D));
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
-    // blocks are assembled and inverted in the bulk precision R: FP64 in the
-    // plain mode; FP32 in the mixed mode (B300's FP64 rate would make the
-    // inversion the most expensive step; it is not among the FP64 steps)
-    size_t smem = sizeof(R) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
+    // blocks are assembled in FP64; level-0 blocks are inverted in the bulk
+    // precision R (FP32 in the mixed mode: B300's FP64 rate would make the
+    // 1.5k-block inversion the most expensive step) with an FP64 redo of
+    // the blocks FP32 cannot carry; the few coarse Galerkin blocks in FP64
+    const size_t smem_r = sizeof(R) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
+    const size_t smem_d = sizeof(double) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_invert<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_invert<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
+        cudaFuncSetAttribute(k_invert<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
         attr_set = true;
     }
-    KL(k_invert<R><<<nb, kInvThreads, smem, st>>>(D));
+    if (sizeof(R) == 4) {
+        // FP32 first; blocks that floored a pivot again in FP64
+        KL(k_invert<R, R><<<nb0, kInvThreads, smem_r, st>>>(D, D.asmb, 0, D.invflag, 0));
+        KL(k_invert<R, double><<<nb0, kInvThreads, smem_d, st>>>(D, D.asmb, 0, D.invflag, 1));
+    } else {
+        KL(k_invert<R, R><<<nb0, kInvThreads, smem_r, st>>>(D, D.asmb, 0, nullptr, 0));
+    }
+    if (nb > nb0) KL(k_invert<R, double><<<nb - nb0, kInvThreads, smem_d, st>>>(D, D.asmbc, nb0, nullptr, 0));
     cudaMemsetAsync(D.bkeys, 0xFF, sizeof(unsigned long long) * D.btab, st);
     KL(k_snapshot<R><<<592, kT, 0, st>>>(D));
 }

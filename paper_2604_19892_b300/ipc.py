@@ -62,7 +62,8 @@ class IterRecord(C.Structure):
     _fields_ = [("restart", C.c_int), ("n_contacts", C.c_int), ("n_update", C.c_int), ("ls_halvings", C.c_int),
                 ("mu", C.c_double), ("nu", C.c_double), ("gz", C.c_double), ("znorm", C.c_double),
                 ("energy_before", C.c_double), ("energy_after", C.c_double), ("alpha_min", C.c_double),
-                ("alpha_max", C.c_double), ("r", C.c_double)]
+                ("alpha_max", C.c_double), ("r", C.c_double), ("pmax", C.c_double), ("ccd_passes", C.c_int),
+                ("cached_pairs", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -91,6 +92,8 @@ EXPORTS = {
     "ipc_eval_forms": (C.c_int, [C.c_void_p, _D, _D, _D, _D, _D, C.c_void_p]),
     "ipc_eval_ccd": (C.c_int, [C.c_void_p, _D, _D, _D, _I, _D, _I, C.c_void_p]),
     "ipc_precond_apply_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ipc_profile_replay": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                     C.POINTER(C.c_double)]),
     "ipc_last_error": (C.c_char_p, []),
     "ipc_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ipc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
@@ -354,6 +357,17 @@ class Scene:
         _check(self.lib.ipc_eval_precond(self.h, _dp(xb), _dp(xc) if xc is not None else None, _dp(g), _dp(z),
                                          _stream_handle(self.stream)))
         return z
+
+    def profile_replay(self, stage: int, reps: int, flush=None, stream=None) -> float:
+        """Mean device ms of one stage's kernels replayed on the current state
+        (2 = MAS block apply, 3 = H~ quadratic forms); `flush` is a CUDA
+        tensor overwritten before each replay to evict L2."""
+        ms = C.c_double()
+        fp = C.c_void_p(flush.data_ptr()) if flush is not None else None
+        fb = flush.numel() * flush.element_size() if flush is not None else 0
+        _check(self.lib.ipc_profile_replay(self.h, int(stage), int(reps), fp, fb, _stream_handle(stream or self.stream),
+                                           C.byref(ms)))
+        return ms.value
 
     def precond_apply_noalloc(self, g_dev, z_dev, stream=None):
         """z = P_base g on device tensors of shape (nv, 3) in the scene's bulk
