@@ -298,7 +298,7 @@ int setup_dev(ipc_scene* s) {
     D.blocks = A.arr<R>((size_t)nb * kBlk * kBlk);
     const int nb0 = m.nlev > 1 ? D.blk_off[1] : nb;
     D.asmb = A.arr<double>((size_t)nb0 * kBlk * kBlk);
-    D.invflag = A.arr<int>(std::max(nb0, 1));
+    D.invflag = A.arr<int>(std::max(nb, 1));
     D.asmbc = A.arr<double>((size_t)std::max(nb - nb0, 1) * kBlk * kBlk);
     D.coarse_r = A.arr<R>(std::max(coff, 1));
     D.coarse_y = A.arr<R>(std::max(coff, 1));

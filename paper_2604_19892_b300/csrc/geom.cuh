@@ -107,6 +107,98 @@ __device__ inline double ee_closest(d3 p1, d3 q1, d3 p2, d3 q2, double& s, doubl
     return dot(dd, dd);
 }
 
+// ---- FP32 prefilter: a conservative lower bound on a pair's distance.
+// Positions enter as FP64 differences from the pair's first vertex (so large
+// coordinates keep their relative accuracy), the closest-point computation
+// runs in FP32, and the bound subtracts a margin far above FP32 rounding.
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 fsub(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ float fdot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 fmad3(f3 a, float t, f3 b) { return {a.x + t * b.x, a.y + t * b.y, a.z + t * b.z}; }
+__device__ __forceinline__ float fclamp01(float t) { return fminf(fmaxf(t, 0.f), 1.f); }
+
+__device__ inline float pt_dist2_f(f3 p, f3 a, f3 b, f3 c) {
+    f3 ab = fsub(b, a), ac = fsub(c, a), ap = fsub(p, a);
+    float d1 = fdot(ab, ap), d2 = fdot(ac, ap);
+    if (d1 <= 0.f && d2 <= 0.f) return fdot(ap, ap);
+    f3 bp = fsub(p, b);
+    float d3v = fdot(ab, bp), d4 = fdot(ac, bp);
+    if (d3v >= 0.f && d4 <= d3v) return fdot(bp, bp);
+    float vc = d1 * d4 - d3v * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3v <= 0.f) {
+        f3 r = fsub(p, fmad3(a, d1 / (d1 - d3v), ab));
+        return fdot(r, r);
+    }
+    f3 cp = fsub(p, c);
+    float d5 = fdot(ab, cp), d6 = fdot(ac, cp);
+    if (d6 >= 0.f && d5 <= d6) return fdot(cp, cp);
+    float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        f3 r = fsub(p, fmad3(a, d2 / (d2 - d6), ac));
+        return fdot(r, r);
+    }
+    float va = d3v * d6 - d5 * d4;
+    if (va <= 0.f && (d4 - d3v) >= 0.f && (d5 - d6) >= 0.f) {
+        f3 r = fsub(p, fmad3(b, (d4 - d3v) / ((d4 - d3v) + (d5 - d6)), fsub(c, b)));
+        return fdot(r, r);
+    }
+    float den = 1.f / (va + vb + vc);
+    f3 q = fmad3(fmad3(a, vb * den, ab), vc * den, ac);
+    f3 r = fsub(p, q);
+    return fdot(r, r);
+}
+
+__device__ inline float ee_dist2_f(f3 p1, f3 q1, f3 p2, f3 q2) {
+    f3 d1 = fsub(q1, p1), d2 = fsub(q2, p2), r = fsub(p1, p2);
+    float a = fdot(d1, d1), e = fdot(d2, d2), f = fdot(d2, r);
+    float s, t;
+    const float tiny = 1e-30f;
+    if (a <= tiny && e <= tiny) {
+        s = t = 0.f;
+    } else if (a <= tiny) {
+        s = 0.f;
+        t = fclamp01(f / e);
+    } else {
+        float c = fdot(d1, r);
+        if (e <= tiny) {
+            t = 0.f;
+            s = fclamp01(-c / a);
+        } else {
+            float b = fdot(d1, d2);
+            float den = a * e - b * b;
+            s = den > 0.f ? fclamp01((b * f - c * e) / den) : 0.f;
+            t = (b * s + f) / e;
+            if (t < 0.f) {
+                t = 0.f;
+                s = fclamp01(-c / a);
+            } else if (t > 1.f) {
+                t = 1.f;
+                s = fclamp01((b - c) / a);
+            }
+        }
+    }
+    f3 dd = fsub(fmad3(p1, s, d1), fmad3(p2, t, d2));
+    return fdot(dd, dd);
+}
+
+// lower bound on the distance of pair v (PT: p, t0, t1, t2; EE: a0, a1, b0,
+// b1) at positions x
+__device__ inline float pair_dist_lb(int kind, const int v[4], const double* x) {
+    const double o0 = x[3 * v[0]], o1 = x[3 * v[0] + 1], o2 = x[3 * v[0] + 2];
+    f3 P[4];
+    float L = 0.f;
+    for (int j = 0; j < 4; ++j) {
+        P[j] = {(float)(x[3 * v[j]] - o0), (float)(x[3 * v[j] + 1] - o1), (float)(x[3 * v[j] + 2] - o2)};
+        L = fmaxf(L, fmaxf(fabsf(P[j].x), fmaxf(fabsf(P[j].y), fabsf(P[j].z))));
+    }
+    float d2 = kind == 0 ? pt_dist2_f(P[0], P[1], P[2], P[3]) : ee_dist2_f(P[0], P[1], P[2], P[3]);
+    float m = d2 - 1e-6f * L * L;
+    if (!(m > 0.f)) return 0.f;
+    return 0.999f * sqrtf(m);
+}
+
 // f(t) = det[A + t dA, B + t dB, C + t dC] = c[0] + c[1] t + c[2] t^2 + c[3] t^3
 __device__ inline void cubic_of(d3 A, d3 dA, d3 B, d3 dB, d3 C, d3 dC, double c[4]) {
     d3 BC = cross(B, C);

@@ -200,6 +200,10 @@ template <class R>
 __device__ void pt_try(const Dev<R>& D, const double* x, const ContactBuf& C, int pv, int f) {
     int t0 = D.sf[3 * f], t1 = D.sf[3 * f + 1], t2 = D.sf[3 * f + 2];
     if (pv == t0 || pv == t1 || pv == t2) return;
+    {
+        const int v[4] = {pv, t0, t1, t2};
+        if (pair_dist_lb(0, v, x) >= D.dhat) return;  // FP32 prefilter
+    }
     d3 P = ld3(x + 3 * pv), A = ld3(x + 3 * t0), B = ld3(x + 3 * t1), Cc = ld3(x + 3 * t2);
     double w[3];
     double d2 = pt_closest(P, A, B, Cc, w);
@@ -216,6 +220,10 @@ template <class R>
 __device__ void ee_try(const Dev<R>& D, const double* x, const ContactBuf& C, int i, int j) {
     int a0 = D.se[2 * i], a1 = D.se[2 * i + 1], b0 = D.se[2 * j], b1 = D.se[2 * j + 1];
     if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
+    {
+        const int v[4] = {a0, a1, b0, b1};
+        if (pair_dist_lb(1, v, x) >= D.dhat) return;  // FP32 prefilter
+    }
     d3 A0 = ld3(x + 3 * a0), A1 = ld3(x + 3 * a1), B0 = ld3(x + 3 * b0), B1 = ld3(x + 3 * b1);
     d3 u = A1 - A0, v = B1 - B0;
     d3 cr = cross(u, v);
@@ -390,6 +398,23 @@ __device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const do
 
 template <class R>
 __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
+    // A pair whose distance exceeds any relative displacement the step can
+    // make, with every vertex scaled anywhere in [0, 1], keeps alpha = 1 and
+    // can never be violated by mixed per-subdomain steps: it is skipped
+    // (FP32 lower bound on d0, sum of the two primitives' largest |p|).
+    {
+        float pa = 0.f, pb = 0.f;
+        for (int j = 0; j < 4; ++j) {
+            const R* q = D.p + 3 * v[j];
+            float m = sqrtf((float)q[0] * (float)q[0] + (float)q[1] * (float)q[1] + (float)q[2] * (float)q[2]);
+            if ((kind == 0 && j == 0) || (kind == 1 && j < 2))
+                pa = fmaxf(pa, m);
+            else
+                pb = fmaxf(pb, m);
+        }
+        float lmix = 1.001f * (pa + pb);
+        if (pair_dist_lb(kind, v, D.x) * (1.f - (float)D.ccd_shrink) > lmix) return;
+    }
     double a = pair_alpha(D, kind, v, D.x, D.p, nullptr);
     int g0 = D.grp0[v[0]], g1 = D.grp0[v[1]], g2 = D.grp0[v[2]], g3 = D.grp0[v[3]];
     int b0 = D.body[v[0]], b1 = D.body[v[1]], b2 = D.body[v[2]], b3 = D.body[v[3]];

@@ -409,13 +409,13 @@ constexpr int kInvThreads = 160;
 static_assert(kNT * kTile == kBlk, "tile size must divide the block size");
 static_assert(kInvThreads >= kNTiles && kInvThreads % 32 == 0, "one thread per lower tile");
 
-// flags (level-0 blocks): pass 0 (T = float) marks a block whose
-// factorisation floored or raised a pivot, i.e. whose conditioning FP32
-// cannot carry (very stiff contacts); pass 1 (T = double) re-inverts only
-// the marked blocks from the same FP64 assembly. flags == nullptr: no marks.
+// Blocks come from the FP64 assembly (level 0: asmb, coarse levels: asmbc).
+// flags: pass 0 (T = float) marks a block whose factorisation floored or
+// raised a pivot, i.e. whose conditioning FP32 cannot carry (very stiff
+// contacts, coarse aggregates); pass 1 (T = double) re-inverts only the
+// marked blocks. flags == nullptr: no marks.
 template <class R, class T>
-__global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, const double* __restrict__ srcbase, int b0,
-                                                       int* flags, int pass) {
+__global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, int pass) {
     extern __shared__ unsigned char smem_raw[];
     T* buf = reinterpret_cast<T*>(smem_raw);      // 96 x 96: L^T, then W
     T* vec = buf + kBlk * kBlk;                   // 2 x 96 broadcast
@@ -423,13 +423,14 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, const double* 
     T* pm = sc + kBlk;                            // 2 x 16 column maxima of L_rk^2
     __shared__ int s_bad;
     const T eps_piv = (T)(sizeof(T) == 8 ? 1e-12 : 1e-6);
-    int b = b0 + blockIdx.x;
+    int b = blockIdx.x;
     if (pass == 1 && !flags[b]) return;  // uniform over the CTA
     int l = 0;
     while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
     int grp = b - D.blk_off[l];
     const int* mem = D.members[l] + (size_t)grp * kSub;
-    const double* src = srcbase + (size_t)(b - b0) * kBlk * kBlk;
+    const double* src = l == 0 ? D.asmb + (size_t)b * kBlk * kBlk
+                               : D.asmbc + (size_t)(b - D.blk_off[1]) * kBlk * kBlk;
     if (threadIdx.x == 0) s_bad = 0;
     for (int r = threadIdx.x; r < kBlk; r += blockDim.x) {
         double d = src[r * kBlk + r];
@@ -1049,10 +1050,10 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
     KL(k_assemble_tets<R><<<nblk(D.nt), kT, 0, st>>>(D));
     KL(k_assemble_mass<R><<<nblk(D.nv), kT, 0, st>>>(D));
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
-    // blocks are assembled in FP64; level-0 blocks are inverted in the bulk
-    // precision R (FP32 in the mixed mode: B300's FP64 rate would make the
-    // 1.5k-block inversion the most expensive step) with an FP64 redo of
-    // the blocks FP32 cannot carry; the few coarse Galerkin blocks in FP64
+    // blocks are assembled in FP64 and inverted in the bulk precision R (FP32
+    // in the mixed mode: B300's FP64 rate, about two FMAs per clock per SM,
+    // would make the inversion the most expensive step) with an FP64 redo of
+    // the blocks FP32 cannot carry
     const size_t smem_r = sizeof(R) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
     const size_t smem_d = sizeof(double) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
     static bool attr_set = false;
@@ -1062,13 +1063,12 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
         attr_set = true;
     }
     if (sizeof(R) == 4) {
-        // FP32 first; blocks that floored a pivot again in FP64
-        KL(k_invert<R, R><<<nb0, kInvThreads, smem_r, st>>>(D, D.asmb, 0, D.invflag, 0));
-        KL(k_invert<R, double><<<nb0, kInvThreads, smem_d, st>>>(D, D.asmb, 0, D.invflag, 1));
+        // FP32 first; the blocks that floored or raised a pivot again in FP64
+        KL(k_invert<R, R><<<nb, kInvThreads, smem_r, st>>>(D, D.invflag, 0));
+        KL(k_invert<R, double><<<nb, kInvThreads, smem_d, st>>>(D, D.invflag, 1));
     } else {
-        KL(k_invert<R, R><<<nb0, kInvThreads, smem_r, st>>>(D, D.asmb, 0, nullptr, 0));
+        KL(k_invert<R, R><<<nb, kInvThreads, smem_r, st>>>(D, nullptr, 0));
     }
-    if (nb > nb0) KL(k_invert<R, double><<<nb - nb0, kInvThreads, smem_d, st>>>(D, D.asmbc, nb0, nullptr, 0));
     cudaMemsetAsync(D.bkeys, 0xFF, sizeof(unsigned long long) * D.btab, st);
     KL(k_snapshot<R><<<592, kT, 0, st>>>(D));
 }
