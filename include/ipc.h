@@ -201,7 +201,8 @@ int ipc_profile_read(ipc_scene* s, ipc_profile* out);
 /* Replays the kernels of one stage on the scene's current state `reps`
  * times and returns their mean device time in *ms_mean: stage 2 = MAS block
  * apply of level-0 and coarse blocks to the scene's gradient (no Woodbury
- * patch), stage 3 = the H~ quadratic forms (Eq. 6) of the scene's z and p.
+ * patch), stage 3 = the H~ quadratic forms (Eq. 6) of the scene's z and p
+ * (the reduction kernel; the packing of z and p before it is not timed).
  * Before each replay, if flush != NULL, flush_bytes of that caller-owned
  * device buffer (16-byte aligned) are read, which evicts the stage's data
  * from L2 without leaving dirty lines; the timed region is a CUDA

@@ -53,6 +53,7 @@ struct Scalars {
     int n_straddle;                // straddling CCD candidates
     int overflow;                  // bit flags: 1 contacts, 2 straddle, 4 upd
     int nan_flag;
+    int async_timeout;             // a bounded wait on an asynchronous copy ran out
     int nonpos;                    // a contact of the last detection has d <= 0
     // first block apply with a non-finite result: block, updates used,
     // max |rhs| (g and U columns), max |Y|, max |lambda|, max dS
@@ -72,6 +73,12 @@ struct ContactBuf {
     double* bp;                    // kappa b'(d)
     double* r;                     // 3 per contact: unit direction (p - c)/d or plane normal
     double* w;                     // 4 per contact: grad d = (w_j r) per vertex
+};
+
+// four values of one vertex vector, one aligned 16-byte (FP32) load
+template <class R>
+struct alignas(4 * sizeof(R)) V4 {
+    R x, y, z, w;
 };
 
 template <class R>
@@ -109,6 +116,7 @@ struct Dev {
     // state
     double *x, *xt, *xs, *xtry, *v;
     R *g, *gtry, *z, *zprev, *p;
+    R* zp4;                                // [nv][2][4]: z and p packed for the forms gathers
     R* hess;                               // [ntp][45][32]
     R* blocks;                             // nblocks * 96 * 96
     double* asmb;                          // level-0 assembly buffer (FP64)

@@ -40,24 +40,69 @@ __device__ __forceinline__ void rank1_dots(const int4 q, int type, const double*
     }
 }
 
+// z and p of each vertex packed into two 4-wide vectors (zp4[2v] = z,
+// zp4[2v+1] = p, w = 0), so the per-tet gathers of the forms are two 16-byte
+// loads per vertex; thread 0 also zeroes the iteration's reduction scalars.
+template <class R>
+__global__ void k_pack_zp(Dev<R> D, int restart) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v == 0) {
+        Scalars* S = D.S;
+        S->gz = S->gp = S->gzprev = 0.0;
+        S->zHz = S->zHp = S->pHp = 0.0;
+        S->znorm = 0.0;
+        S->pmax = 0.0;
+        S->maxdisp = 0.0;
+    }
+    if (v >= D.nv) return;
+    V4<R>* o = reinterpret_cast<V4<R>*>(D.zp4) + 2 * v;
+    o[0] = {D.z[3 * v], D.z[3 * v + 1], D.z[3 * v + 2], (R)0};
+    if (restart)
+        o[1] = {(R)0, (R)0, (R)0, (R)0};
+    else
+        o[1] = {D.p[3 * v], D.p[3 * v + 1], D.p[3 * v + 2], (R)0};
+}
+
 // One pass for all reductions of an iteration. Thread i takes tet i (the
 // stored projected Hessian: (G_t z)^T K_t (G_t p) and the like), vertex i
 // (g.z, g.p, g.z_prev, mass terms, |z_v|), and, grid-stride, the C_base
-// rank-1 terms and the classified updates. Per-thread values are in the
-// bulk precision R (contact terms in FP64); each warp sums in R, the warps'
-// partials are summed in FP64 with one atomic per block and value.
+// rank-1 terms and the classified updates. Values are summed in the bulk
+// precision R within a block (contact terms formed in FP64), the block
+// totals in FP64 across blocks.
 template <class R>
-__global__ void __launch_bounds__(256) k_forms_all(Dev<R> D, ContactBuf C, int restart) {
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_forms_all(Dev<R> D, ContactBuf C, int restart) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
     R zz = 0, zp = 0, pp = 0, gz = 0, gp = 0, gzp = 0, zn = 0;
-    if (i < D.nt) {
-        int4 q = D.tets[i];
+    for (int t = i; t < D.nt; t += nth) {
+        // all 45 + 9 coalesced packet loads issued before the gathers
+        const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
+        R hv[kH];
+#pragma unroll
+        for (int k = 0; k < kH; ++k) hv[k] = hp[k * kPack];
+        int4 q = D.tets[t];
         int vid[4] = {q.x, q.y, q.z, q.w};
-        const R* Bb = D.tetB + (size_t)(i / kPack) * 9 * kPack + (i % kPack);
+        const R* Bb = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
         R B[3][3];
 #pragma unroll
         for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = Bb[c * kPack];
+        const V4<R>* zpk = reinterpret_cast<const V4<R>*>(D.zp4);
+        V4<R> zv[4], pv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            zv[j] = zpk[2 * vid[j]];
+            pv[j] = zpk[2 * vid[j] + 1];
+        }
+        R ez[3][3], ep[3][3];  // edge vectors x_j - x_0 of z and p
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            ez[j][0] = zv[j + 1].x - zv[0].x;
+            ez[j][1] = zv[j + 1].y - zv[0].y;
+            ez[j][2] = zv[j + 1].z - zv[0].z;
+            ep[j][0] = pv[j + 1].x - pv[0].x;
+            ep[j][1] = pv[j + 1].y - pv[0].y;
+            ep[j][2] = pv[j + 1].z - pv[0].z;
+        }
         R dz[9], dp[9];  // vec(dF), column-major
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -66,13 +111,12 @@ __global__ void __launch_bounds__(256) k_forms_all(Dev<R> D, ContactBuf C, int r
                 R sz = 0, sp = 0;
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    sz += (D.z[3 * vid[j + 1] + r] - D.z[3 * vid[0] + r]) * B[j][c];
-                    if (!restart) sp += (D.p[3 * vid[j + 1] + r] - D.p[3 * vid[0] + r]) * B[j][c];
+                    sz += ez[j][r] * B[j][c];
+                    sp += ep[j][r] * B[j][c];
                 }
                 dz[3 * c + r] = sz;
                 dp[3 * c + r] = sp;
             }
-        const R* hp = D.hess + (size_t)(i / kPack) * kH * kPack + (i % kPack);
         R Hz[9], Hp[9];
 #pragma unroll
         for (int a = 0; a < 9; ++a) Hz[a] = Hp[a] = 0;
@@ -80,7 +124,7 @@ __global__ void __launch_bounds__(256) k_forms_all(Dev<R> D, ContactBuf C, int r
         for (int a = 0; a < 9; ++a)
 #pragma unroll
             for (int b = a; b < 9; ++b) {
-                R h = hp[pk(a, b) * kPack];
+                R h = hv[pk(a, b)];
                 Hz[a] += h * dz[b];
                 Hp[a] += h * dp[b];
                 if (b != a) {
@@ -95,12 +139,12 @@ __global__ void __launch_bounds__(256) k_forms_all(Dev<R> D, ContactBuf C, int r
             pp += dp[a] * Hp[a];
         }
     }
-    if (i < D.nv) {
-        const R m = D.mass[i];
+    for (int v = i; v < D.nv; v += nth) {
+        const R m = D.mass[v];
         R zsq = 0;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            R gi = D.g[3 * i + r], zi = D.z[3 * i + r], pi = restart ? (R)0 : D.p[3 * i + r], zpi = D.zprev[3 * i + r];
+            R gi = D.g[3 * v + r], zi = D.z[3 * v + r], pi = restart ? (R)0 : D.p[3 * v + r], zpi = D.zprev[3 * v + r];
             gz += gi * zi;
             gp += gi * pi;
             gzp += gi * zpi;
@@ -109,17 +153,17 @@ __global__ void __launch_bounds__(256) k_forms_all(Dev<R> D, ContactBuf C, int r
             pp += m * pi * pi;
             zsq += zi * zi;
         }
-        zn = sqrt(zsq);
+        zn = fmax(zn, sqrt(zsq));
     }
-    double czz = 0, czp = 0, cpp = 0;
+    // rank-1 terms (few threads): FP64 per contact, added in R
     const int nb = min(*D.Cb.count, D.cap);
     for (int c = i; c < nb; c += nth) {
         double nz, np;
         rank1_dots(D.Cb.v[c], D.Cb.type[c], D.Cb.r + 3 * c, D.Cb.w + 4 * c, D.z, D.p, !restart, nz, np);
         double k = D.Cb.k[c];
-        czz += k * nz * nz;
-        czp += k * nz * np;
-        cpp += k * np * np;
+        zz += (R)(k * nz * nz);
+        zp += (R)(k * nz * np);
+        pp += (R)(k * np * np);
     }
     const int nu = min(D.S->n_upd, D.upd_cap);
     for (int u = i; u < nu; u += nth) {
@@ -127,47 +171,36 @@ __global__ void __launch_bounds__(256) k_forms_all(Dev<R> D, ContactBuf C, int r
         double nz, np;
         rank1_dots(C.v[c], C.type[c], C.r + 3 * c, C.w + 4 * c, D.z, D.p, !restart, nz, np);
         double sd = D.upd_dS[u];
-        czz += sd * nz * nz;
-        czp += sd * nz * np;
-        cpp += sd * np * np;
+        zz += (R)(sd * nz * nz);
+        zp += (R)(sd * nz * np);
+        pp += (R)(sd * np * np);
     }
-    // warp sums: bulk terms in R, contact terms in FP64 (zero in most warps)
-    zz = warp_sum(zz);
-    zp = warp_sum(zp);
-    pp = warp_sum(pp);
-    gz = warp_sum(gz);
-    gp = warp_sum(gp);
-    gzp = warp_sum(gzp);
+    // warp and block sums in R (B300's FP64 pipe is too narrow even for
+    // per-warp scalar work), one FP64 atomic per block and value
+    R t[6] = {zz, zp, pp, gz, gp, gzp};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t[k] = warp_sum(t[k]);
     zn = warp_max(zn);
-    const bool any_c = __any_sync(0xffffffffu, czz != 0.0 || czp != 0.0 || cpp != 0.0);
-    if (any_c) {
-        czz = warp_sum(czz);
-        czp = warp_sum(czp);
-        cpp = warp_sum(cpp);
-    }
-    __shared__ double sh[6][32];
+    __shared__ R sh[7][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
-        sh[0][w] = (double)zz + czz;
-        sh[1][w] = (double)zp + czp;
-        sh[2][w] = (double)pp + cpp;
-        sh[3][w] = (double)gz;
-        sh[4][w] = (double)gp;
-        sh[5][w] = (double)gzp;
-        if (zn > (R)0) atomicMaxPos(&D.S->znorm, (double)zn);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sh[k][w] = t[k];
+        sh[6][w] = zn;
     }
     __syncthreads();
     if (w == 0) {
         const int nw = blockDim.x >> 5;
-        double t[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) t[k] = warp_sum(lane < nw ? sh[k][lane] : 0.0);
+        for (int k = 0; k < 6; ++k) t[k] = warp_sum(lane < nw ? sh[k][lane] : (R)0);
+        R m = warp_max(lane < nw ? sh[6][lane] : (R)0);
         if (lane == 0) {
             Scalars* S = D.S;
             double* dst[6] = {&S->zHz, &S->zHp, &S->pHp, &S->gz, &S->gp, &S->gzprev};
 #pragma unroll
             for (int k = 0; k < 6; ++k)
-                if (t[k] != 0.0) atomicAdd(dst[k], t[k]);
+                if (t[k] != (R)0) atomicAdd(dst[k], (double)t[k]);
+            if (m > (R)0) atomicMaxPos(&S->znorm, (double)m);
         }
     }
 }
@@ -215,20 +248,23 @@ __global__ void k_direction(Dev<R> D, int restart) {
         D.S->mu = mu;
         D.S->nu = nu;
     }
-    double pm = 0.0, dm = 0.0;
+    // per vertex in the bulk precision R; |p| and the drift are rounded up
+    // by a relative 1e-6 so that the FP32 bounds stay upper bounds
+    const R mur = (R)(-mu), nur = (R)nu;
+    R pm = 0, dm = 0;
     if (v < D.nv) {
-        double s = 0.0;
+        R s = 0;
         for (int r = 0; r < 3; ++r) {
-            double pv = restart ? 0.0 : (double)D.p[3 * v + r];
-            double pn = -mu * (double)D.z[3 * v + r] + nu * pv;
-            D.p[3 * v + r] = (R)pn;
+            R pv = restart ? (R)0 : D.p[3 * v + r];
+            R pn = mur * D.z[3 * v + r] + nur * pv;
+            D.p[3 * v + r] = pn;
             s += pn * pn;
         }
         pm = sqrt(s);
         if (D.xref) {
-            double q = 0.0;
+            R q = 0;
             for (int r = 0; r < 3; ++r) {
-                double e = D.x[3 * v + r] - D.xref[3 * v + r];
+                R e = (R)(D.x[3 * v + r] - D.xref[3 * v + r]);
                 q += e * e;
             }
             dm = sqrt(q);
@@ -236,17 +272,26 @@ __global__ void k_direction(Dev<R> D, int restart) {
     }
     pm = warp_max(pm);
     dm = warp_max(dm);
-    if ((threadIdx.x & 31) == 0 && pm > 0.0) atomicMaxPos(&D.S->pmax, pm);
-    if ((threadIdx.x & 31) == 0 && dm > 0.0) atomicMaxPos(&D.S->maxdisp, dm);
+    if ((threadIdx.x & 31) == 0 && pm > (R)0) atomicMaxPos(&D.S->pmax, (1.0 + 1e-6) * (double)pm);
+    if ((threadIdx.x & 31) == 0 && dm > (R)0) atomicMaxPos(&D.S->maxdisp, (1.0 + 1e-6) * (double)dm);
 }
 
 }  // namespace
 
 template <class R>
+void launch_forms_prep(const Dev<R>& D, bool restart, cudaStream_t st) {
+    KL(k_pack_zp<R><<<nblk(std::max(D.nv, 1)), kT, 0, st>>>(D, restart ? 1 : 0));
+}
+
+template <class R>
+void launch_forms_main(const Dev<R>& D, const ContactBuf& C, bool restart, cudaStream_t st) {
+    KL(k_forms_all<R><<<nblk(std::max(std::max(D.nt, D.nv), 1)), kT, 0, st>>>(D, C, restart ? 1 : 0));
+}
+
+template <class R>
 void launch_forms(const Dev<R>& D, const ContactBuf& C, bool restart, cudaStream_t st) {
-    int rs = restart ? 1 : 0;
-    launch_zero_scalars(D, st);
-    KL(k_forms_all<R><<<nblk(std::max(std::max(D.nt, D.nv), 1)), kT, 0, st>>>(D, C, rs));
+    launch_forms_prep(D, restart, st);
+    launch_forms_main(D, C, restart, st);
 }
 
 template <class R>
@@ -257,6 +302,8 @@ void launch_direction(const Dev<R>& D, bool restart, cudaStream_t st) {
 
 #define INST(R)                                                                            \
     template void launch_forms<R>(const Dev<R>&, const ContactBuf&, bool, cudaStream_t); \
+    template void launch_forms_prep<R>(const Dev<R>&, bool, cudaStream_t);                \
+    template void launch_forms_main<R>(const Dev<R>&, const ContactBuf&, bool, cudaStream_t); \
     template void launch_direction<R>(const Dev<R>&, bool, cudaStream_t);
 INST(double)
 INST(float)

@@ -23,6 +23,7 @@
 // corrects z_d = B g_d - W lambda (Eq. 7).  Coarse levels stay frozen (Eq. 8).
 #include <type_traits>
 
+#include "bulk.cuh"
 #include "kernels.h"
 
 namespace ipcb {
@@ -804,6 +805,63 @@ __device__ __forceinline__ void unpack16(const double2& v, double e[2]) {
     e[1] = v.y;
 }
 
+// Block apply without Woodbury updates (restart iterations, coarse levels):
+// y_b = B_b r_b, one CTA of 96 threads per block. The whole 96 x 96 block
+// (36.9 KB in FP32) streams into shared memory as one bulk copy
+// (cp.async.bulk, completing on an mbarrier) while the CTA gathers r_b;
+// thread c then forms y_c = sum_j B_jc r_j from shared memory (B is
+// symmetric, column reads are conflict-free).
+template <class R>
+__global__ void __launch_bounds__(96) k_block_apply_plain(Dev<R> D, const R* __restrict__ g, R* __restrict__ z) {
+    extern __shared__ __align__(128) unsigned char bsm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ R rhs[kBlk];
+    const R* Bs = reinterpret_cast<const R*>(bsm);
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x;
+    constexpr uint32_t kBytes = kBlk * kBlk * sizeof(R);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, kBytes);
+        bulk_g2s(bsm, D.blocks + (size_t)b * kBlk * kBlk, kBytes, &bar);
+    }
+    int l = 0;
+    while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
+    const int grp = b - D.blk_off[l];
+    const int node = D.members[l][(size_t)grp * kSub + tid / 3];
+    const int comp = tid % 3;
+    if (l == 0)
+        rhs[tid] = node >= 0 ? g[3 * node + comp] : (R)0;
+    else
+        rhs[tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : (R)0;
+    __syncthreads();  // rhs complete; the barrier's initialisation is visible
+    const bool arrived = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!arrived)) {
+        // record, wait (bounded) for the copy in flight, leave z unwritten
+        if (tid == 0) {
+            D.S->async_timeout = 1;
+            mbar_wait(&bar, 0);
+        }
+        return;
+    }
+    R acc0 = 0, acc1 = 0;
+#pragma unroll 8
+    for (int j = 0; j < kBlk; j += 2) {
+        acc0 += Bs[j * kBlk + tid] * rhs[j];
+        acc1 += Bs[(j + 1) * kBlk + tid] * rhs[j + 1];
+    }
+    const R out = acc0 + acc1;
+    if (node >= 0) {
+        if (l == 0)
+            z[3 * node + comp] = out;
+        else
+            D.coarse_y[D.coarse_off[l] + 3 * node + comp] = out;
+    }
+    double od = (double)out;
+    if (!(od - od == 0.0)) atomicCAS(&D.S->dbg_block, -1, b);
+}
+
 template <class R>
 __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z,
                                                     ContactBuf C, int woodbury) {
@@ -1095,7 +1153,16 @@ void launch_restrict(const Dev<R>& D, const R* g, cudaStream_t st) {
 
 template <class R>
 void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool woodbury, cudaStream_t st) {
-    KL(k_block_apply<R><<<D.blk_off[D.nlev], 96, 0, st>>>(D, g, z, C, woodbury ? 1 : 0));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_block_apply_plain<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kBlk * kBlk * sizeof(R)));
+        attr = true;
+    }
+    if (woodbury)
+        KL(k_block_apply<R><<<D.blk_off[D.nlev], 96, 0, st>>>(D, g, z, C, 1));
+    else
+        KL(k_block_apply_plain<R><<<D.blk_off[D.nlev], 96, kBlk * kBlk * sizeof(R), st>>>(D, g, z));
 }
 
 template <class R>

@@ -35,6 +35,10 @@ template <class R> void launch_blocks(const Dev<R>& D, const R* g, R* z, const C
 template <class R> void launch_prolong(const Dev<R>& D, R* z, cudaStream_t st);
 // reductions for the 2x2 system (supplement Eq. 13-19), r_k and |z|_inf
 template <class R> void launch_forms(const Dev<R>& D, const ContactBuf& C, bool restart, cudaStream_t st);
+// the two halves of launch_forms: packing z, p and zeroing the sums; the
+// reduction kernel itself
+template <class R> void launch_forms_prep(const Dev<R>& D, bool restart, cudaStream_t st);
+template <class R> void launch_forms_main(const Dev<R>& D, const ContactBuf& C, bool restart, cudaStream_t st);
 // (mu, nu) and p <- -mu z + nu p
 template <class R> void launch_direction(const Dev<R>& D, bool restart, cudaStream_t st);
 // per-subdomain step sizes for p at x with verification (supplement Sec. 3)

@@ -157,6 +157,21 @@ def test_forms_parity(lib, name):
         np.testing.assert_allclose(fg, fo, rtol=1e-10)
 
 
+@pytest.mark.parametrize("name", list(SCENES))
+def test_forms_fp32(lib, name):
+    """FP32 bulk: the quadratic forms come from the bulk-copy staged tet pass
+    (FP32 per-tet products, FP32 block sums, FP64 across blocks)."""
+    sc = SCENES[name]
+    g, o = _pair(lib, sc, precision=1)
+    xb = contact_state(sc, 0.9)
+    xc = contact_state(sc, 0.4)
+    z, p = RNG.normal(size=(2,) + xb.shape)
+    for cur in (None, xc):
+        fg = g.hess_forms(xb, z, p, cur)
+        fo = o.hess_forms(xb, z, p, cur)
+        np.testing.assert_allclose(fg, fo, rtol=2e-5)
+
+
 @pytest.mark.parametrize("bp", [1, 2])  # hashed grid, cached candidate lists
 @pytest.mark.parametrize("name", list(SCENES))
 def test_ccd_parity(lib, name, bp):
