@@ -89,6 +89,7 @@ def _lib_handle():
             "o_precond_apply": (None, [C.c_void_p, _D, _D, _D, _D]),
             "o_hess_forms": (None, [C.c_void_p, _D, _D, _D, _D, _D]),
             "o_cubic_safe": (C.c_double, [_D, C.c_double]),
+            "o_pair_safe": (C.c_double, [C.c_int, _D, _D, C.c_double, C.c_double]),
             "o_safe_bisect": (C.c_double, [_D, C.c_double, C.c_double, C.c_double, C.c_double]),
             "o_pt_cubic": (None, [_D, _D, _D]),
             "o_ee_cubic": (None, [_D, _D, _D]),
@@ -334,6 +335,13 @@ def psd_project(A):
 def cubic_safe(coef, alpha_l):
     c, cp = _d(coef)
     return _lib_handle().o_cubic_safe(cp, alpha_l)
+
+
+def pair_safe(kind, X, Q, shrink, dhat):
+    """Safe fraction of a PT (kind 0) / EE (kind 1) pair: X, Q are 4 x 3."""
+    x, xp = _d(np.asarray(X, dtype=np.float64).reshape(12))
+    q, qp = _d(np.asarray(Q, dtype=np.float64).reshape(12))
+    return _lib_handle().o_pair_safe(int(kind), xp, qp, shrink, dhat)
 
 
 def safe_bisect(coef, xs, xu, ys, yu):

@@ -183,13 +183,10 @@ static double dist_at(int kind, const double* X, const double* Q, double t) {
 
 /* safe fraction of the motion x + t q, t in [0,1], for a PT (kind 0) or
  * EE (kind 1) pair on vertices v[4] (PT: p, t0, t1, t2). */
-static double pair_safe(const OScene* s, int kind, const int* v, const double* x, const double* q) {
-    double X[12], Q[12];
-    for (int j = 0; j < 4; ++j)
-        for (int r = 0; r < 3; ++r) {
-            X[3 * j + r] = x[3 * v[j] + r];
-            Q[3 * j + r] = q[3 * v[j] + r];
-        }
+/* safe fraction of the motion X + t Q, t in [0,1], of one PT (kind 0:
+ * p, t0, t1, t2) or EE (kind 1: a0, a1, b0, b1) pair given as 4 x 3
+ * positions and displacements. */
+double o_pair_safe(int kind, const double* X, const double* Q, double shrink, double dhat) {
     double d0, l, coef[4];
     if (kind == 0) {
         double w[3];
@@ -208,7 +205,7 @@ static double pair_safe(const OScene* s, int kind, const int* v, const double* x
         l = o_ltight_ee(Q);
         o_ee_cubic(X, Q, coef);
     }
-    double al = l > 0.0 ? (1.0 - s->prm.ccd_shrink) * d0 / l : INFINITY;
+    double al = l > 0.0 ? (1.0 - shrink) * d0 / l : INFINITY;
     double a = o_cubic_safe(coef, al);
     /* The coplanarity walk only rules out crossing: a grazing motion may end
      * arbitrarily close to contact.  Reading: when the end of the step lies
@@ -216,7 +213,7 @@ static double pair_safe(const OScene* s, int kind, const int* v, const double* x
      * the conservative bound alpha_l (where d >= s d0 holds) and the walk's
      * result, 12 halvings. */
     if (a > al) {
-        double thr = s->prm.ccd_shrink * (d0 < s->prm.dhat ? d0 : s->prm.dhat);
+        double thr = shrink * (d0 < dhat ? d0 : dhat);
         if (dist_at(kind, X, Q, a) < thr) {
             double lo = al > 0.0 ? al : 0.0, hi = a;
             for (int it = 0; it < 12; ++it) {
@@ -230,6 +227,16 @@ static double pair_safe(const OScene* s, int kind, const int* v, const double* x
         }
     }
     return a;
+}
+
+static double pair_safe(const OScene* s, int kind, const int* v, const double* x, const double* q) {
+    double X[12], Q[12];
+    for (int j = 0; j < 4; ++j)
+        for (int r = 0; r < 3; ++r) {
+            X[3 * j + r] = x[3 * v[j] + r];
+            Q[3 * j + r] = q[3 * v[j] + r];
+        }
+    return o_pair_safe(kind, X, Q, s->prm.ccd_shrink, s->prm.dhat);
 }
 
 static void swept_box(const double* x, const double* p, const int* v, int n, double* lo, double* hi) {

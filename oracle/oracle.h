@@ -139,6 +139,9 @@ void o_hess_forms(OScene* s, const double* x_base, const double* x_curr,
 
 /* ---- CCD -------------------------------------------------------------- */
 double o_cubic_safe(const double coef[4], double alpha_l);   /* d,c,b,a */
+/* safe fraction of one PT (kind 0: p, t0, t1, t2) or EE (kind 1) pair moving
+ * X + t Q, 4 x 3 doubles each */
+double o_pair_safe(int kind, const double* X, const double* Q, double shrink, double dhat);
 double o_safe_bisect(const double coef[4], double xs, double xu, double ys, double yu);
 void o_pt_cubic(const double* x4, const double* p4, double coef[4]);
 void o_ee_cubic(const double* x4, const double* p4, double coef[4]);

@@ -383,3 +383,61 @@ def test_subspace_iteration_reproduces_pcg_on_a_quadratic():
         ref.append(x.copy())
     for a, c in zip(ours, ref):
         assert np.linalg.norm(a - c) <= 1e-9 * np.linalg.norm(c)
+
+
+def test_pair_safe_cuts_a_grazing_step_at_the_minimum_separation():
+    """A point sliding over a triangle towards its plane never becomes
+    coplanar, so the coplanarity walk alone would allow the whole step and
+    leave a 1e-9 gap; the step is cut where the gap reaches s min(d0, dhat),
+    to the bisection's resolution (the distance is linear in t there)."""
+    s, dhat = 0.1, 1e-3
+    X = np.array([[-0.5, 0.25, 1e-3], [0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=float)
+    Q = np.zeros((4, 3))
+    Q[0] = [0.75, 0.0, -(1e-3 - 1e-9)]
+    a = O.pair_safe(0, X, Q, s, dhat)
+    d0 = math.sqrt(0.25 + 1e-6)
+    thr = s * min(d0, dhat)
+    t_star = (1e-3 - thr) / (1e-3 - 1e-9)          # over the interior, d(t) = z(t)
+    al = (1 - s) * d0 / np.linalg.norm(Q[0])
+    assert a < 1.0
+    assert abs(a - t_star) <= (1.0 - al) * 2.0 ** -12 + 1e-12
+    assert _brute_pt_distance(X + a * Q) >= thr * (1 - 1e-12)
+
+
+def test_pair_safe_direct_approach_keeps_the_minimum_separation():
+    """Falling straight onto a triangle: the plane is crossed at t = 0.5, the
+    walk stops before it, and the step ends at least s min(d0, dhat) away."""
+    s, dhat = 0.1, 1e-3
+    X = np.array([[0.25, 0.25, 1e-3], [0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=float)
+    Q = np.zeros((4, 3))
+    Q[0] = [0, 0, -2e-3]
+    a = O.pair_safe(0, X, Q, s, dhat)
+    assert a < 0.5
+    assert 1e-3 - 2e-3 * a >= s * 1e-3 * (1 - 1e-12)
+
+
+def test_pair_safe_random_pairs_never_cross_and_end_apart():
+    """Random PT and EE pairs and motions: no coplanarity sign change on
+    [0, alpha] beyond alpha_l, and a step longer than alpha_l ends at least
+    s min(d0, dhat) away."""
+    s, dhat = 0.1, 0.05
+    for trial in range(300):
+        kind = trial % 2
+        X = RNG.normal(size=(4, 3)) * 0.1
+        Q = RNG.normal(size=(4, 3)) * 0.1
+        a = O.pair_safe(kind, X, Q, s, dhat)
+        assert 0.0 <= a <= 1.0
+        dist = _brute_pt_distance if kind == 0 else _brute_ee_distance
+        d0 = dist(X)
+        l = (O.ltight_pt if kind == 0 else O.ltight_ee)(Q.reshape(12))
+        al = (1 - s) * d0 / l if l > 0 else math.inf
+        if a > al:
+            assert dist(X + a * Q) >= s * min(d0, dhat) * (1 - 1e-6)
+
+
+def _brute_pt_distance(X):
+    return _pt_brute(X[0], X[1], X[2], X[3])
+
+
+def _brute_ee_distance(X):
+    return _ee_brute(X[0], X[1], X[2], X[3])
