@@ -137,7 +137,8 @@ def stage_bytes(nv, nt, nblocks, rsize):
 # since), scaled by the units a launch processes: profiles/ holds the
 # summaries and commands
 TRAFFIC = {
-    ("mas_blocks", "fp32"): {"bytes_per_block": 56.39e6 / 1507},
+    ("mas_blocks", "fp32"): {"bytes_per_block": (56.331008e6 + 0.063488e6) / 1507},
+    ("forms", "fp32"): {"bytes_per_tet": (49.592832e6 + 0.042752e6) / 196608},
 }
 
 
