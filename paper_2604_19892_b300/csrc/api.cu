@@ -301,6 +301,83 @@ int setup_dev(ipc_scene* s) {
     D.asmb = A.arr<double>((size_t)nb0 * kBlk * kBlk);
     D.invflag = A.arr<int>(std::max(nb, 1));
     D.asmbc = A.arr<double>((size_t)std::max(nb - nb0, 1) * kBlk * kBlk);
+    // diagonal of each block's mass term: the lumped mass of the block's
+    // nodes (sums of vertex masses at the coarse levels), fixed by the mesh
+    std::vector<double> mdiag((size_t)nb * kBlk, 0.0);
+    {
+        std::vector<double> mnode;
+        for (int l = 0; l < m.nlev; ++l) {
+            mnode.assign(m.nnodes[l], 0.0);
+            for (int v = 0; v < m.nv; ++v) mnode[l == 0 ? v : m.node_of_vert[l][v]] += (double)massr[v];
+            for (int g = 0; g < m.ngroups[l]; ++g)
+                for (int sl = 0; sl < kSub; ++sl) {
+                    int n = m.members[l][(size_t)g * kSub + sl];
+                    if (n < 0) continue;
+                    for (int c = 0; c < 3; ++c) mdiag[((size_t)D.blk_off[l] + g) * kBlk + 3 * sl + c] = mnode[n];
+                }
+        }
+    }
+    double* d_mdiag = A.arr<double>(mdiag.size());
+    D.mdiag = d_mdiag;
+    // coarse assembly targets: for every coarse level and every tet touching
+    // more than one node there, each pair of its nodes inside one group, keyed
+    // by (coarse block, lower slot, higher slot); sorted by key, then tet
+    std::vector<int4> ctgt;
+    std::vector<int2> centry;
+    {
+        struct Contrib {
+            long long key;
+            int t, masks;
+        };
+        std::vector<Contrib> cs;
+        for (int l = 1; l < m.nlev; ++l) {
+            const int cb0 = D.blk_off[l] - D.blk_off[1];
+            for (int t = 0; t < m.nt; ++t) {
+                int nd[4], mk[4], nn = 0;
+                for (int a = 0; a < 4; ++a) {
+                    const int n = m.node_of_vert[l][m.tets[4 * t + a]];
+                    int k = 0;
+                    while (k < nn && nd[k] != n) ++k;
+                    if (k == nn) {
+                        nd[nn] = n;
+                        mk[nn++] = 0;
+                    }
+                    mk[k] |= 1 << a;
+                }
+                if (nn < 2) continue;
+                for (int i = 0; i < nn; ++i)
+                    for (int j = i; j < nn; ++j) {
+                        const int gi = m.group_of[l][nd[i]], gj = m.group_of[l][nd[j]];
+                        if (gi != gj) continue;
+                        int si = m.slot_of[l][nd[i]], sj = m.slot_of[l][nd[j]];
+                        int mi = mk[i], mj = mk[j];
+                        if (si > sj) {
+                            std::swap(si, sj);
+                            std::swap(mi, mj);
+                        }
+                        const long long key = ((long long)(cb0 + gi) * kBlk + si) * kBlk + sj;
+                        cs.push_back({key, t, mi | (mj << 4)});
+                    }
+            }
+        }
+        std::sort(cs.begin(), cs.end(), [](const Contrib& x, const Contrib& y) {
+            return x.key != y.key ? x.key < y.key : x.t < y.t;
+        });
+        centry.resize(cs.size());
+        for (size_t e = 0; e < cs.size(); ++e) {
+            centry[e] = make_int2(cs[e].t, cs[e].masks);
+            if (e == 0 || cs[e].key != cs[e - 1].key) {
+                const long long k = cs[e].key;
+                ctgt.push_back(make_int4((int)(k / (kBlk * kBlk)), (int)(k / kBlk % kBlk), (int)(k % kBlk), (int)e));
+            }
+        }
+        ctgt.push_back(make_int4(0, 0, 0, (int)cs.size()));
+    }
+    int4* d_ctgt = A.arr<int4>(ctgt.size());
+    int2* d_centry = A.arr<int2>(std::max<size_t>(centry.size(), 1));
+    D.nctgt = (int)ctgt.size() - 1;
+    D.ctgt = d_ctgt;
+    D.centry = d_centry;
     D.coarse_r = A.arr<R>(std::max(coff, 1));
     D.coarse_y = A.arr<R>(std::max(coff, 1));
     D.C = alloc_contacts(A, D.cap);
@@ -374,6 +451,9 @@ int setup_dev(ipc_scene* s) {
     CUDA_TRY(cudaMemcpy(d_lam, m.lam.data(), sizeof(double) * m.nt, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_mass, massr.data(), sizeof(R) * m.nv, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_massd, m.mass.data(), sizeof(double) * m.nv, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_mdiag, mdiag.data(), sizeof(double) * mdiag.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_ctgt, ctgt.data(), sizeof(int4) * ctgt.size(), cudaMemcpyHostToDevice));
+    if (!centry.empty()) CUDA_TRY(cudaMemcpy(d_centry, centry.data(), sizeof(int2) * centry.size(), cudaMemcpyHostToDevice));
     if (D.nsv) CUDA_TRY(cudaMemcpy(d_sv, m.sv.data(), sizeof(int) * D.nsv, cudaMemcpyHostToDevice));
     if (D.nsf) CUDA_TRY(cudaMemcpy(d_sf, m.sf.data(), sizeof(int) * m.sf.size(), cudaMemcpyHostToDevice));
     if (D.nse) CUDA_TRY(cudaMemcpy(d_se, m.se.data(), sizeof(int) * m.se.size(), cudaMemcpyHostToDevice));

@@ -121,6 +121,10 @@ struct Dev {
     R* blocks;                             // nblocks * 96 * 96
     double* asmb;                          // level-0 assembly buffer (FP64)
     double* asmbc;                         // coarse-level assembly buffer (FP64)
+    const double* mdiag;                   // per block: mass diagonal (96 entries), fixed
+    int nctgt;                             // coarse assembly targets (node-pair 3x3 blocks)
+    const int4* ctgt;                      // nctgt + 1: coarse block, slot i <= slot j, first entry
+    const int2* centry;                    // per target: (tet, vertex masks: bits 0-3 node i, 4-7 node j)
     int* invflag;                          // level-0 blocks to re-invert in FP64
     R* coarse_r;                           // restricted residuals, 3 * nnodes[l] per level, offsets coarse_off
     R* coarse_y;

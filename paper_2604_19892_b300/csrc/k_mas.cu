@@ -307,15 +307,43 @@ __device__ __forceinline__ bool one_node(const Dev<R>& D, int l, const int* v, i
     return true;
 }
 
-// 3x3 blocks K_ab = sum_{c,c'} Bf[a][c] Bf[b][c'] H[3c+r][3c'+s] of the tet's
-// 12x12 Hessian G^T H G, scattered into every level where the tet spans
-// more than one node
+// Every assembly block set to its mass term: zero except the lumped node
+// masses on the diagonal (a table fixed by the mesh), level 0 into asmb, the
+// coarse levels into asmbc. Four FP64 entries (two 16-byte stores) per thread
+// and step; only diagonal rows read the table.
 template <class R>
-__global__ void k_assemble_tets(Dev<R> D) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_init_blocks(Dev<R> D, int nb0, int nb) {
+    constexpr int kQ = kBlk * kBlk / 4;  // 4-entry groups per block
+    const int n4 = nb * kQ;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += gridDim.x * blockDim.x) {
+        const int b = e / kQ;
+        const int rem = 4 * (e - b * kQ);
+        const int row = rem / kBlk, col = rem - row * kBlk;
+        const int dc = row - col;  // the diagonal sits at entry dc of this group if 0 <= dc < 4
+        const double dg = (dc >= 0 && dc < 4) ? D.mdiag[(size_t)b * kBlk + row] : 0.0;
+        double* dst = (b < nb0 ? D.asmb + (size_t)b * (kBlk * kBlk) : D.asmbc + (size_t)(b - nb0) * (kBlk * kBlk)) + rem;
+        reinterpret_cast<double2*>(dst)[0] = make_double2(dc == 0 ? dg : 0.0, dc == 1 ? dg : 0.0);
+        reinterpret_cast<double2*>(dst)[1] = make_double2(dc == 2 ? dg : 0.0, dc == 3 ? dg : 0.0);
+    }
+}
+
+// Elastic terms h^2 K_t of every tet, K_t = G^T H G with G the 9x12 map from
+// the four vertex displacements to dF (rows Bf[a], Bf[0] = -sum of the rest).
+// Level 0 takes the 3x3 blocks K_ab = sum_{c,c2} Bf[a][c] H[3c+r][3c2+s] Bf[b][c2]
+// of the vertex pairs inside one subdomain, with FP64 atomics (a vertex pair
+// is shared by a few tets only: 24 at most on the sphere pile).
+template <class R>
+__global__ void k_assemble_tets0(Dev<R> D) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= D.nt) return;
-    int4 q = D.tets[t];
-    int vid[4] = {q.x, q.y, q.z, q.w};
+    const int4 q = D.tets[t];
+    const int vid[4] = {q.x, q.y, q.z, q.w};
+    int g[4], sl[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        g[a] = D.grp0[vid[a]];
+        sl[a] = D.slot0[vid[a]];
+    }
     R Bm[3][3];
     load_B(D, t, Bm);
     R Bf[4][3];
@@ -331,34 +359,94 @@ __global__ void k_assemble_tets(Dev<R> D) {
             H[i][j] = v;
             H[j][i] = v;
         }
-    unsigned levels = 0;
-    for (int l = 0; l < D.nlev; ++l)
-        if (!one_node(D, l, vid, 4)) levels |= 1u << l;
-    for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-            R blk[3][3];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        R HB[9][3];
+        for (int i = 0; i < 9; ++i)
+            for (int s2 = 0; s2 < 3; ++s2) {
+                R inner = 0;
+                for (int c2 = 0; c2 < 3; ++c2) inner += H[i][3 * c2 + s2] * Bf[b][c2];
+                HB[i][s2] = inner;
+            }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (g[a] != g[b]) continue;
+            double* A = D.asmb + (size_t)g[a] * (kBlk * kBlk) + (3 * sl[a]) * kBlk + 3 * sl[b];
             for (int r = 0; r < 3; ++r)
-                for (int s = 0; s < 3; ++s) {
+                for (int s2 = 0; s2 < 3; ++s2) {
                     R acc = 0;
-                    for (int c = 0; c < 3; ++c) {
-                        R inner = 0;
-                        for (int c2 = 0; c2 < 3; ++c2) inner += Bf[b][c2] * H[3 * c + r][3 * c2 + s];
-                        acc += Bf[a][c] * inner;
-                    }
-                    blk[r][s] = acc;
+                    for (int c = 0; c < 3; ++c) acc += Bf[a][c] * HB[3 * c + r][s2];
+                    atomicAdd(&A[r * kBlk + s2], (double)acc);
                 }
-            for (int l = 0; l < D.nlev; ++l)
-                if (levels & (1u << l)) add_block(D, l, vid[a], vid[b], blk);
         }
+    }
 }
 
+// Coarse levels. For level-l nodes P, Q the Galerkin block of a tet is
+// (sum_{a in P} Bf[a])^T H (sum_{b in Q} Bf[b]) in the same 3x3 sense, and a
+// tet inside one node adds nothing (its rows sum to zero). The mesh fixes
+// which tets reach which node pair, so the host lists, per target (coarse
+// block, slot si <= slot sj), its contributions (tet, vertex mask of P, of Q)
+// once; one warp per target sums them in registers, reduces across lanes and
+// adds the 3x3 block (and its transpose) to the block without atomics: no
+// other thread writes those entries in this kernel.
 template <class R>
-__global__ void k_assemble_mass(Dev<R> D) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= D.nv) return;
-    R m = D.mass[v];
-    R blk[3][3] = {{m, 0, 0}, {0, m, 0}, {0, 0, m}};
-    for (int l = 0; l < D.nlev; ++l) add_block(D, l, v, v, blk);
+__global__ void __launch_bounds__(256) k_assemble_coarse(Dev<R> D) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= D.nctgt) return;
+    const int4 tg = D.ctgt[wid];  // coarse block, si, sj, first contribution
+    const int end = D.ctgt[wid + 1].w;
+    R acc[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc[e] = 0;
+    for (int e = tg.w + lane; e < end; e += 32) {
+        const int2 c = D.centry[e];
+        const int t = c.x;
+        R Bm[3][3];
+        load_B(D, t, Bm);
+        R BA[3], BB[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const R b0 = -(Bm[0][k] + Bm[1][k] + Bm[2][k]);
+            BA[k] = ((c.y & 1) ? b0 : (R)0) + ((c.y & 2) ? Bm[0][k] : (R)0) + ((c.y & 4) ? Bm[1][k] : (R)0) +
+                    ((c.y & 8) ? Bm[2][k] : (R)0);
+            BB[k] = ((c.y & 16) ? b0 : (R)0) + ((c.y & 32) ? Bm[0][k] : (R)0) + ((c.y & 64) ? Bm[1][k] : (R)0) +
+                    ((c.y & 128) ? Bm[2][k] : (R)0);
+        }
+        // HB[i][s] = sum_c2 H[i][3 c2 + s] BB[c2], streamed over the packed entries
+        const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
+        R HB[9][3];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) HB[i][k] = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+#pragma unroll
+            for (int j = i; j < 9; ++j) {
+                const R v = hp[pk(i, j) * kPack];
+                HB[i][j % 3] += v * BB[j / 3];
+                if (j != i) HB[j][i % 3] += v * BB[i / 3];
+            }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) acc[3 * r + k] += BA[0] * HB[r][k] + BA[1] * HB[3 + r][k] + BA[2] * HB[6 + r][k];
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+    if (lane == 0) {
+        double* A = D.asmbc + (size_t)tg.x * (kBlk * kBlk);
+        const int si = tg.y, sj = tg.z;
+        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 3; ++k) {
+                A[(3 * si + r) * kBlk + 3 * sj + k] += (double)acc[3 * r + k];
+                if (si != sj) A[(3 * sj + k) * kBlk + 3 * si + r] += (double)acc[3 * r + k];
+            }
+    }
 }
 
 template <class R>
@@ -410,6 +498,39 @@ constexpr int kInvThreads = 160;
 static_assert(kNT * kTile == kBlk, "tile size must divide the block size");
 static_assert(kInvThreads >= kNTiles && kInvThreads % 32 == 0, "one thread per lower tile");
 
+template <class T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+// six consecutive entries from shared memory (p is 8-byte aligned for float,
+// 16-byte for double: every tile starts at an even index)
+template <class T>
+__device__ __forceinline__ void lds6(const T* p, T v[kTile]) {
+    using V = typename Vec2<T>::type;
+    const V* q = reinterpret_cast<const V*>(p);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const V w = q[i];
+        v[2 * i] = w.x;
+        v[2 * i + 1] = w.y;
+    }
+}
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+// non-negative floats and doubles order like their bit patterns
+__device__ __forceinline__ void smem_max(float* p, float v) {
+    atomicMax(reinterpret_cast<unsigned*>(p), __float_as_uint(v));
+}
+__device__ __forceinline__ void smem_max(double* p, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+
 // Blocks come from the FP64 assembly (level 0: asmb, coarse levels: asmbc).
 // flags: pass 0 (T = float) marks a block whose factorisation floored or
 // raised a pivot, i.e. whose conditioning FP32 cannot carry (very stiff
@@ -421,7 +542,8 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
     T* buf = reinterpret_cast<T*>(smem_raw);      // 96 x 96: L^T, then W
     T* vec = buf + kBlk * kBlk;                   // 2 x 96 broadcast
     T* sc = vec + 2 * kBlk;                       // diagonal scaling s
-    T* pm = sc + kBlk;                            // 2 x 16 column maxima of L_rk^2
+    T* idg = sc + kBlk;                           // 1 / L_kk
+    T* pm = idg + kBlk;                           // 3 rotating slots: max_r L_rk^2 of step k
     __shared__ int s_bad;
     const T eps_piv = (T)(sizeof(T) == 8 ? 1e-12 : 1e-6);
     int b = blockIdx.x;
@@ -432,7 +554,10 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
     const int* mem = D.members[l] + (size_t)grp * kSub;
     const double* src = l == 0 ? D.asmb + (size_t)b * kBlk * kBlk
                                : D.asmbc + (size_t)(b - D.blk_off[1]) * kBlk * kBlk;
-    if (threadIdx.x == 0) s_bad = 0;
+    if (threadIdx.x == 0) {
+        s_bad = 0;
+        pm[0] = pm[1] = pm[2] = (T)0;
+    }
     for (int r = threadIdx.x; r < kBlk; r += blockDim.x) {
         double d = src[r * kBlk + r];
         sc[r] = (mem[r / 3] < 0 || !(d > 0.0)) ? (T)1 : (T)(1.0 / sqrt(d));
@@ -473,6 +598,11 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
         for (int kk = 0; kk < kTile; ++kk) {
             const int k = kTile * kt + kk;
             T* vb = vec + (k & 1) * kBlk;
+            T* pmk = pm + k % 3;
+            // slot (k + 1) % 3 was last read in step k - 2, which every thread
+            // finished before the previous barrier; step k + 1 writes it after
+            // the next one
+            if (threadIdx.x == 0) pm[(k + 1) % 3] = (T)0;
             if (act && tj == kt) {
                 T m = (T)0;
 #pragma unroll
@@ -481,7 +611,7 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
                     vb[r0 + rr] = v;
                     if ((ti > kt || rr > kk) && v * v > m) m = v * v;
                 }
-                pm[(k & 1) * kNT + ti] = m;
+                if (m > (T)0) smem_max(pmk, m);
             }
             __syncthreads();
             if (act && ti >= kt && tj >= kt) {
@@ -492,17 +622,20 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
                 const T raw = vb[k];
                 T piv = raw;
                 if (!(piv > eps_piv)) piv = eps_piv;
-                const T* pmk = pm + (k & 1) * kNT;
-                for (int q = kt; q < kNT; ++q) piv = pmk[q] > piv ? pmk[q] : piv;
+                const T pmax = *pmk;
+                if (pmax > piv) piv = pmax;
                 if (ti == kt && tj == kt && piv != raw) s_bad = 1;
-                const T sq = sqrt(piv);
-                const T ip = (T)1 / piv, isq = (T)1 / sq;
+                // L_kk = piv * isq, the column below scaled by isq, the trailing
+                // update by ip = isq^2: L L^T reproduces the rank-1 update exactly
+                // up to the rounding of isq
+                const T isq = inv_sqrt(piv);
+                const T sq = piv * isq, ip = isq * isq;
+                if (ti == kt && tj == kt) idg[k] = isq;
                 T vr[kTile], vc[kTile];
+                lds6(vb + r0, vr);
+                lds6(vb + c0, vc);
 #pragma unroll
-                for (int q = 0; q < kTile; ++q) {
-                    vr[q] = vb[r0 + q];
-                    vc[q] = vb[c0 + q] * ip;
-                }
+                for (int q = 0; q < kTile; ++q) vc[q] *= ip;
 #pragma unroll
                 for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
@@ -540,7 +673,7 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
             T* vb = vec + (k & 1) * kBlk;
             const T* Lk = buf + k * kBlk;                 // column k of L
             if (act && ti == kt) {
-                const T il = (T)1 / Lk[k];
+                const T il = idg[k];
 #pragma unroll
                 for (int cc = 0; cc < kTile; ++cc) {
                     a[kk][cc] *= il;
@@ -550,11 +683,11 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
             __syncthreads();
             if (act && ti >= kt && tj <= kt) {
                 T lr[kTile], wc[kTile];
+                lds6(Lk + r0, lr);
+                lds6(vb + c0, wc);
 #pragma unroll
-                for (int q = 0; q < kTile; ++q) {
-                    lr[q] = (ti > kt || q > kk) ? Lk[r0 + q] : (T)0;
-                    wc[q] = vb[c0 + q];
-                }
+                for (int q = 0; q < kTile; ++q)
+                    if (!(ti > kt || q > kk)) lr[q] = (T)0;
 #pragma unroll
                 for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
@@ -585,11 +718,8 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
     for (int k = r0; k < kBlk; ++k) {
         const T* Wk = buf + k * kBlk;
         T wr[kTile], wc[kTile];
-#pragma unroll
-        for (int q = 0; q < kTile; ++q) {
-            wr[q] = Wk[r0 + q];
-            wc[q] = Wk[c0 + q];
-        }
+        lds6(Wk + r0, wr);
+        lds6(Wk + c0, wc);
 #pragma unroll
         for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
@@ -1102,18 +1232,17 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
     int nb = D.blk_off[D.nlev];
     KL(k_clear_upd<R><<<1, 1, 0, st>>>(D));
     const int nb0 = D.nlev > 1 ? D.blk_off[1] : nb;
-    cudaMemsetAsync(D.asmb, 0, sizeof(double) * (size_t)nb0 * kBlk * kBlk, st);
-    if (nb > nb0) cudaMemsetAsync(D.asmbc, 0, sizeof(double) * (size_t)(nb - nb0) * kBlk * kBlk, st);
+    KL(k_init_blocks<R><<<nblk((long long)nb * (kBlk * kBlk / 4), 256), 256, 0, st>>>(D, nb0, nb));
     KL(k_tet_hessian<R><<<nblk(D.nt, 64), 64, 0, st>>>(D, x));
-    KL(k_assemble_tets<R><<<nblk(D.nt), kT, 0, st>>>(D));
-    KL(k_assemble_mass<R><<<nblk(D.nv), kT, 0, st>>>(D));
+    KL(k_assemble_tets0<R><<<nblk(D.nt), kT, 0, st>>>(D));
+    if (D.nctgt > 0) KL(k_assemble_coarse<R><<<nblk(32LL * D.nctgt, 256), 256, 0, st>>>(D));
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
     // blocks are assembled in FP64 and inverted in the bulk precision R (FP32
     // in the mixed mode: B300's FP64 rate, about two FMAs per clock per SM,
     // would make the inversion the most expensive step) with an FP64 redo of
     // the blocks FP32 cannot carry
-    const size_t smem_r = sizeof(R) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
-    const size_t smem_d = sizeof(double) * ((size_t)kBlk * kBlk + 3 * kBlk + 2 * kNT);
+    const size_t smem_r = sizeof(R) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
+    const size_t smem_d = sizeof(double) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_invert<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
