@@ -319,23 +319,31 @@ int setup_dev(ipc_scene* s) {
     }
     double* d_mdiag = A.arr<double>(mdiag.size());
     D.mdiag = d_mdiag;
-    // coarse assembly targets: for every coarse level and every tet touching
-    // more than one node there, each pair of its nodes inside one group, keyed
-    // by (coarse block, lower slot, higher slot); sorted by key, then tet
-    std::vector<int4> ctgt;
-    std::vector<int2> centry;
+    // coarse elastic assembly contributions, fixed by the mesh: on every
+    // coarse level, for every tet touching more than one node and every pair
+    // of its node sets (P, Q) inside one group, the target (coarse block, node
+    // slot i <= node slot j) and the tet's vertex masks of P (bits 0-3) and Q
+    // (bits 4-7).
+    // Sorted by target then tet; targets with many entries are cut into
+    // chunks of at most kChunk summed separately (and added atomically).
+    std::vector<int> tcon_off(m.nt + 1, 0);
+    std::vector<int2> tcon;
+    std::vector<int4> items;
+    long long ncon = 0;
     {
+        constexpr int kChunk = 64;
         struct Contrib {
             long long key;
             int t, masks;
         };
         std::vector<Contrib> cs;
+        cs.reserve((size_t)m.nt * 14);
         for (int l = 1; l < m.nlev; ++l) {
-            const int cb0 = D.blk_off[l] - D.blk_off[1];
             for (int t = 0; t < m.nt; ++t) {
                 int nd[4], mk[4], nn = 0;
                 for (int a = 0; a < 4; ++a) {
-                    const int n = m.node_of_vert[l][m.tets[4 * t + a]];
+                    const int v = m.tets[4 * t + a];
+                    const int n = m.node_of_vert[l][v];
                     int k = 0;
                     while (k < nn && nd[k] != n) ++k;
                     if (k == nn) {
@@ -355,7 +363,7 @@ int setup_dev(ipc_scene* s) {
                             std::swap(si, sj);
                             std::swap(mi, mj);
                         }
-                        const long long key = ((long long)(cb0 + gi) * kBlk + si) * kBlk + sj;
+                        const long long key = ((long long)(D.blk_off[l] - D.blk_off[1] + gi) * kSub + si) * kSub + sj;
                         cs.push_back({key, t, mi | (mj << 4)});
                     }
             }
@@ -363,21 +371,33 @@ int setup_dev(ipc_scene* s) {
         std::sort(cs.begin(), cs.end(), [](const Contrib& x, const Contrib& y) {
             return x.key != y.key ? x.key < y.key : x.t < y.t;
         });
-        centry.resize(cs.size());
-        for (size_t e = 0; e < cs.size(); ++e) {
-            centry[e] = make_int2(cs[e].t, cs[e].masks);
-            if (e == 0 || cs[e].key != cs[e - 1].key) {
-                const long long k = cs[e].key;
-                ctgt.push_back(make_int4((int)(k / (kBlk * kBlk)), (int)(k / kBlk % kBlk), (int)(k % kBlk), (int)e));
-            }
+        ncon = (long long)cs.size();
+        for (const Contrib& c : cs) ++tcon_off[c.t + 1];
+        for (int t = 0; t < m.nt; ++t) tcon_off[t + 1] += tcon_off[t];
+        tcon.resize(cs.size());
+        std::vector<int> cur(tcon_off.begin(), tcon_off.end() - 1);
+        for (size_t e = 0; e < cs.size(); ++e) tcon[cur[cs[e].t]++] = make_int2((int)e, cs[e].masks);
+        for (size_t e = 0; e < cs.size();) {
+            size_t f = e;
+            while (f < cs.size() && cs[f].key == cs[e].key) ++f;
+            const long long k = cs[e].key;
+            const int blk = (int)(k / (kSub * kSub)), si = (int)(k / kSub % kSub), sj = (int)(k % kSub);
+            const int split = f - e > (size_t)kChunk ? 1 : 0;
+            for (size_t c = e; c < f; c += kChunk) items.push_back(make_int4(blk, si, sj | (split << 8), (int)c));
+            e = f;
         }
-        ctgt.push_back(make_int4(0, 0, 0, (int)cs.size()));
+        items.push_back(make_int4(0, 0, 0, (int)cs.size()));
     }
-    int4* d_ctgt = A.arr<int4>(ctgt.size());
-    int2* d_centry = A.arr<int2>(std::max<size_t>(centry.size(), 1));
-    D.nctgt = (int)ctgt.size() - 1;
-    D.ctgt = d_ctgt;
-    D.centry = d_centry;
+    if (12 * ncon >= (1LL << 31)) return fail(IPC_ERR_CAPACITY, "scene: mesh too large for the assembly contribution list");
+    int* d_tcon_off = A.arr<int>(tcon_off.size());
+    int2* d_tcon = A.arr<int2>(std::max<size_t>(tcon.size(), 1));
+    int4* d_items = A.arr<int4>(items.size());
+    D.ncon = (int)ncon;
+    D.nitem = (int)items.size() - 1;
+    D.cval = A.arr<R>(std::max<size_t>(12 * (size_t)ncon, 1));
+    D.tcon_off = d_tcon_off;
+    D.tcon = d_tcon;
+    D.item = d_items;
     D.coarse_r = A.arr<R>(std::max(coff, 1));
     D.coarse_y = A.arr<R>(std::max(coff, 1));
     D.C = alloc_contacts(A, D.cap);
@@ -452,8 +472,9 @@ int setup_dev(ipc_scene* s) {
     CUDA_TRY(cudaMemcpy(d_mass, massr.data(), sizeof(R) * m.nv, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_massd, m.mass.data(), sizeof(double) * m.nv, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_mdiag, mdiag.data(), sizeof(double) * mdiag.size(), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(d_ctgt, ctgt.data(), sizeof(int4) * ctgt.size(), cudaMemcpyHostToDevice));
-    if (!centry.empty()) CUDA_TRY(cudaMemcpy(d_centry, centry.data(), sizeof(int2) * centry.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_tcon_off, tcon_off.data(), sizeof(int) * tcon_off.size(), cudaMemcpyHostToDevice));
+    if (!tcon.empty()) CUDA_TRY(cudaMemcpy(d_tcon, tcon.data(), sizeof(int2) * tcon.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
     if (D.nsv) CUDA_TRY(cudaMemcpy(d_sv, m.sv.data(), sizeof(int) * D.nsv, cudaMemcpyHostToDevice));
     if (D.nsf) CUDA_TRY(cudaMemcpy(d_sf, m.sf.data(), sizeof(int) * m.sf.size(), cudaMemcpyHostToDevice));
     if (D.nse) CUDA_TRY(cudaMemcpy(d_se, m.se.data(), sizeof(int) * m.se.size(), cudaMemcpyHostToDevice));

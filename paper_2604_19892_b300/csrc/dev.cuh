@@ -122,9 +122,11 @@ struct Dev {
     double* asmb;                          // level-0 assembly buffer (FP64)
     double* asmbc;                         // coarse-level assembly buffer (FP64)
     const double* mdiag;                   // per block: mass diagonal (96 entries), fixed
-    int nctgt;                             // coarse assembly targets (node-pair 3x3 blocks)
-    const int4* ctgt;                      // nctgt + 1: coarse block, slot i <= slot j, first entry
-    const int2* centry;                    // per target: (tet, vertex masks: bits 0-3 node i, 4-7 node j)
+    int ncon, nitem;                       // coarse elastic assembly: contributions, summation items
+    R* cval;                               // 12 x ncon: 3x3 value of each contribution (+3 pad)
+    const int* tcon_off;                   // per tet (nt + 1): its contributions,
+    const int2* tcon;                      //   (slot in cval, vertex masks: bits 0-3 set i, 4-7 set j)
+    const int4* item;                      // nitem + 1: global block, slot i, slot j | split << 8, first entry
     int* invflag;                          // level-0 blocks to re-invert in FP64
     R* coarse_r;                           // restricted residuals, 3 * nnodes[l] per level, offsets coarse_off
     R* coarse_y;

@@ -31,6 +31,7 @@ namespace ipcb {
 namespace {
 
 constexpr int kT = 128;
+constexpr int kCon = 12;  // values per coarse assembly record: a 3x3 block, padded to 16 bytes
 inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
 
 __host__ __device__ __forceinline__ int pk(int i, int j) {  // packed upper index, i <= j
@@ -259,54 +260,6 @@ __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __re
 
 // ------------------------------------------------------ block assembly
 
-template <class R, class V>
-__device__ __forceinline__ void add_block(const Dev<R>& D, int l, int va, int vb, const V blk[3][3]) {
-    int na, nb, ga, gb, sa, sb;
-    if (l == 0) {
-        ga = D.grp0[va];
-        gb = D.grp0[vb];
-        if (ga != gb) return;
-        sa = D.slot0[va];
-        sb = D.slot0[vb];
-    } else {
-        na = D.node_of_vert[l][va];
-        nb = D.node_of_vert[l][vb];
-        ga = D.grp_of_node[l][na];
-        gb = D.grp_of_node[l][nb];
-        if (ga != gb) return;
-        sa = D.slot_of_node[l][na];
-        sb = D.slot_of_node[l][nb];
-    }
-    // blocks are summed in FP64 (coarse Galerkin blocks add many terms of
-    // both signs, stiff contacts must cancel exactly), inverted in R
-    if (l == 0) {
-        double* A = D.asmb + (size_t)ga * (kBlk * kBlk);
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                double v = (double)blk[r][c];
-                if (v != 0.0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
-            }
-    } else {
-        double* A = D.asmbc + ((size_t)(D.blk_off[l] - D.blk_off[1] + ga)) * (kBlk * kBlk);
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 3; ++c) {
-                double v = (double)blk[r][c];
-                if (v != 0.0) atomicAdd(&A[(3 * sa + r) * kBlk + 3 * sb + c], v);
-            }
-    }
-}
-
-// is every vertex of the term inside one level-l node? (translation-invariant
-// terms then add nothing at that level)
-template <class R>
-__device__ __forceinline__ bool one_node(const Dev<R>& D, int l, const int* v, int n) {
-    if (l == 0) return false;
-    int a = D.node_of_vert[l][v[0]];
-    for (int j = 1; j < n; ++j)
-        if (D.node_of_vert[l][v[j]] != a) return false;
-    return true;
-}
-
 // Every assembly block set to its mass term: zero except the lumped node
 // masses on the diagonal (a table fixed by the mesh), level 0 into asmb, the
 // coarse levels into asmbc. Four FP64 entries (two 16-byte stores) per thread
@@ -382,96 +335,193 @@ __global__ void k_assemble_tets0(Dev<R> D) {
     }
 }
 
-// Coarse levels. For level-l nodes P, Q the Galerkin block of a tet is
-// (sum_{a in P} Bf[a])^T H (sum_{b in Q} Bf[b]) in the same 3x3 sense, and a
-// tet inside one node adds nothing (its rows sum to zero). The mesh fixes
-// which tets reach which node pair, so the host lists, per target (coarse
-// block, slot si <= slot sj), its contributions (tet, vertex mask of P, of Q)
-// once; one warp per target sums them in registers, reduces across lanes and
-// adds the 3x3 block (and its transpose) to the block without atomics: no
-// other thread writes those entries in this kernel.
+// Coarse levels. At level l the Galerkin block of nodes P, Q sums the level-0
+// blocks of their vertices, (sum_{a in P} Bf[a])^T H (sum_{b in Q} Bf[b]) in
+// the same 3x3 sense, and a tet inside one node adds nothing (its rows sum to
+// zero). The mesh fixes which (tet, vertex set P, vertex set Q) reach which
+// target 3x3 block (coarse block, node slot i <= node slot j), so the host
+// lists these contributions once, sorted by target. The assembly is then two
+// passes: one thread per tet writes each of its contributions to its slot of
+// a value array (one 16-byte aligned record of kCon values each), and one
+// warp per target (long targets cut into chunks, added atomically) sums its
+// contiguous run and adds the block and its transpose.
 template <class R>
-__global__ void __launch_bounds__(256) k_assemble_coarse(Dev<R> D) {
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= D.nctgt) return;
-    const int4 tg = D.ctgt[wid];  // coarse block, si, sj, first contribution
-    const int end = D.ctgt[wid + 1].w;
-    R acc[9];
+__global__ void k_asm_contrib(Dev<R> D) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= D.nt) return;
+    const int e0 = D.tcon_off[t], e1 = D.tcon_off[t + 1];
+    R Bm[3][3];
+    load_B(D, t, Bm);
+    R b0[3];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) acc[e] = 0;
-    for (int e = tg.w + lane; e < end; e += 32) {
-        const int2 c = D.centry[e];
-        const int t = c.x;
-        R Bm[3][3];
-        load_B(D, t, Bm);
+    for (int c = 0; c < 3; ++c) b0[c] = -(Bm[0][c] + Bm[1][c] + Bm[2][c]);
+    const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
+    R H[9][9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = i; j < 9; ++j) {
+            const R v = hp[pk(i, j) * kPack];
+            H[i][j] = v;
+            H[j][i] = v;
+        }
+    int2 nxt = e0 < e1 ? D.tcon[e0] : make_int2(0, 0);
+    for (int e = e0; e < e1; ++e) {
+        const int2 c = nxt;
+        if (e + 1 < e1) nxt = D.tcon[e + 1];
+        const int mk = c.y;
         R BA[3], BB[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const R b0 = -(Bm[0][k] + Bm[1][k] + Bm[2][k]);
-            BA[k] = ((c.y & 1) ? b0 : (R)0) + ((c.y & 2) ? Bm[0][k] : (R)0) + ((c.y & 4) ? Bm[1][k] : (R)0) +
-                    ((c.y & 8) ? Bm[2][k] : (R)0);
-            BB[k] = ((c.y & 16) ? b0 : (R)0) + ((c.y & 32) ? Bm[0][k] : (R)0) + ((c.y & 64) ? Bm[1][k] : (R)0) +
-                    ((c.y & 128) ? Bm[2][k] : (R)0);
+            BA[k] = ((mk & 1) ? b0[k] : (R)0) + ((mk & 2) ? Bm[0][k] : (R)0) + ((mk & 4) ? Bm[1][k] : (R)0) +
+                    ((mk & 8) ? Bm[2][k] : (R)0);
+            BB[k] = ((mk & 16) ? b0[k] : (R)0) + ((mk & 32) ? Bm[0][k] : (R)0) + ((mk & 64) ? Bm[1][k] : (R)0) +
+                    ((mk & 128) ? Bm[2][k] : (R)0);
         }
-        // HB[i][s] = sum_c2 H[i][3 c2 + s] BB[c2], streamed over the packed entries
-        const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
         R HB[9][3];
 #pragma unroll
         for (int i = 0; i < 9; ++i)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) HB[i][k] = 0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-#pragma unroll
-            for (int j = i; j < 9; ++j) {
-                const R v = hp[pk(i, j) * kPack];
-                HB[i][j % 3] += v * BB[j / 3];
-                if (j != i) HB[j][i % 3] += v * BB[i / 3];
-            }
+            for (int k = 0; k < 3; ++k) HB[i][k] = H[i][k] * BB[0] + H[i][3 + k] * BB[1] + H[i][6 + k] * BB[2];
+        R K[12];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) acc[3 * r + k] += BA[0] * HB[r][k] + BA[1] * HB[3 + r][k] + BA[2] * HB[6 + r][k];
-    }
+            for (int k = 0; k < 3; ++k) K[3 * r + k] = BA[0] * HB[r][k] + BA[1] * HB[3 + r][k] + BA[2] * HB[6 + r][k];
+        K[9] = K[10] = K[11] = (R)0;
+        V4<R>* out = reinterpret_cast<V4<R>*>(D.cval + (size_t)kCon * c.x);
 #pragma unroll
-    for (int e = 0; e < 9; ++e)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
-    if (lane == 0) {
-        double* A = D.asmbc + (size_t)tg.x * (kBlk * kBlk);
-        const int si = tg.y, sj = tg.z;
-        for (int r = 0; r < 3; ++r)
-            for (int k = 0; k < 3; ++k) {
-                A[(3 * si + r) * kBlk + 3 * sj + k] += (double)acc[3 * r + k];
-                if (si != sj) A[(3 * sj + k) * kBlk + 3 * si + r] += (double)acc[3 * r + k];
-            }
+        for (int q = 0; q < 3; ++q) out[q] = V4<R>{K[4 * q], K[4 * q + 1], K[4 * q + 2], K[4 * q + 3]};
     }
 }
 
 template <class R>
+__global__ void __launch_bounds__(256) k_asm_sum(Dev<R> D) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per item
+    const int lane = threadIdx.x & 31;
+    if (i >= D.nitem) return;
+    const int4 it = D.item[i];  // coarse block, slot i, slot j | split << 8, first entry
+    const int end = D.item[i + 1].w;
+    R acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = 0;
+    for (int e = it.w + lane; e < end; e += 32) {
+        const V4<R>* in = reinterpret_cast<const V4<R>*>(D.cval + (size_t)kCon * e);
+        const V4<R> a = in[0], b = in[1], c = in[2];
+        acc[0] += a.x;
+        acc[1] += a.y;
+        acc[2] += a.z;
+        acc[3] += a.w;
+        acc[4] += b.x;
+        acc[5] += b.y;
+        acc[6] += b.z;
+        acc[7] += b.w;
+        acc[8] += c.x;
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    const int si = it.y, sj = it.z & 0xff;
+    const bool split = (it.z >> 8) != 0;
+    double* A = D.asmbc + (size_t)it.x * (kBlk * kBlk);
+    // lanes 0-8 take one entry each (and its transpose)
+    if (lane < 9) {
+        const int r = lane / 3, k = lane - 3 * r;
+        R v = acc[0];
+#pragma unroll
+        for (int q = 1; q < 9; ++q)
+            if (q == lane) v = acc[q];
+        double* p0 = A + (3 * si + r) * kBlk + 3 * sj + k;
+        double* p1 = A + (3 * sj + k) * kBlk + 3 * si + r;
+        if (split) {
+            atomicAdd(p0, (double)v);
+            if (si != sj) atomicAdd(p1, (double)v);
+        } else {
+            // the only writer of these entries in this kernel
+            *p0 += (double)v;
+            if (si != sj) *p1 += (double)v;
+        }
+    }
+}
+
+// Contact terms kappa b''(d) grad d grad d^T (Eq. 1, Alg. 1), in FP64 with
+// FP64 atomics (their stiffness spans many orders of magnitude, and their
+// weights cancel at the coarse levels). Level 0 takes the vertex pairs inside
+// one subdomain; a coarse level sums the weights of the vertices sharing a
+// node, W_P = sum_{a in P} w_a, and adds k W_P W_Q r r^T per node pair (none
+// for a pair or edge contact inside one node: its weights sum to zero).
+__device__ __forceinline__ void add_rr(double* A, int si, int sj, const double kr[3][3], double c) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int s2 = 0; s2 < 3; ++s2) {
+            const double v = c * kr[r][s2];
+            if (v != 0.0) atomicAdd(&A[(3 * si + r) * kBlk + 3 * sj + s2], v);
+        }
+}
+
+template <class R>
 __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
-    int n = min(*C.count, D.cap);
+    const int n = min(*C.count, D.cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int4 q = C.v[i];
-        int vid[4] = {q.x, q.y, q.z, q.w};
-        int nvv = C.type[i] == 2 ? 1 : 4;
-        double k = C.k[i];
-        double r[3] = {C.r[3 * i], C.r[3 * i + 1], C.r[3 * i + 2]};
-        double w[4] = {C.w[4 * i], C.w[4 * i + 1], C.w[4 * i + 2], C.w[4 * i + 3]};
-        for (int a = 0; a < nvv; ++a)
-            for (int b = 0; b < nvv; ++b) {
-                // kept in FP64 until the store: the coarse levels sum these
-                // (weights summing to zero) with FP64 atomics, so a stiff
-                // contact's translation-invariant terms cancel there
-                double blk[3][3];
-                for (int rr = 0; rr < 3; ++rr)
-                    for (int s = 0; s < 3; ++s) blk[rr][s] = k * w[a] * w[b] * r[rr] * r[s];
-                for (int l = 0; l < D.nlev; ++l) {
-                    if (nvv == 4 && one_node(D, l, vid, 4)) continue;
-                    add_block(D, l, vid[a], vid[b], blk);
-                }
+        const int4 q = C.v[i];
+        const int vid[4] = {q.x, q.y, q.z, q.w};
+        const int nvv = C.type[i] == 2 ? 1 : 4;
+        const double k = C.k[i];
+        const double r[3] = {C.r[3 * i], C.r[3 * i + 1], C.r[3 * i + 2]};
+        const double w[4] = {C.w[4 * i], C.w[4 * i + 1], C.w[4 * i + 2], C.w[4 * i + 3]};
+        double kr[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) kr[a][b] = k * r[a] * r[b];
+        int g[4], sl[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            g[a] = a < nvv ? D.grp0[vid[a]] : -1;
+            sl[a] = a < nvv ? D.slot0[vid[a]] : 0;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (a < nvv && b < nvv && g[a] == g[b]) add_rr(D.asmb + (size_t)g[a] * (kBlk * kBlk), sl[a], sl[b], kr, w[a] * w[b]);
+        for (int l = 1; l < D.nlev; ++l) {
+            int nd[4];
+            double W[4] = {0.0, 0.0, 0.0, 0.0};
+            int m = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (a >= nvv) break;
+                const int nn = D.node_of_vert[l][vid[a]];
+                int kk = m;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u < m && nd[u] == nn && kk == m) kk = u;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u == kk) {
+                        if (kk == m) nd[u] = nn;
+                        W[u] += w[a];
+                    }
+                if (kk == m) ++m;
             }
+            if (nvv == 4 && m == 1) continue;
+            double* Ab = D.asmbc + (size_t)(D.blk_off[l] - D.blk_off[1]) * (kBlk * kBlk);
+            int ng[4], ns[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ng[u] = u < m ? D.grp_of_node[l][nd[u]] : -1;
+                ns[u] = u < m ? D.slot_of_node[l][nd[u]] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (u < m && v < m && ng[u] == ng[v])
+                        add_rr(Ab + (size_t)ng[u] * (kBlk * kBlk), ns[u], ns[v], kr, W[u] * W[v]);
+        }
     }
 }
 
@@ -1235,7 +1285,10 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
     KL(k_init_blocks<R><<<nblk((long long)nb * (kBlk * kBlk / 4), 256), 256, 0, st>>>(D, nb0, nb));
     KL(k_tet_hessian<R><<<nblk(D.nt, 64), 64, 0, st>>>(D, x));
     KL(k_assemble_tets0<R><<<nblk(D.nt), kT, 0, st>>>(D));
-    if (D.nctgt > 0) KL(k_assemble_coarse<R><<<nblk(32LL * D.nctgt, 256), 256, 0, st>>>(D));
+    if (D.nitem > 0) {
+        KL(k_asm_contrib<R><<<nblk(D.nt), kT, 0, st>>>(D));
+        KL(k_asm_sum<R><<<nblk(32LL * D.nitem, 256), 256, 0, st>>>(D));
+    }
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
     // blocks are assembled in FP64 and inverted in the bulk precision R (FP32
     // in the mixed mode: B300's FP64 rate, about two FMAs per clock per SM,
