@@ -33,6 +33,11 @@ namespace {
 
 constexpr int kT = 128;
 constexpr int kMaxCells = 64;
+// Grid queries: kSplit threads per query primitive share its bucket entries
+// (and the large-box and brute-force lists) round-robin, so one crowded
+// neighbourhood is not one thread's serial walk; every entry is still visited
+// by exactly one of them.
+constexpr int kSplit = 8;
 constexpr int kCcdPasses = 8;   // verification passes before the uniform fallback
 
 inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
@@ -243,14 +248,15 @@ __device__ void ee_try(const Dev<R>& D, const double* x, const ContactBuf& C, in
 
 template <class R>
 __global__ void k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
-    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (qi >= D.nsv) return;
     int pv = D.sv[qi];
     double px = x[3 * pv], py = x[3 * pv + 1], pz = x[3 * pv + 2];
     double inv = 1.0 / *D.cellsz;
     unsigned long long cc = pack_cell(cellc(px, inv), cellc(py, inv), cellc(pz, inv));
     int bk = bucket_of(cc, D.nbuckets);
-    for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+    for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
         if (D.gcell[e] != cc) continue;
         int f = D.gentry[e];
         const double* b = D.pbox + 6 * (size_t)f;
@@ -258,7 +264,7 @@ __global__ void k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) 
         pt_try(D, x, C, pv, f);
     }
     int nl = *D.gnlarge;
-    for (int k = 0; k < nl; ++k) {
+    for (int k = sub; k < nl; k += kSplit) {
         int f = D.glarge[k];
         const double* b = D.pbox + 6 * (size_t)f;
         if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
@@ -269,7 +275,8 @@ __global__ void k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) 
 // EE: query edge i (plain box) against stored edges j > i (boxes inflated)
 template <class R>
 __global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int* gin) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (i >= D.nse) return;
     int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
     double lo[3], hi[3];
@@ -280,7 +287,7 @@ __global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, 
     long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
     if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
     if (nc > kMaxCells) {
-        for (int j = i + 1; j < D.nse; ++j) {
+        for (int j = i + 1 + sub; j < D.nse; j += kSplit) {
             const double* b = D.pbox + 6 * (size_t)j;
             if (overlap(lo, hi, b, b + 3)) ee_try(D, x, C, i, j);
         }
@@ -291,7 +298,7 @@ __global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, 
             for (int c = k0; c <= k1; ++c) {
                 unsigned long long cc = pack_cell(a, bb, c);
                 int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
                     if (D.gcell[e] != cc) continue;
                     int j = D.gentry[e];
                     if (j <= i) continue;
@@ -305,7 +312,7 @@ __global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, 
                 }
             }
     int nl = *D.gnlarge;
-    for (int k = 0; k < nl; ++k) {
+    for (int k = sub; k < nl; k += kSplit) {
         int j = D.glarge[k];
         if (j <= i) continue;
         const double* b = D.pbox + 6 * (size_t)j;
@@ -402,22 +409,48 @@ __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
     // make, with every vertex scaled anywhere in [0, 1], keeps alpha = 1 and
     // can never be violated by mixed per-subdomain steps: it is skipped
     // (FP32 lower bound on d0, sum of the two primitives' largest |p|).
+    //
+    // Otherwise its own step bound alpha_l = (1 - s) d0 / l uses l, the
+    // largest relative displacement between a vertex of one primitive and one
+    // of the other: where FP32 bounds already give d0 (1 - s) > l, the FP64
+    // walk would return exactly 1 (CUBICSAFE starts at alpha_l >= 1), so it is
+    // not run. A pair inside one subdomain and one body moves with one common
+    // scale t in [0, 1] under every step the line search tries (per subdomain,
+    // per body, uniform), so that bound alone also keeps it safe and it needs
+    // no verification.
+    const int g0 = D.grp0[v[0]], g1 = D.grp0[v[1]], g2 = D.grp0[v[2]], g3 = D.grp0[v[3]];
+    const int b0 = D.body[v[0]], b1 = D.body[v[1]], b2 = D.body[v[2]], b3 = D.body[v[3]];
+    const bool one_scale = g1 == g0 && g2 == g0 && g3 == g0 && b1 == b0 && b2 == b0 && b3 == b0;
+    bool whole_step = false;
     {
+        float P[4][3];
         float pa = 0.f, pb = 0.f;
         for (int j = 0; j < 4; ++j) {
             const R* q = D.p + 3 * v[j];
-            float m = sqrtf((float)q[0] * (float)q[0] + (float)q[1] * (float)q[1] + (float)q[2] * (float)q[2]);
+            P[j][0] = (float)q[0];
+            P[j][1] = (float)q[1];
+            P[j][2] = (float)q[2];
+            float m = sqrtf(P[j][0] * P[j][0] + P[j][1] * P[j][1] + P[j][2] * P[j][2]);
             if ((kind == 0 && j == 0) || (kind == 1 && j < 2))
                 pa = fmaxf(pa, m);
             else
                 pb = fmaxf(pb, m);
         }
-        float lmix = 1.001f * (pa + pb);
-        if (pair_dist_lb(kind, v, D.x) * (1.f - (float)D.ccd_shrink) > lmix) return;
+        const float lim = pair_dist_lb(kind, v, D.x) * (1.f - (float)D.ccd_shrink);
+        if (lim > 1.001f * (pa + pb)) return;
+        // primitive A: vertex 0 (PT) or 0, 1 (EE); B: the rest
+        float lr = 0.f;
+        for (int i = 0; i < (kind == 0 ? 1 : 2); ++i)
+            for (int j = (kind == 0 ? 1 : 2); j < 4; ++j) {
+                const float dx = P[i][0] - P[j][0], dy = P[i][1] - P[j][1], dz = P[i][2] - P[j][2];
+                lr = fmaxf(lr, sqrtf(dx * dx + dy * dy + dz * dz));
+            }
+        // FP32 rounding of p and of the differences: a margin of 1e-3 of the
+        // absolute displacements covers it many times over
+        whole_step = lim > 1.001f * lr + 1e-3f * (pa + pb);
+        if (one_scale && whole_step) return;
     }
-    double a = pair_alpha(D, kind, v, D.x, D.p, nullptr);
-    int g0 = D.grp0[v[0]], g1 = D.grp0[v[1]], g2 = D.grp0[v[2]], g3 = D.grp0[v[3]];
-    int b0 = D.body[v[0]], b1 = D.body[v[1]], b2 = D.body[v[2]], b3 = D.body[v[3]];
+    const double a = whole_step ? 1.0 : pair_alpha(D, kind, v, D.x, D.p, nullptr);
     if (a < 1.0) {
         atomicMinPos(&D.alpha[g0], a);
         if (g1 != g0) atomicMinPos(&D.alpha[g1], a);
@@ -429,7 +462,7 @@ __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
         if (b3 != b0 && b3 != b1 && b3 != b2) atomicMinPos(&D.alpha_b[b3], a);
     }
     // keep every pair that straddles subdomains or bodies for verification
-    if (!(g1 == g0 && g2 == g0 && g3 == g0) || !(b1 == b0 && b2 == b0 && b3 == b0)) {
+    if (!one_scale) {
         int k = *(volatile int*)&D.S->n_straddle < D.straddle_cap ? atomicAdd(&D.S->n_straddle, 1) : D.straddle_cap;
         if (k < D.straddle_cap) {
             D.str_v[k] = make_int4(v[0], v[1], v[2], v[3]);
@@ -442,7 +475,8 @@ __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
 
 template <class R>
 __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
-    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (qi >= D.nsv) return;
     int pv = D.sv[qi];
     double lo[3], hi[3];
@@ -458,7 +492,7 @@ __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
         ccd_pair(D, 0, v);
     };
     if (nc > kMaxCells) {
-        for (int f = 0; f < D.nsf; ++f) {
+        for (int f = sub; f < D.nsf; f += kSplit) {
             const double* b = D.pbox + 6 * (size_t)f;
             if (overlap(lo, hi, b, b + 3)) visit(f);
         }
@@ -469,7 +503,7 @@ __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
             for (int c = k0; c <= k1; ++c) {
                 unsigned long long cc = pack_cell(a, bb, c);
                 int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
                     if (D.gcell[e] != cc) continue;
                     int f = D.gentry[e];
                     const double* b = D.pbox + 6 * (size_t)f;
@@ -481,7 +515,7 @@ __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
                 }
             }
     int nl = *D.gnlarge;
-    for (int k = 0; k < nl; ++k) {
+    for (int k = sub; k < nl; k += kSplit) {
         int f = D.glarge[k];
         const double* b = D.pbox + 6 * (size_t)f;
         if (overlap(lo, hi, b, b + 3)) visit(f);
@@ -490,7 +524,8 @@ __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
 
 template <class R>
 __global__ void k_ccd_ee(Dev<R> D, const int* gin) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (i >= D.nse) return;
     int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
     double lo[3], hi[3];
@@ -506,7 +541,7 @@ __global__ void k_ccd_ee(Dev<R> D, const int* gin) {
         ccd_pair(D, 1, v);
     };
     if (nc > kMaxCells) {
-        for (int j = i + 1; j < D.nse; ++j) {
+        for (int j = i + 1 + sub; j < D.nse; j += kSplit) {
             const double* b = D.pbox + 6 * (size_t)j;
             if (overlap(lo, hi, b, b + 3)) visit(j);
         }
@@ -517,7 +552,7 @@ __global__ void k_ccd_ee(Dev<R> D, const int* gin) {
             for (int c = k0; c <= k1; ++c) {
                 unsigned long long cc = pack_cell(a, bb, c);
                 int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
                     if (D.gcell[e] != cc) continue;
                     int j = D.gentry[e];
                     if (j <= i) continue;
@@ -530,7 +565,7 @@ __global__ void k_ccd_ee(Dev<R> D, const int* gin) {
                 }
             }
     int nl = *D.gnlarge;
-    for (int k = 0; k < nl; ++k) {
+    for (int k = sub; k < nl; k += kSplit) {
         int j = D.glarge[k];
         if (j <= i) continue;
         const double* b = D.pbox + 6 * (size_t)j;
@@ -581,14 +616,15 @@ __device__ __forceinline__ void append_pair(int2* list, int* count, int cap, int
 
 template <class R>
 __global__ void k_cand_pt(Dev<R> D, const double* __restrict__ x) {
-    int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (qi >= D.nsv) return;
     int pv = D.sv[qi];
     double px = x[3 * pv], py = x[3 * pv + 1], pz = x[3 * pv + 2];
     double inv = 1.0 / *D.cellsz;
     unsigned long long cc = pack_cell(cellc(px, inv), cellc(py, inv), cellc(pz, inv));
     int bk = bucket_of(cc, D.nbuckets);
-    for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+    for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
         if (D.gcell[e] != cc) continue;
         int f = D.gentry[e];
         const double* b = D.pbox + 6 * (size_t)f;
@@ -597,7 +633,7 @@ __global__ void k_cand_pt(Dev<R> D, const double* __restrict__ x) {
         append_pair(D.cand_pt, &D.cand_n[0], D.cand_cap, pv, f);
     }
     int nl = *D.gnlarge;
-    for (int k = 0; k < nl; ++k) {
+    for (int k = sub; k < nl; k += kSplit) {
         int f = D.glarge[k];
         const double* b = D.pbox + 6 * (size_t)f;
         if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
@@ -614,7 +650,8 @@ __device__ __forceinline__ bool edges_adjacent(const Dev<R>& D, int i, int j) {
 
 template <class R>
 __global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (i >= D.nse) return;
     int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
     double lo[3], hi[3];
@@ -625,7 +662,7 @@ __global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
     long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
     if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
     if (nc > kMaxCells) {
-        for (int j = i + 1; j < D.nse; ++j) {
+        for (int j = i + 1 + sub; j < D.nse; j += kSplit) {
             const double* b = D.pbox + 6 * (size_t)j;
             if (overlap(lo, hi, b, b + 3) && !edges_adjacent(D, i, j))
                 append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
@@ -637,7 +674,7 @@ __global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
             for (int c = k0; c <= k1; ++c) {
                 unsigned long long cc = pack_cell(a, bb, c);
                 int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk]; e < D.gstart[bk + 1]; ++e) {
+                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
                     if (D.gcell[e] != cc) continue;
                     int j = D.gentry[e];
                     if (j <= i) continue;
@@ -651,7 +688,7 @@ __global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
                 }
             }
     int nl = *D.gnlarge;
-    for (int k = 0; k < nl; ++k) {
+    for (int k = sub; k < nl; k += kSplit) {
         int j = D.glarge[k];
         if (j <= i) continue;
         const double* b = D.pbox + 6 * (size_t)j;
@@ -849,9 +886,9 @@ void launch_detect(const Dev<R>& D, const double* x, const ContactBuf& C, cudaSt
     KL(k_reset_detect<R><<<1, 1, 0, st>>>(D, C));
     int* gin = D.gin;
     build_grid<R>(D, D.sf, 3, D.nsf, x, nullptr, D.dhat, gin, false, st);
-    if (D.nsv) KL(k_prox_pt<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
+    if (D.nsv) KL(k_prox_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, x, C));
     build_grid<R>(D, D.se, 2, D.nse, x, nullptr, D.dhat, gin, false, st);
-    if (D.nse) KL(k_prox_ee<R><<<nblk(D.nse), kT, 0, st>>>(D, x, C, gin));
+    if (D.nse) KL(k_prox_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, x, C, gin));
     if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
 }
 
@@ -863,9 +900,9 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
     int* gin = D.gin;
     build_grid<R>(D, D.sf, 3, D.nsf, D.x, D.p, 0.0, gin, true, st);
-    if (D.nsv) KL(k_ccd_pt<R><<<nblk(D.nsv), kT, 0, st>>>(D, gin));
+    if (D.nsv) KL(k_ccd_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, gin));
     build_grid<R>(D, D.se, 2, D.nse, D.x, D.p, 0.0, gin, true, st);
-    if (D.nse) KL(k_ccd_ee<R><<<nblk(D.nse), kT, 0, st>>>(D, gin));
+    if (D.nse) KL(k_ccd_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, gin));
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     Scalars* S = D.S;
     Grouping sub{D.grp0, D.alpha, D.shrink, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes, &S->alpha_min,
@@ -891,8 +928,8 @@ void launch_cand_build(const Dev<R>& D, const double* x, double delta, cudaStrea
         if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, x, (const R*)nullptr, infl, gin));
         scan_exclusive(D.gcount, D.gstart, D.nbuckets, D.gtmp, st);
         if (nprim > 0) KL(k_grid_fill<R><<<nblk(nprim), kT, 0, st>>>(D, nprim, gin));
-        if (pass == 0 && D.nsv) KL(k_cand_pt<R><<<nblk(D.nsv), kT, 0, st>>>(D, x));
-        if (pass == 1 && D.nse) KL(k_cand_ee<R><<<nblk(D.nse), kT, 0, st>>>(D, x));
+        if (pass == 0 && D.nsv) KL(k_cand_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, x));
+        if (pass == 1 && D.nse) KL(k_cand_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, x));
     }
     cudaMemcpyAsync(D.xref, x, sizeof(double) * 3 * (size_t)D.nv, cudaMemcpyDeviceToDevice, st);
 }
