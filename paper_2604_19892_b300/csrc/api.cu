@@ -436,7 +436,10 @@ int setup_dev(ipc_scene* s) {
     D.gnlarge = A.arr<int>(1);
     D.gin = A.arr<int>(nprim);
     D.gtmp = A.arr<int>(std::max(D.nbuckets, m.ngroups[0]) / 1024 + 16);
-    D.pbox = A.arr<double>(6 * (size_t)nprim);
+    D.pbox = A.arr<float4>(2 * (size_t)nprim);
+    D.xf = A.arr<float4>(m.nv);
+    D.xpf = A.arr<float4>(m.nv);
+    D.cellinv = A.arr<float>(1);
     D.cellsz = A.arr<double>(1);
     D.cand_cap = 48 * (D.nsv + D.nse) + 4096;
     D.xref = A.arr<double>(3 * (size_t)m.nv);

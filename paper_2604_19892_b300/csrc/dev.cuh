@@ -167,7 +167,10 @@ struct Dev {
     int* gnlarge;
     int* gin;                              // per stored primitive: 1 if binned
     int* gtmp;                             // scan temporaries
-    double* pbox;                          // per stored primitive: lo(3) hi(3)
+    float4* pbox;                          // per stored primitive: FP32 lo, hi (grown by the error bounds)
+    float4* xf;                            // FP32 surface positions at the evaluation point (.w: error bound)
+    float4* xpf;                           // FP32 surface positions at x + p (CCD), else a copy of xf
+    float* cellinv;                        // 1 / cell size, FP32
     double* cellsz;                        // scalar: cell size of the current build
     // cached candidate pairs (built at xref with margin delta): every PT / EE
     // pair whose query box at xref overlaps the stored box inflated by

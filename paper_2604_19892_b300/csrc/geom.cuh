@@ -183,22 +183,6 @@ __device__ inline float ee_dist2_f(f3 p1, f3 q1, f3 p2, f3 q2) {
     return fdot(dd, dd);
 }
 
-// lower bound on the distance of pair v (PT: p, t0, t1, t2; EE: a0, a1, b0,
-// b1) at positions x
-__device__ inline float pair_dist_lb(int kind, const int v[4], const double* x) {
-    const double o0 = x[3 * v[0]], o1 = x[3 * v[0] + 1], o2 = x[3 * v[0] + 2];
-    f3 P[4];
-    float L = 0.f;
-    for (int j = 0; j < 4; ++j) {
-        P[j] = {(float)(x[3 * v[j]] - o0), (float)(x[3 * v[j] + 1] - o1), (float)(x[3 * v[j] + 2] - o2)};
-        L = fmaxf(L, fmaxf(fabsf(P[j].x), fmaxf(fabsf(P[j].y), fabsf(P[j].z))));
-    }
-    float d2 = kind == 0 ? pt_dist2_f(P[0], P[1], P[2], P[3]) : ee_dist2_f(P[0], P[1], P[2], P[3]);
-    float m = d2 - 1e-6f * L * L;
-    if (!(m > 0.f)) return 0.f;
-    return 0.999f * sqrtf(m);
-}
-
 // f(t) = det[A + t dA, B + t dB, C + t dC] = c[0] + c[1] t + c[2] t^2 + c[3] t^3
 __device__ inline void cubic_of(d3 A, d3 dA, d3 B, d3 dB, d3 C, d3 dC, double c[4]) {
     d3 BC = cross(B, C);

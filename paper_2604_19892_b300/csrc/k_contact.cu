@@ -42,7 +42,7 @@ constexpr int kCcdPasses = 8;   // verification passes before the uniform fallba
 
 inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
 
-__device__ __forceinline__ int cellc(double v, double inv) { return (int)floor(v * inv); }
+__device__ __forceinline__ int cellc(float v, float inv) { return (int)floorf(v * inv); }
 
 __device__ __forceinline__ unsigned long long pack_cell(int i, int j, int k) {
     const int off = 1 << 20;
@@ -52,59 +52,176 @@ __device__ __forceinline__ unsigned long long pack_cell(int i, int j, int k) {
 
 __device__ __forceinline__ int bucket_of(unsigned long long c, int nb) { return (int)(mix64(c) & (unsigned long long)(nb - 1)); }
 
-// box of a primitive with vertices vid[0..n): positions x, optional sweep by p
+// ------------------------------------------------------- FP32 broad phase
+//
+// Every box and grid cell is computed in FP32 from FP32 copies of the surface
+// positions (x, and x + p for CCD), each copy carrying in .w a bound on its
+// rounding error. Boxes are grown by that bound, so an FP32 box contains the
+// exact one and FP32 boxes that miss each other prove the exact boxes miss:
+// the candidate pairs are a superset of the exact-box ones, and every pair
+// then takes the FP64 tests as before (same contacts, same step bounds). B300
+// runs FP64 at a small fraction of its FP32 rate, and the broad phase visits
+// every neighbour of every primitive.
+
+// FP32 copies of the surface positions at x and at x + p (x again without p)
 template <class R>
-__device__ __forceinline__ void prim_box(const double* x, const R* p, const int* vid, int n, double infl, double lo[3],
-                                         double hi[3]) {
-    for (int r = 0; r < 3; ++r) {
-        lo[r] = 1e300;
-        hi[r] = -1e300;
+__global__ void k_vert_f32(Dev<R> D, const double* __restrict__ x, const R* __restrict__ p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D.nsv) return;
+    const int v = D.sv[i];
+    const double a0 = x[3 * v], a1 = x[3 * v + 1], a2 = x[3 * v + 2];
+    float4 f = make_float4((float)a0, (float)a1, (float)a2, 0.f);
+    float m = fmaxf(fabsf(f.x), fmaxf(fabsf(f.y), fabsf(f.z)));
+    float4 g = f;
+    if (p) {
+        g = make_float4((float)(a0 + (double)p[3 * v]), (float)(a1 + (double)p[3 * v + 1]),
+                        (float)(a2 + (double)p[3 * v + 2]), 0.f);
+        m = fmaxf(m, fmaxf(fabsf(g.x), fmaxf(fabsf(g.y), fabsf(g.z))));
     }
-    for (int k = 0; k < n; ++k)
-        for (int r = 0; r < 3; ++r) {
-            double a = x[3 * vid[k] + r];
-            double b = p ? a + (double)p[3 * vid[k] + r] : a;
-            double mn = fmin(a, b), mx = fmax(a, b);
-            lo[r] = fmin(lo[r], mn);
-            hi[r] = fmax(hi[r], mx);
-        }
+    // rounding to FP32 moves a coordinate by at most 2^-24 of its size; the
+    // bound covers that and the FP32 arithmetic on boxes and distances
+    const float e = 4e-7f * m + 1e-30f;
+    f.w = e;
+    g.w = e;
+    D.xf[v] = f;
+    D.xpf[v] = g;
+}
+
+// FP32 box of the primitive with vertices vid[0..n) over [x, x + p], grown by
+// infl (rounded up by the caller) and by the vertices' error bounds
+template <class R>
+__device__ __forceinline__ void prim_box(const Dev<R>& D, const int* vid, int n, float infl, float lo[3], float hi[3]) {
+    float e = 0.f;
+    lo[0] = lo[1] = lo[2] = 3.0e38f;
+    hi[0] = hi[1] = hi[2] = -3.0e38f;
+    for (int k = 0; k < n; ++k) {
+        const float4 a = D.xf[vid[k]], b = D.xpf[vid[k]];
+        lo[0] = fminf(lo[0], fminf(a.x, b.x));
+        lo[1] = fminf(lo[1], fminf(a.y, b.y));
+        lo[2] = fminf(lo[2], fminf(a.z, b.z));
+        hi[0] = fmaxf(hi[0], fmaxf(a.x, b.x));
+        hi[1] = fmaxf(hi[1], fmaxf(a.y, b.y));
+        hi[2] = fmaxf(hi[2], fmaxf(a.z, b.z));
+        e = fmaxf(e, a.w);
+    }
+    const float g = infl + e;
     for (int r = 0; r < 3; ++r) {
-        lo[r] -= infl;
-        hi[r] += infl;
+        lo[r] -= g;
+        hi[r] += g;
     }
 }
 
-__device__ __forceinline__ bool overlap(const double* lo1, const double* hi1, const double* lo2, const double* hi2) {
+template <class R>
+__device__ __forceinline__ void load_box(const Dev<R>& D, int j, float lo[3], float hi[3]) {
+    const float4 a = D.pbox[2 * (size_t)j], b = D.pbox[2 * (size_t)j + 1];
+    lo[0] = a.x;
+    lo[1] = a.y;
+    lo[2] = a.z;
+    hi[0] = b.x;
+    hi[1] = b.y;
+    hi[2] = b.z;
+}
+
+__device__ __forceinline__ bool overlap(const float* lo1, const float* hi1, const float* lo2, const float* hi2) {
     return !(hi1[0] < lo2[0] || hi2[0] < lo1[0] || hi1[1] < lo2[1] || hi2[1] < lo1[1] || hi1[2] < lo2[2] ||
              hi2[2] < lo1[2]);
 }
 
 // cell indices of the box fit in int (and the box is finite)
-__device__ __forceinline__ bool box_in_range(const double* lo, const double* hi, double inv) {
+__device__ __forceinline__ bool box_in_range(const float* lo, const float* hi, float inv) {
     bool ok = true;
-    for (int r = 0; r < 3; ++r) ok &= fabs(lo[r] * inv) < 1e9 && fabs(hi[r] * inv) < 1e9;
+    for (int r = 0; r < 3; ++r) ok &= fabsf(lo[r] * inv) < 1e9f && fabsf(hi[r] * inv) < 1e9f;
     return ok;
+}
+
+// Lower bound on the distance of pair v (PT: p, t0, t1, t2; EE: a0, a1, b0,
+// b1) from the FP32 positions: FP32 distance of the differences to vertex 0,
+// less a margin for the closest-point arithmetic (1e-6 of the squared local
+// extent, as the FP64 test would see it) and twice the position error bound.
+template <class R>
+__device__ __forceinline__ float pair_dist_lb(const Dev<R>& D, int kind, const int v[4]) {
+    const float4 o = D.xf[v[0]];
+    f3 P[4];
+    float L = 0.f, e = o.w;
+    for (int j = 0; j < 4; ++j) {
+        const float4 q = D.xf[v[j]];
+        P[j] = {q.x - o.x, q.y - o.y, q.z - o.z};
+        L = fmaxf(L, fmaxf(fabsf(P[j].x), fmaxf(fabsf(P[j].y), fabsf(P[j].z))));
+        e = fmaxf(e, q.w);
+    }
+    const float d2 = kind == 0 ? pt_dist2_f(P[0], P[1], P[2], P[3]) : ee_dist2_f(P[0], P[1], P[2], P[3]);
+    const float m = d2 - 1e-6f * L * L;
+    if (!(m > 0.f)) return 0.f;
+    return fmaxf(0.999f * sqrtf(m) - 2.f * e, 0.f);
+}
+
+// Visits every stored primitive j whose box overlaps the query box once:
+// the query walks its own cells and keeps a pair only in the cell holding
+// the low corner of the two boxes' intersection; boxes too large for the
+// grid are in a short list, and a query box too large for it scans all
+// nstored. Thread sub of kSplit takes every kSplit-th entry.
+template <class R, class F>
+__device__ __forceinline__ void grid_query(const Dev<R>& D, const float lo[3], const float hi[3], int nstored, int sub,
+                                           F&& visit) {
+    const float inv = *D.cellinv;
+    const int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
+    const int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
+    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
+    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
+    float blo[3], bhi[3];
+    if (nc > kMaxCells) {
+        for (int j = sub; j < nstored; j += kSplit) {
+            load_box(D, j, blo, bhi);
+            if (overlap(lo, hi, blo, bhi)) visit(j);
+        }
+        return;
+    }
+    for (int a = i0; a <= i1; ++a)
+        for (int bb = j0; bb <= j1; ++bb)
+            for (int c = k0; c <= k1; ++c) {
+                const unsigned long long cc = pack_cell(a, bb, c);
+                const int bk = bucket_of(cc, D.nbuckets);
+                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
+                    if (D.gcell[e] != cc) continue;
+                    const int j = D.gentry[e];
+                    load_box(D, j, blo, bhi);
+                    if (!overlap(lo, hi, blo, bhi)) continue;
+                    if (cellc(fmaxf(lo[0], blo[0]), inv) != a || cellc(fmaxf(lo[1], blo[1]), inv) != bb ||
+                        cellc(fmaxf(lo[2], blo[2]), inv) != c)
+                        continue;
+                    visit(j);
+                }
+            }
+    const int nl = *D.gnlarge;
+    for (int k = sub; k < nl; k += kSplit) {
+        const int j = D.glarge[k];
+        load_box(D, j, blo, bhi);
+        if (overlap(lo, hi, blo, bhi)) visit(j);
+    }
+}
+
+// infl as FP32, never below the FP64 value
+__host__ inline float round_up_f(double v) {
+    float f = (float)v;
+    if ((double)f < v) f = nextafterf(f, 3.0e38f);
+    return f;
 }
 
 // ---------------------------------------------------------------- grid build
 
 template <class R>
-__global__ void k_grid_count(Dev<R> D, const int* prims, int nper, int nprim, const double* x, const R* p, double infl,
-                             int* gin) {
+__global__ void k_grid_count(Dev<R> D, const int* prims, int nper, int nprim, float infl, int* gin) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nprim) return;
     int vid[3];
     for (int k = 0; k < nper; ++k) vid[k] = prims[nper * i + k];
-    double lo[3], hi[3];
-    prim_box(x, p, vid, nper, infl, lo, hi);
-    for (int r = 0; r < 3; ++r) {
-        D.pbox[6 * (size_t)i + r] = lo[r];
-        D.pbox[6 * (size_t)i + 3 + r] = hi[r];
-    }
-    double inv = 1.0 / *D.cellsz;
+    float lo[3], hi[3];
+    prim_box(D, vid, nper, infl, lo, hi);
+    D.pbox[2 * (size_t)i] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    D.pbox[2 * (size_t)i + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    const float inv = *D.cellinv;
     // a box outside the cell-index range (or not finite) goes to the large list
-    bool finite = true;
-    for (int r = 0; r < 3; ++r) finite &= fabs(lo[r] * inv) < 1e9 && fabs(hi[r] * inv) < 1e9;
+    const bool finite = box_in_range(lo, hi, inv);
     long long n0 = finite ? (long long)cellc(hi[0], inv) - cellc(lo[0], inv) + 1 : kMaxCells + 1;
     long long n1 = finite ? (long long)cellc(hi[1], inv) - cellc(lo[1], inv) + 1 : kMaxCells + 1;
     long long n2 = finite ? (long long)cellc(hi[2], inv) - cellc(lo[2], inv) + 1 : kMaxCells + 1;
@@ -131,9 +248,9 @@ template <class R>
 __global__ void k_grid_fill(Dev<R> D, int nprim, const int* gin) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nprim || !gin[i]) return;
-    const double* lo = D.pbox + 6 * (size_t)i;
-    const double* hi = lo + 3;
-    double inv = 1.0 / *D.cellsz;
+    float lo[3], hi[3];
+    load_box(D, i, lo, hi);
+    const float inv = *D.cellinv;
     int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
     int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
     for (int a = i0; a <= i1; ++a)
@@ -153,17 +270,17 @@ __global__ void k_set_cell(Dev<R> D, int ccd) {
     if (ccd) cs = fmax(cs, D.S->pmax);
     else cs = fmax(cs, 2.0 * D.dhat);
     *D.cellsz = cs;
+    *D.cellinv = (float)(1.0 / cs);
 }
 
 template <class R>
-void build_grid(const Dev<R>& D, const int* prims, int nper, int nprim, const double* x, const R* p, double infl,
-                int* gin, bool ccd, cudaStream_t st) {
+void build_grid(const Dev<R>& D, const int* prims, int nper, int nprim, float infl, int* gin, bool ccd, cudaStream_t st) {
     cudaMemsetAsync(D.gcount, 0, sizeof(int) * (D.nbuckets + 1), st);
     cudaMemsetAsync(D.gfill, 0, sizeof(int) * D.nbuckets, st);
     cudaMemsetAsync(D.gtotal, 0, sizeof(int), st);
     cudaMemsetAsync(D.gnlarge, 0, sizeof(int), st);
     KL(k_set_cell<R><<<1, 1, 0, st>>>(D, ccd ? 1 : 0));
-    if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, x, p, infl, gin));
+    if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, infl, gin));
     scan_exclusive(D.gcount, D.gstart, D.nbuckets, D.gtmp, st);
     if (nprim > 0) KL(k_grid_fill<R><<<nblk(nprim), kT, 0, st>>>(D, nprim, gin));
 }
@@ -207,7 +324,7 @@ __device__ void pt_try(const Dev<R>& D, const double* x, const ContactBuf& C, in
     if (pv == t0 || pv == t1 || pv == t2) return;
     {
         const int v[4] = {pv, t0, t1, t2};
-        if (pair_dist_lb(0, v, x) >= D.dhat) return;  // FP32 prefilter
+        if (pair_dist_lb(D, 0, v) >= D.dhat) return;  // FP32 prefilter
     }
     d3 P = ld3(x + 3 * pv), A = ld3(x + 3 * t0), B = ld3(x + 3 * t1), Cc = ld3(x + 3 * t2);
     double w[3];
@@ -227,7 +344,7 @@ __device__ void ee_try(const Dev<R>& D, const double* x, const ContactBuf& C, in
     if (a0 == b0 || a0 == b1 || a1 == b0 || a1 == b1) return;
     {
         const int v[4] = {a0, a1, b0, b1};
-        if (pair_dist_lb(1, v, x) >= D.dhat) return;  // FP32 prefilter
+        if (pair_dist_lb(D, 1, v) >= D.dhat) return;  // FP32 prefilter
     }
     d3 A0 = ld3(x + 3 * a0), A1 = ld3(x + 3 * a1), B0 = ld3(x + 3 * b0), B1 = ld3(x + 3 * b1);
     d3 u = A1 - A0, v = B1 - B0;
@@ -251,73 +368,23 @@ __global__ void k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) 
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (qi >= D.nsv) return;
-    int pv = D.sv[qi];
-    double px = x[3 * pv], py = x[3 * pv + 1], pz = x[3 * pv + 2];
-    double inv = 1.0 / *D.cellsz;
-    unsigned long long cc = pack_cell(cellc(px, inv), cellc(py, inv), cellc(pz, inv));
-    int bk = bucket_of(cc, D.nbuckets);
-    for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
-        if (D.gcell[e] != cc) continue;
-        int f = D.gentry[e];
-        const double* b = D.pbox + 6 * (size_t)f;
-        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
-        pt_try(D, x, C, pv, f);
-    }
-    int nl = *D.gnlarge;
-    for (int k = sub; k < nl; k += kSplit) {
-        int f = D.glarge[k];
-        const double* b = D.pbox + 6 * (size_t)f;
-        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
-        pt_try(D, x, C, pv, f);
-    }
+    const int pv = D.sv[qi];
+    float lo[3], hi[3];
+    prim_box(D, &pv, 1, 0.f, lo, hi);
+    grid_query(D, lo, hi, D.nsf, sub, [&](int f) { pt_try(D, x, C, pv, f); });
 }
 
-// EE: query edge i (plain box) against stored edges j > i (boxes inflated)
 template <class R>
 __global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int* gin) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (i >= D.nse) return;
-    int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
-    double lo[3], hi[3];
-    prim_box<R>(x, nullptr, vid, 2, 0.0, lo, hi);
-    double inv = 1.0 / *D.cellsz;
-    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
-    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
-    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
-    if (nc > kMaxCells) {
-        for (int j = i + 1 + sub; j < D.nse; j += kSplit) {
-            const double* b = D.pbox + 6 * (size_t)j;
-            if (overlap(lo, hi, b, b + 3)) ee_try(D, x, C, i, j);
-        }
-        return;
-    }
-    for (int a = i0; a <= i1; ++a)
-        for (int bb = j0; bb <= j1; ++bb)
-            for (int c = k0; c <= k1; ++c) {
-                unsigned long long cc = pack_cell(a, bb, c);
-                int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
-                    if (D.gcell[e] != cc) continue;
-                    int j = D.gentry[e];
-                    if (j <= i) continue;
-                    const double* b = D.pbox + 6 * (size_t)j;
-                    if (!overlap(lo, hi, b, b + 3)) continue;
-                    // keep the pair only in the cell of the intersection's low corner
-                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
-                        cellc(fmax(lo[2], b[2]), inv) != c)
-                        continue;
-                    ee_try(D, x, C, i, j);
-                }
-            }
-    int nl = *D.gnlarge;
-    for (int k = sub; k < nl; k += kSplit) {
-        int j = D.glarge[k];
-        if (j <= i) continue;
-        const double* b = D.pbox + 6 * (size_t)j;
-        if (overlap(lo, hi, b, b + 3)) ee_try(D, x, C, i, j);
-    }
+    const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+    float lo[3], hi[3];
+    prim_box(D, vid, 2, 0.f, lo, hi);
+    grid_query(D, lo, hi, D.nse, sub, [&](int j) {
+        if (j > i) ee_try(D, x, C, i, j);
+    });
 }
 
 template <class R>
@@ -436,7 +503,7 @@ __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
             else
                 pb = fmaxf(pb, m);
         }
-        const float lim = pair_dist_lb(kind, v, D.x) * (1.f - (float)D.ccd_shrink);
+        const float lim = pair_dist_lb(D, kind, v) * (1.f - (float)D.ccd_shrink);
         if (lim > 1.001f * (pa + pb)) return;
         // primitive A: vertex 0 (PT) or 0, 1 (EE); B: the rest
         float lr = 0.f;
@@ -478,48 +545,14 @@ __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (qi >= D.nsv) return;
-    int pv = D.sv[qi];
-    double lo[3], hi[3];
-    prim_box(D.x, D.p, &pv, 1, 0.0, lo, hi);
-    double inv = 1.0 / *D.cellsz;
-    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
-    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
-    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
-    auto visit = [&](int f) {
+    const int pv = D.sv[qi];
+    float lo[3], hi[3];
+    prim_box(D, &pv, 1, 0.f, lo, hi);
+    grid_query(D, lo, hi, D.nsf, sub, [&](int f) {
         int v[4] = {pv, D.sf[3 * f], D.sf[3 * f + 1], D.sf[3 * f + 2]};
         if (pv == v[1] || pv == v[2] || pv == v[3]) return;
         ccd_pair(D, 0, v);
-    };
-    if (nc > kMaxCells) {
-        for (int f = sub; f < D.nsf; f += kSplit) {
-            const double* b = D.pbox + 6 * (size_t)f;
-            if (overlap(lo, hi, b, b + 3)) visit(f);
-        }
-        return;
-    }
-    for (int a = i0; a <= i1; ++a)
-        for (int bb = j0; bb <= j1; ++bb)
-            for (int c = k0; c <= k1; ++c) {
-                unsigned long long cc = pack_cell(a, bb, c);
-                int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
-                    if (D.gcell[e] != cc) continue;
-                    int f = D.gentry[e];
-                    const double* b = D.pbox + 6 * (size_t)f;
-                    if (!overlap(lo, hi, b, b + 3)) continue;
-                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
-                        cellc(fmax(lo[2], b[2]), inv) != c)
-                        continue;
-                    visit(f);
-                }
-            }
-    int nl = *D.gnlarge;
-    for (int k = sub; k < nl; k += kSplit) {
-        int f = D.glarge[k];
-        const double* b = D.pbox + 6 * (size_t)f;
-        if (overlap(lo, hi, b, b + 3)) visit(f);
-    }
+    });
 }
 
 template <class R>
@@ -527,50 +560,15 @@ __global__ void k_ccd_ee(Dev<R> D, const int* gin) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (i >= D.nse) return;
-    int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
-    double lo[3], hi[3];
-    prim_box(D.x, D.p, vid, 2, 0.0, lo, hi);
-    double inv = 1.0 / *D.cellsz;
-    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
-    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
-    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
-    auto visit = [&](int j) {
+    const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+    float lo[3], hi[3];
+    prim_box(D, vid, 2, 0.f, lo, hi);
+    grid_query(D, lo, hi, D.nse, sub, [&](int j) {
+        if (j <= i) return;
         int v[4] = {vid[0], vid[1], D.se[2 * j], D.se[2 * j + 1]};
         if (v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3]) return;
         ccd_pair(D, 1, v);
-    };
-    if (nc > kMaxCells) {
-        for (int j = i + 1 + sub; j < D.nse; j += kSplit) {
-            const double* b = D.pbox + 6 * (size_t)j;
-            if (overlap(lo, hi, b, b + 3)) visit(j);
-        }
-        return;
-    }
-    for (int a = i0; a <= i1; ++a)
-        for (int bb = j0; bb <= j1; ++bb)
-            for (int c = k0; c <= k1; ++c) {
-                unsigned long long cc = pack_cell(a, bb, c);
-                int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
-                    if (D.gcell[e] != cc) continue;
-                    int j = D.gentry[e];
-                    if (j <= i) continue;
-                    const double* b = D.pbox + 6 * (size_t)j;
-                    if (!overlap(lo, hi, b, b + 3)) continue;
-                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
-                        cellc(fmax(lo[2], b[2]), inv) != c)
-                        continue;
-                    visit(j);
-                }
-            }
-    int nl = *D.gnlarge;
-    for (int k = sub; k < nl; k += kSplit) {
-        int j = D.glarge[k];
-        if (j <= i) continue;
-        const double* b = D.pbox + 6 * (size_t)j;
-        if (overlap(lo, hi, b, b + 3)) visit(j);
-    }
+    });
 }
 
 template <class R>
@@ -619,27 +617,13 @@ __global__ void k_cand_pt(Dev<R> D, const double* __restrict__ x) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (qi >= D.nsv) return;
-    int pv = D.sv[qi];
-    double px = x[3 * pv], py = x[3 * pv + 1], pz = x[3 * pv + 2];
-    double inv = 1.0 / *D.cellsz;
-    unsigned long long cc = pack_cell(cellc(px, inv), cellc(py, inv), cellc(pz, inv));
-    int bk = bucket_of(cc, D.nbuckets);
-    for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
-        if (D.gcell[e] != cc) continue;
-        int f = D.gentry[e];
-        const double* b = D.pbox + 6 * (size_t)f;
-        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
-        if (pv == D.sf[3 * f] || pv == D.sf[3 * f + 1] || pv == D.sf[3 * f + 2]) continue;
+    const int pv = D.sv[qi];
+    float lo[3], hi[3];
+    prim_box(D, &pv, 1, 4.f * D.xf[pv].w, lo, hi);
+    grid_query(D, lo, hi, D.nsf, sub, [&](int f) {
+        if (pv == D.sf[3 * f] || pv == D.sf[3 * f + 1] || pv == D.sf[3 * f + 2]) return;
         append_pair(D.cand_pt, &D.cand_n[0], D.cand_cap, pv, f);
-    }
-    int nl = *D.gnlarge;
-    for (int k = sub; k < nl; k += kSplit) {
-        int f = D.glarge[k];
-        const double* b = D.pbox + 6 * (size_t)f;
-        if (px < b[0] || px > b[3] || py < b[1] || py > b[4] || pz < b[2] || pz > b[5]) continue;
-        if (pv == D.sf[3 * f] || pv == D.sf[3 * f + 1] || pv == D.sf[3 * f + 2]) continue;
-        append_pair(D.cand_pt, &D.cand_n[0], D.cand_cap, pv, f);
-    }
+    });
 }
 
 template <class R>
@@ -653,51 +637,20 @@ __global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
     if (i >= D.nse) return;
-    int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
-    double lo[3], hi[3];
-    prim_box<R>(x, nullptr, vid, 2, 0.0, lo, hi);
-    double inv = 1.0 / *D.cellsz;
-    int i0 = cellc(lo[0], inv), j0 = cellc(lo[1], inv), k0 = cellc(lo[2], inv);
-    int i1 = cellc(hi[0], inv), j1 = cellc(hi[1], inv), k1 = cellc(hi[2], inv);
-    long long nc = ((long long)i1 - i0 + 1) * ((long long)j1 - j0 + 1) * ((long long)k1 - k0 + 1);
-    if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
-    if (nc > kMaxCells) {
-        for (int j = i + 1 + sub; j < D.nse; j += kSplit) {
-            const double* b = D.pbox + 6 * (size_t)j;
-            if (overlap(lo, hi, b, b + 3) && !edges_adjacent(D, i, j))
-                append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
-        }
-        return;
-    }
-    for (int a = i0; a <= i1; ++a)
-        for (int bb = j0; bb <= j1; ++bb)
-            for (int c = k0; c <= k1; ++c) {
-                unsigned long long cc = pack_cell(a, bb, c);
-                int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
-                    if (D.gcell[e] != cc) continue;
-                    int j = D.gentry[e];
-                    if (j <= i) continue;
-                    const double* b = D.pbox + 6 * (size_t)j;
-                    if (!overlap(lo, hi, b, b + 3)) continue;
-                    if (cellc(fmax(lo[0], b[0]), inv) != a || cellc(fmax(lo[1], b[1]), inv) != bb ||
-                        cellc(fmax(lo[2], b[2]), inv) != c)
-                        continue;
-                    if (edges_adjacent(D, i, j)) continue;
-                    append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
-                }
-            }
-    int nl = *D.gnlarge;
-    for (int k = sub; k < nl; k += kSplit) {
-        int j = D.glarge[k];
-        if (j <= i) continue;
-        const double* b = D.pbox + 6 * (size_t)j;
-        if (overlap(lo, hi, b, b + 3) && !edges_adjacent(D, i, j)) append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
-    }
+    const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+    float lo[3], hi[3];
+    prim_box(D, vid, 2, 4.f * fmaxf(D.xf[vid[0]].w, D.xf[vid[1]].w), lo, hi);
+    grid_query(D, lo, hi, D.nse, sub, [&](int j) {
+        if (j > i && !edges_adjacent(D, i, j)) append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
+    });
 }
 
 template <class R>
-__global__ void k_set_cell_cand(Dev<R> D, double infl) { *D.cellsz = fmax(D.cell, 2.0 * infl); }
+__global__ void k_set_cell_cand(Dev<R> D, double infl) {
+    const double cs = fmax(D.cell, 2.0 * infl);
+    *D.cellsz = cs;
+    *D.cellinv = (float)(1.0 / cs);
+}
 
 template <class R>
 __global__ void k_prox_pt_list(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
@@ -723,9 +676,9 @@ __global__ void k_ccd_pt_list(Dev<R> D) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         int2 q = D.cand_pt[k];
         int v[4] = {q.x, D.sf[3 * q.y], D.sf[3 * q.y + 1], D.sf[3 * q.y + 2]};
-        double lo[3], hi[3], tlo[3], thi[3];
-        prim_box(D.x, D.p, v, 1, 0.0, lo, hi);
-        prim_box(D.x, D.p, v + 1, 3, 0.0, tlo, thi);
+        float lo[3], hi[3], tlo[3], thi[3];
+        prim_box(D, v, 1, 0.f, lo, hi);
+        prim_box(D, v + 1, 3, 0.f, tlo, thi);
         if (overlap(lo, hi, tlo, thi)) ccd_pair(D, 0, v);
     }
 }
@@ -736,9 +689,9 @@ __global__ void k_ccd_ee_list(Dev<R> D) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         int2 q = D.cand_ee[k];
         int v[4] = {D.se[2 * q.x], D.se[2 * q.x + 1], D.se[2 * q.y], D.se[2 * q.y + 1]};
-        double lo[3], hi[3], blo[3], bhi[3];
-        prim_box(D.x, D.p, v, 2, 0.0, lo, hi);
-        prim_box(D.x, D.p, v + 2, 2, 0.0, blo, bhi);
+        float lo[3], hi[3], blo[3], bhi[3];
+        prim_box(D, v, 2, 0.f, lo, hi);
+        prim_box(D, v + 2, 2, 0.f, blo, bhi);
         if (overlap(lo, hi, blo, bhi)) ccd_pair(D, 1, v);
     }
 }
@@ -884,10 +837,12 @@ void verify_groupings(const Dev<R>& D, const Grouping& sub, const Grouping& bod,
 template <class R>
 void launch_detect(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
     KL(k_reset_detect<R><<<1, 1, 0, st>>>(D, C));
+    if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, (const R*)nullptr));
     int* gin = D.gin;
-    build_grid<R>(D, D.sf, 3, D.nsf, x, nullptr, D.dhat, gin, false, st);
+    const float dh = round_up_f(D.dhat);
+    build_grid<R>(D, D.sf, 3, D.nsf, dh, gin, false, st);
     if (D.nsv) KL(k_prox_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, x, C));
-    build_grid<R>(D, D.se, 2, D.nse, x, nullptr, D.dhat, gin, false, st);
+    build_grid<R>(D, D.se, 2, D.nse, dh, gin, false, st);
     if (D.nse) KL(k_prox_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, x, C, gin));
     if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
 }
@@ -898,10 +853,11 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     KL(k_ccd_begin<R><<<1, 1, 0, st>>>(D));
     KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
     KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
+    if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
     int* gin = D.gin;
-    build_grid<R>(D, D.sf, 3, D.nsf, D.x, D.p, 0.0, gin, true, st);
+    build_grid<R>(D, D.sf, 3, D.nsf, 0.f, gin, true, st);
     if (D.nsv) KL(k_ccd_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, gin));
-    build_grid<R>(D, D.se, 2, D.nse, D.x, D.p, 0.0, gin, true, st);
+    build_grid<R>(D, D.se, 2, D.nse, 0.f, gin, true, st);
     if (D.nse) KL(k_ccd_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, gin));
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     Scalars* S = D.S;
@@ -916,6 +872,7 @@ template <class R>
 void launch_cand_build(const Dev<R>& D, const double* x, double delta, cudaStream_t st) {
     const double infl = D.dhat + 2.001 * delta;
     cudaMemsetAsync(D.cand_n, 0, 2 * sizeof(int), st);
+    if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, (const R*)nullptr));
     int* gin = D.gin;
     for (int pass = 0; pass < 2; ++pass) {
         const int* prims = pass == 0 ? D.sf : D.se;
@@ -925,7 +882,7 @@ void launch_cand_build(const Dev<R>& D, const double* x, double delta, cudaStrea
         cudaMemsetAsync(D.gtotal, 0, sizeof(int), st);
         cudaMemsetAsync(D.gnlarge, 0, sizeof(int), st);
         KL(k_set_cell_cand<R><<<1, 1, 0, st>>>(D, infl));
-        if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, x, (const R*)nullptr, infl, gin));
+        if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, round_up_f(infl), gin));
         scan_exclusive(D.gcount, D.gstart, D.nbuckets, D.gtmp, st);
         if (nprim > 0) KL(k_grid_fill<R><<<nblk(nprim), kT, 0, st>>>(D, nprim, gin));
         if (pass == 0 && D.nsv) KL(k_cand_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, x));
@@ -937,6 +894,7 @@ void launch_cand_build(const Dev<R>& D, const double* x, double delta, cudaStrea
 template <class R>
 void launch_detect_list(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
     KL(k_reset_detect<R><<<1, 1, 0, st>>>(D, C));
+    if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, (const R*)nullptr));
     KL(k_prox_pt_list<R><<<1184, kT, 0, st>>>(D, x, C));
     KL(k_prox_ee_list<R><<<1184, kT, 0, st>>>(D, x, C));
     if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
@@ -948,6 +906,7 @@ void launch_ccd_list(const Dev<R>& D, cudaStream_t st) {
     KL(k_ccd_begin<R><<<1, 1, 0, st>>>(D));
     KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
     KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
+    if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
     KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D));
     KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D));
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
