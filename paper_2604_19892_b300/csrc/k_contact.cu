@@ -765,7 +765,31 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
                 int v[4] = {q.x, q.y, q.z, q.w};
                 int g0 = G.of[v[0]];
                 if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) continue;
-                double rho = pair_alpha(D, D.str_t[k], v, D.x, D.p, G.alpha, G.of);
+                const int kind = D.str_t[k];
+                {
+                    // the FP64 walk returns exactly 1 where the FP32 distance
+                    // bound exceeds the largest relative displacement of the
+                    // actual motion alpha_g(v) p_v (CUBICSAFE starts at
+                    // alpha_l >= 1): skip it there
+                    float P[4][3], pm = 0.f;
+                    for (int j = 0; j < 4; ++j) {
+                        const float sj = (float)G.alpha[G.of[v[j]]];
+                        const R* q = D.p + 3 * v[j];
+                        P[j][0] = sj * (float)q[0];
+                        P[j][1] = sj * (float)q[1];
+                        P[j][2] = sj * (float)q[2];
+                        pm = fmaxf(pm, sqrtf(P[j][0] * P[j][0] + P[j][1] * P[j][1] + P[j][2] * P[j][2]));
+                    }
+                    float lr = 0.f;
+                    for (int i = 0; i < (kind == 0 ? 1 : 2); ++i)
+                        for (int j = (kind == 0 ? 1 : 2); j < 4; ++j) {
+                            const float dx = P[i][0] - P[j][0], dy = P[i][1] - P[j][1], dz = P[i][2] - P[j][2];
+                            lr = fmaxf(lr, sqrtf(dx * dx + dy * dy + dz * dz));
+                        }
+                    const float lim = pair_dist_lb(D, kind, v) * (1.f - (float)D.ccd_shrink);
+                    if (lim > 1.001f * lr + 2e-3f * pm) continue;
+                }
+                double rho = pair_alpha(D, kind, v, D.x, D.p, G.alpha, G.of);
                 if (rho < 1.0) {
                     vf[pass] = 1;
                     double m = G.alpha[g0];
