@@ -63,94 +63,84 @@ __global__ void k_pack_zp(Dev<R> D, int restart) {
         o[1] = {D.p[3 * v], D.p[3 * v + 1], D.p[3 * v + 2], (R)0};
 }
 
-// One pass for all reductions of an iteration. Thread i takes tet i (the
-// stored projected Hessian: (G_t z)^T K_t (G_t p) and the like), vertex i
-// (g.z, g.p, g.z_prev, mass terms, |z_v|), and, grid-stride, the C_base
-// rank-1 terms and the classified updates. Values are summed in the bulk
-// precision R within a block (contact terms formed in FP64), the block
-// totals in FP64 across blocks.
+// (G_t z)^T K_t (G_t z), (G_t z)^T K_t (G_t p), (G_t p)^T K_t (G_t p) of one tet
+// from its packed Hessian hv, rest inverse B and vertex ids, added to zz, zp, pp
 template <class R>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_forms_all(Dev<R> D, ContactBuf C, int restart) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nth = gridDim.x * blockDim.x;
-    R zz = 0, zp = 0, pp = 0, gz = 0, gp = 0, gzp = 0, zn = 0;
-    for (int t = i; t < D.nt; t += nth) {
-        // all 45 + 9 coalesced packet loads issued before the gathers
-        const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
-        R hv[kH];
+__device__ __forceinline__ void tet_forms(const Dev<R>& D, const R hv[kH], const R B[3][3], const int vid[4], R& zz,
+                                          R& zp, R& pp) {
+    const V4<R>* zpk = reinterpret_cast<const V4<R>*>(D.zp4);
+    V4<R> zv[4], pv[4];
 #pragma unroll
-        for (int k = 0; k < kH; ++k) hv[k] = hp[k * kPack];
-        int4 q = D.tets[t];
-        int vid[4] = {q.x, q.y, q.z, q.w};
-        const R* Bb = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
-        R B[3][3];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = Bb[c * kPack];
-        const V4<R>* zpk = reinterpret_cast<const V4<R>*>(D.zp4);
-        V4<R> zv[4], pv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            zv[j] = zpk[2 * vid[j]];
-            pv[j] = zpk[2 * vid[j] + 1];
-        }
-        R ez[3][3], ep[3][3];  // edge vectors x_j - x_0 of z and p
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            ez[j][0] = zv[j + 1].x - zv[0].x;
-            ez[j][1] = zv[j + 1].y - zv[0].y;
-            ez[j][2] = zv[j + 1].z - zv[0].z;
-            ep[j][0] = pv[j + 1].x - pv[0].x;
-            ep[j][1] = pv[j + 1].y - pv[0].y;
-            ep[j][2] = pv[j + 1].z - pv[0].z;
-        }
-        R dz[9], dp[9];  // vec(dF), column-major
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                R sz = 0, sp = 0;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    sz += ez[j][r] * B[j][c];
-                    sp += ep[j][r] * B[j][c];
-                }
-                dz[3 * c + r] = sz;
-                dp[3 * c + r] = sp;
-            }
-        R Hz[9], Hp[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) Hz[a] = Hp[a] = 0;
-#pragma unroll
-        for (int a = 0; a < 9; ++a)
-#pragma unroll
-            for (int b = a; b < 9; ++b) {
-                R h = hv[pk(a, b)];
-                Hz[a] += h * dz[b];
-                Hp[a] += h * dp[b];
-                if (b != a) {
-                    Hz[b] += h * dz[a];
-                    Hp[b] += h * dp[a];
-                }
-            }
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            zz += dz[a] * Hz[a];
-            zp += dp[a] * Hz[a];
-            pp += dp[a] * Hp[a];
-        }
+    for (int j = 0; j < 4; ++j) {
+        zv[j] = zpk[2 * vid[j]];
+        pv[j] = zpk[2 * vid[j] + 1];
     }
+    R ez[3][3], ep[3][3];  // edge vectors x_j - x_0 of z and p
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        ez[j][0] = zv[j + 1].x - zv[0].x;
+        ez[j][1] = zv[j + 1].y - zv[0].y;
+        ez[j][2] = zv[j + 1].z - zv[0].z;
+        ep[j][0] = pv[j + 1].x - pv[0].x;
+        ep[j][1] = pv[j + 1].y - pv[0].y;
+        ep[j][2] = pv[j + 1].z - pv[0].z;
+    }
+    R dz[9], dp[9];  // vec(dF), column-major
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            R sz = 0, sp = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                sz += ez[j][r] * B[j][c];
+                sp += ep[j][r] * B[j][c];
+            }
+            dz[3 * c + r] = sz;
+            dp[3 * c + r] = sp;
+        }
+    R Hz[9], Hp[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Hz[a] = Hp[a] = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a)
+#pragma unroll
+        for (int b = a; b < 9; ++b) {
+            R h = hv[pk(a, b)];
+            Hz[a] += h * dz[b];
+            Hp[a] += h * dp[b];
+            if (b != a) {
+                Hz[b] += h * dz[a];
+                Hp[b] += h * dp[a];
+            }
+        }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        zz += dz[a] * Hz[a];
+        zp += dp[a] * Hz[a];
+        pp += dp[a] * Hp[a];
+    }
+}
+
+// The rest of an iteration's reductions, thread i of nth grid-stride:
+// vertex terms (g.z, g.p, g.z_prev, mass terms, |z_v|), the C_base rank-1
+// terms and the classified updates, added to t = {zz, zp, pp, gz, gp, gzp}
+// and zn.
+template <class R>
+__device__ __forceinline__ void forms_rest(const Dev<R>& D, const ContactBuf& C, int restart, int i, int nth, R t[6],
+                                           R& zn) {
     for (int v = i; v < D.nv; v += nth) {
         const R m = D.mass[v];
         R zsq = 0;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             R gi = D.g[3 * v + r], zi = D.z[3 * v + r], pi = restart ? (R)0 : D.p[3 * v + r], zpi = D.zprev[3 * v + r];
-            gz += gi * zi;
-            gp += gi * pi;
-            gzp += gi * zpi;
-            zz += m * zi * zi;
-            zp += m * zi * pi;
-            pp += m * pi * pi;
+            t[3] += gi * zi;
+            t[4] += gi * pi;
+            t[5] += gi * zpi;
+            t[0] += m * zi * zi;
+            t[1] += m * zi * pi;
+            t[2] += m * pi * pi;
             zsq += zi * zi;
         }
         zn = fmax(zn, sqrt(zsq));
@@ -161,9 +151,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_forms_all(Dev<R
         double nz, np;
         rank1_dots(D.Cb.v[c], D.Cb.type[c], D.Cb.r + 3 * c, D.Cb.w + 4 * c, D.z, D.p, !restart, nz, np);
         double k = D.Cb.k[c];
-        zz += (R)(k * nz * nz);
-        zp += (R)(k * nz * np);
-        pp += (R)(k * np * np);
+        t[0] += (R)(k * nz * nz);
+        t[1] += (R)(k * nz * np);
+        t[2] += (R)(k * np * np);
     }
     const int nu = min(D.S->n_upd, D.upd_cap);
     for (int u = i; u < nu; u += nth) {
@@ -171,13 +161,16 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_forms_all(Dev<R
         double nz, np;
         rank1_dots(C.v[c], C.type[c], C.r + 3 * c, C.w + 4 * c, D.z, D.p, !restart, nz, np);
         double sd = D.upd_dS[u];
-        zz += (R)(sd * nz * nz);
-        zp += (R)(sd * nz * np);
-        pp += (R)(sd * np * np);
+        t[0] += (R)(sd * nz * nz);
+        t[1] += (R)(sd * nz * np);
+        t[2] += (R)(sd * np * np);
     }
-    // warp and block sums in R (B300's FP64 pipe is too narrow even for
-    // per-warp scalar work), one FP64 atomic per block and value
-    R t[6] = {zz, zp, pp, gz, gp, gzp};
+}
+
+// Warp and block sums in R (B300's FP64 pipe is too narrow even for per-warp
+// scalar work), then one FP64 atomic per block and value.
+template <class R>
+__device__ __forceinline__ void forms_reduce(const Dev<R>& D, R t[6], R zn) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) t[k] = warp_sum(t[k]);
     zn = warp_max(zn);
@@ -203,6 +196,39 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_forms_all(Dev<R
             if (m > (R)0) atomicMaxPos(&S->znorm, (double)m);
         }
     }
+}
+
+// One pass for all reductions of an iteration. Thread i takes tet i (all
+// 45 + 9 coalesced packet loads issued before the gathers), vertex i, and,
+// grid-stride, the rank-1 terms. In FP32, three CTAs per SM (85 registers a
+// thread) keep the 54 packet loads of a tet in flight: 16.5 us on the
+// 196,608-tet sphere pile against 18.4 us at four CTAs (64 registers). Bulk
+// copies staging 4 packets per CTA, or a persistent CTA per SM streaming
+// packets through a 3-stage ring, measured 20.6 us and 22.6 us: a tet moves
+// 232 bytes but also gathers its vertices and does the 9x9 products, and a
+// CTA's copy latency then adds to its arithmetic instead of hiding behind
+// other warps' loads.
+template <class R>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 2) k_forms_all(Dev<R> D, ContactBuf C, int restart) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nth = gridDim.x * blockDim.x;
+    R zz = 0, zp = 0, pp = 0;
+    for (int t = i; t < D.nt; t += nth) {
+        const R* hp = D.hess + (size_t)(t / kPack) * kH * kPack + (t % kPack);
+        R hv[kH];
+#pragma unroll
+        for (int k = 0; k < kH; ++k) hv[k] = hp[k * kPack];
+        const int4 q = D.tets[t];
+        const int vid[4] = {q.x, q.y, q.z, q.w};
+        const R* Bb = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
+        R B[3][3];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = Bb[c * kPack];
+        tet_forms(D, hv, B, vid, zz, zp, pp);
+    }
+    R t[6] = {zz, zp, pp, 0, 0, 0}, zn = 0;
+    forms_rest(D, C, restart, i, nth, t, zn);
+    forms_reduce(D, t, zn);
 }
 
 // (mu, nu): restart mu = g.z / z^T H~ z; else the 2x2 system of Eq. 10 with
