@@ -415,11 +415,13 @@ int setup_dev(ipc_scene* s) {
     D.topk = A.arr<int>((size_t)m.ngroups[0] * std::max(1, D.K));
     D.alpha = A.arr<double>(m.ngroups[0]);
     D.shrink = A.arr<double>(m.ngroups[0]);
+    D.shrink3 = A.arr<double>(m.ngroups[0]);
     D.nbody = m.nbody;
     int* d_body = A.arr<int>(m.nv);
     D.body = d_body;
     D.alpha_b = A.arr<double>(m.nbody);
     D.shrink_b = A.arr<double>(m.nbody);
+    D.shrink3_b = A.arr<double>(m.nbody);
     D.vflags = A.arr<int>(32);
     D.str_v = A.arr<int4>(D.straddle_cap);
     D.str_t = A.arr<int>(D.straddle_cap);

@@ -49,6 +49,7 @@ struct Scalars {
     int ccd_passes;                // verification passes run
     int ccd_viol_b, ccd_uniform_b, ccd_passes_b;  // the same for the body grouping
     double alpha_bmin, alpha_bmax; // smallest / largest per-body step
+    double vstat[4];               // verification scratch: final min / max per grouping
     int n_upd;                     // classified updates
     int n_straddle;                // straddling CCD candidates
     int overflow;                  // bit flags: 1 contacts, 2 straddle, 4 upd
@@ -147,10 +148,12 @@ struct Dev {
     // CCD
     double* alpha;                         // per level-0 group
     double* shrink;
+    double* shrink3;                       // second verification scratch per level-0 subdomain
     int nbody;
     const int* body;                       // connected body of each vertex
     double* alpha_b;                       // per body
     double* shrink_b;
+    double* shrink3_b;
     int* vflags;                           // verification: violation flag per grouping and pass
     int4* str_v;                           // straddling candidates: vertices
     int* str_t;                            // 0 PT (p, t0, t1, t2), 1 EE (a0, a1, b0, b1)

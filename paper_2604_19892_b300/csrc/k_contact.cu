@@ -718,25 +718,74 @@ __global__ void k_ccd_begin(Dev<R> D) {
 struct Grouping {
     const int* of;        // group of each vertex
     double* alpha;
-    double* shrink;
+    double* shrink;       // scratch, n
+    double* third;        // scratch, n
     int n;
     int* viol;
     int* state;           // 0 running, 1 uniform fallback, 2 verified
     int* passes;
-    double* amin;         // minimum before verification (the uniform step)
-    double* amax;
+    double* amin;         // minimum before verification (the uniform step); on exit the final minimum
+    double* amax;         // on exit the final maximum
+    double* fmin;         // scratch scalars for the final minimum and maximum
+    double* fmax;
 };
 
+// is straddling pair k violated under grouping G's steps a? (the FP64 walk
+// with the actual motion a_g(v) p_v, skipped where FP32 bounds prove rho = 1);
+// if so, m = the smallest step of the groups it touches
+template <class R>
+__device__ __forceinline__ bool pair_violated(const Dev<R>& D, const Grouping& G, const double* a, int k, int v[4],
+                                              double& m) {
+    const int4 q = D.str_v[k];
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+    const int g0 = G.of[v[0]];
+    if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) return false;
+    const int kind = D.str_t[k];
+    {
+        // the FP64 walk returns exactly 1 where the FP32 distance bound
+        // exceeds the largest relative displacement of the actual motion
+        // (CUBICSAFE starts at alpha_l >= 1): skip it there
+        float P[4][3], pm = 0.f;
+        for (int j = 0; j < 4; ++j) {
+            const float sj = (float)a[G.of[v[j]]];
+            const R* qq = D.p + 3 * v[j];
+            P[j][0] = sj * (float)qq[0];
+            P[j][1] = sj * (float)qq[1];
+            P[j][2] = sj * (float)qq[2];
+            pm = fmaxf(pm, sqrtf(P[j][0] * P[j][0] + P[j][1] * P[j][1] + P[j][2] * P[j][2]));
+        }
+        float lr = 0.f;
+        for (int i = 0; i < (kind == 0 ? 1 : 2); ++i)
+            for (int j = (kind == 0 ? 1 : 2); j < 4; ++j) {
+                const float dx = P[i][0] - P[j][0], dy = P[i][1] - P[j][1], dz = P[i][2] - P[j][2];
+                lr = fmaxf(lr, sqrtf(dx * dx + dy * dy + dz * dz));
+            }
+        const float lim = pair_dist_lb(D, kind, v) * (1.f - (float)D.ccd_shrink);
+        if (lim > 1.001f * lr + 2e-3f * pm) return false;
+    }
+    const double rho = pair_alpha(D, kind, v, D.x, D.p, a, G.of);
+    if (!(rho < 1.0)) return false;
+    m = a[g0];
+    for (int j = 1; j < 4; ++j) m = fmin(m, a[G.of[v[j]]]);
+    return true;
+}
+
 // Verification of the straddling candidates for both groupings (level-0
-// subdomains, then bodies) in one cooperative launch: per pass, every
-// straddling pair is re-checked with the actual motion alpha_g(v) p_v; a
-// violating pair lowers every group it touches to the pair's smallest alpha
-// (the pair then moves uniformly on a segment already checked). The pass
-// loop stops at the first clean pass; after kCcdPasses passes with a
-// violation, or when the candidate list overflowed, the grouping takes the
-// uniform step min_g alpha_g. Grid-wide barriers are cooperative-groups
-// syncs of a co-resident grid (cudaLaunchCooperativeKernel); every thread
-// executes the same sequence of them.
+// subdomains and bodies, side by side) in one cooperative launch: per pass,
+// every straddling pair is re-checked with the actual motion alpha_g(v) p_v;
+// a violating pair lowers every group it touches to the pair's smallest alpha
+// (the pair then moves uniformly on a segment already checked). A grouping
+// stops at its first clean pass; after kCcdPasses passes with a violation, or
+// when the candidate list overflowed, it takes the uniform step
+// min_g alpha_g. A pass needs one grid barrier: it reads the steps from
+// buffer k mod 3 and takes minima into buffer k + 1 mod 3 (each group's own
+// step and the violations' minima, both commutative), while buffer
+// k + 2 mod 3, which nothing touches in this pass, is reset for the next.
+// Grid-wide barriers are cooperative-groups syncs of a co-resident grid
+// (cudaLaunchCooperativeKernel); every thread executes the same sequence.
 template <class R>
 __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Grouping G1) {
     cg::grid_group grid = cg::this_grid();
@@ -745,97 +794,97 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
     const int lane = threadIdx.x & 31;
     const int nstr = min(D.S->n_straddle, D.straddle_cap);
     const bool overflow = (D.S->overflow & 2) != 0;
+    const Grouping* Gs[2] = {&G0, &G1};
+    if (tid == 0) {
+        *G0.amin = *G1.amin = 1.0;
+        *G0.fmin = *G1.fmin = 1.0;
+        *G0.fmax = *G1.fmax = 0.0;
+    }
+    grid.sync();
     for (int gi = 0; gi < 2; ++gi) {
-        const Grouping& G = gi ? G1 : G0;
-        int* vf = D.vflags + gi * kCcdPasses;
-        if (tid == 0) *G.amin = 1.0;
-        grid.sync();
+        const Grouping& G = *Gs[gi];
         double mn = 1.0;
-        for (int g = tid; g < G.n; g += nth) mn = fmin(mn, G.alpha[g]);
+        for (int g = tid; g < G.n; g += nth) {
+            mn = fmin(mn, G.alpha[g]);
+            G.shrink[g] = 1.0;  // the target of pass 0
+        }
         for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
         if (lane == 0 && mn < 1.0) atomicMinPos(G.amin, mn);
-        grid.sync();
-        int state = overflow ? 1 : 0;  // 0 running, 1 uniform fallback, 2 verified
-        int passes = overflow ? -1 : 0;
-        for (int pass = 0; pass < kCcdPasses && state == 0; ++pass) {
-            for (int g = tid; g < G.n; g += nth) G.shrink[g] = G.alpha[g];
-            grid.sync();
+    }
+    grid.sync();
+    // state 0 running, 1 uniform fallback, 2 verified; fin = the buffer
+    // holding a verified grouping's steps
+    int state[2] = {overflow ? 1 : 0, overflow ? 1 : 0};
+    int passes[2] = {overflow ? -1 : 0, overflow ? -1 : 0};
+    int fin[2] = {0, 0};
+    for (int pass = 0; pass < kCcdPasses && (state[0] == 0 || state[1] == 0); ++pass) {
+        for (int gi = 0; gi < 2; ++gi) {
+            if (state[gi] != 0) continue;
+            const Grouping& G = *Gs[gi];
+            double* bufs[3] = {G.alpha, G.shrink, G.third};
+            const double* A = bufs[pass % 3];
+            double* B = bufs[(pass + 1) % 3];
+            double* Z = bufs[(pass + 2) % 3];
+            int* vf = D.vflags + gi * kCcdPasses;
+            for (int g = tid; g < G.n; g += nth) {
+                atomicMinPos(&B[g], A[g]);
+                Z[g] = 1.0;
+            }
             for (int k = tid; k < nstr; k += nth) {
-                int4 q = D.str_v[k];
-                int v[4] = {q.x, q.y, q.z, q.w};
-                int g0 = G.of[v[0]];
-                if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) continue;
-                const int kind = D.str_t[k];
-                {
-                    // the FP64 walk returns exactly 1 where the FP32 distance
-                    // bound exceeds the largest relative displacement of the
-                    // actual motion alpha_g(v) p_v (CUBICSAFE starts at
-                    // alpha_l >= 1): skip it there
-                    float P[4][3], pm = 0.f;
-                    for (int j = 0; j < 4; ++j) {
-                        const float sj = (float)G.alpha[G.of[v[j]]];
-                        const R* q = D.p + 3 * v[j];
-                        P[j][0] = sj * (float)q[0];
-                        P[j][1] = sj * (float)q[1];
-                        P[j][2] = sj * (float)q[2];
-                        pm = fmaxf(pm, sqrtf(P[j][0] * P[j][0] + P[j][1] * P[j][1] + P[j][2] * P[j][2]));
-                    }
-                    float lr = 0.f;
-                    for (int i = 0; i < (kind == 0 ? 1 : 2); ++i)
-                        for (int j = (kind == 0 ? 1 : 2); j < 4; ++j) {
-                            const float dx = P[i][0] - P[j][0], dy = P[i][1] - P[j][1], dz = P[i][2] - P[j][2];
-                            lr = fmaxf(lr, sqrtf(dx * dx + dy * dy + dz * dz));
-                        }
-                    const float lim = pair_dist_lb(D, kind, v) * (1.f - (float)D.ccd_shrink);
-                    if (lim > 1.001f * lr + 2e-3f * pm) continue;
-                }
-                double rho = pair_alpha(D, kind, v, D.x, D.p, G.alpha, G.of);
-                if (rho < 1.0) {
+                int v[4];
+                double m;
+                if (pair_violated(D, G, A, k, v, m)) {
                     vf[pass] = 1;
-                    double m = G.alpha[g0];
-                    for (int j = 1; j < 4; ++j) m = fmin(m, G.alpha[G.of[v[j]]]);
-                    for (int j = 0; j < 4; ++j) atomicMinPos(&G.shrink[G.of[v[j]]], m);
+                    for (int j = 0; j < 4; ++j) atomicMinPos(&B[G.of[v[j]]], m);
                 }
             }
-            grid.sync();
-            if (__ldcg(&vf[pass]) == 0) {
-                state = 2;
-                passes = pass + 1;
-                break;
-            }
-            for (int g = tid; g < G.n; g += nth) G.alpha[g] = G.shrink[g];
-            grid.sync();
-        }
-        if (state == 0) {
-            state = 1;
-            passes = -1;
-        }
-        if (state == 1) {
-            const double a = __ldcg(G.amin);
-            for (int g = tid; g < G.n; g += nth) G.alpha[g] = a;
-        }
-        if (tid == 0) {
-            *G.state = state;
-            *G.passes = passes;
-            *G.viol = state != 2;
-            *G.amin = 1.0;
-            *G.amax = 0.0;
         }
         grid.sync();
+        for (int gi = 0; gi < 2; ++gi) {
+            if (state[gi] != 0) continue;
+            if (__ldcg(&D.vflags[gi * kCcdPasses + pass]) == 0) {
+                state[gi] = 2;
+                passes[gi] = pass + 1;
+                fin[gi] = pass % 3;
+            }
+        }
+    }
+    // write the result into alpha (the verified buffer, or the uniform step),
+    // gathering its minimum and maximum on the way
+    for (int gi = 0; gi < 2; ++gi) {
+        const Grouping& G = *Gs[gi];
+        if (state[gi] == 0) {
+            state[gi] = 1;
+            passes[gi] = -1;
+        }
+        const double* src = fin[gi] == 0 ? G.alpha : fin[gi] == 1 ? G.shrink : G.third;
+        const double a_uni = __ldcg(G.amin);
         double lo = 1.0, hi = 0.0;
         for (int g = tid; g < G.n; g += nth) {
-            lo = fmin(lo, G.alpha[g]);
-            hi = fmax(hi, G.alpha[g]);
+            const double a = state[gi] == 1 ? a_uni : src[g];
+            if (state[gi] == 1 || fin[gi] != 0) G.alpha[g] = a;
+            lo = fmin(lo, a);
+            hi = fmax(hi, a);
         }
         for (int o = 16; o > 0; o >>= 1) {
             lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
         if (lane == 0) {
-            if (lo < 1.0) atomicMinPos(G.amin, lo);
-            if (hi > 0.0) atomicMaxPos(G.amax, hi);
+            if (lo < 1.0) atomicMinPos(G.fmin, lo);
+            if (hi > 0.0) atomicMaxPos(G.fmax, hi);
         }
-        grid.sync();
+    }
+    grid.sync();
+    if (tid == 0) {
+        for (int gi = 0; gi < 2; ++gi) {
+            const Grouping& G = *Gs[gi];
+            *G.state = state[gi];
+            *G.passes = passes[gi];
+            *G.viol = state[gi] != 2;
+            *G.amin = *G.fmin;
+            *G.amax = *G.fmax;
+        }
     }
 }
 
@@ -885,10 +934,10 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     if (D.nse) KL(k_ccd_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, gin));
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     Scalars* S = D.S;
-    Grouping sub{D.grp0, D.alpha, D.shrink, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes, &S->alpha_min,
-                 &S->alpha_max};
-    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b, &S->ccd_passes_b,
-                 &S->alpha_bmin, &S->alpha_bmax};
+    Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
+                 &S->alpha_min, &S->alpha_max, &S->vstat[0], &S->vstat[1]};
+    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
+                 &S->ccd_passes_b, &S->alpha_bmin, &S->alpha_bmax, &S->vstat[2], &S->vstat[3]};
     verify_groupings(D, sub, bod, st);
 }
 
@@ -935,10 +984,10 @@ void launch_ccd_list(const Dev<R>& D, cudaStream_t st) {
     KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D));
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     Scalars* S = D.S;
-    Grouping sub{D.grp0, D.alpha, D.shrink, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes, &S->alpha_min,
-                 &S->alpha_max};
-    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b, &S->ccd_passes_b,
-                 &S->alpha_bmin, &S->alpha_bmax};
+    Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
+                 &S->alpha_min, &S->alpha_max, &S->vstat[0], &S->vstat[1]};
+    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
+                 &S->ccd_passes_b, &S->alpha_bmin, &S->alpha_bmax, &S->vstat[2], &S->vstat[3]};
     verify_groupings(D, sub, bod, st);
 }
 
