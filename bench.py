@@ -137,8 +137,8 @@ def stage_bytes(nv, nt, nblocks, rsize):
 # since), scaled by the units a launch processes: profiles/ holds the
 # summaries and commands
 TRAFFIC = {
-    ("mas_blocks", "fp32"): {"bytes_per_block": (56.331008e6 + 0.063488e6) / 1507},
-    ("forms", "fp32"): {"bytes_per_tet": (49.592832e6 + 0.042752e6) / 196608},
+    ("mas_blocks", "fp32"): {"bytes_per_block": (56.330496e6 + 0.015872e6) / 1507},
+    ("forms", "fp32"): {"bytes_per_tet": (49.594880e6 + 0.052736e6) / 196608},
 }
 
 

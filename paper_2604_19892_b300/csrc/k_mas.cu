@@ -1144,61 +1144,75 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
     }
     R out = Y[0][tid];
     if (ns > 0) {
-        // capacitance I + U^T W and r = U^T z_base, FP64 dot products per warp
+        // capacitance I + U^T W (symmetric: the half a <= c) and r = U^T z_base.
+        // U and W = B U hold bulk-precision values, so the products are summed
+        // in R per warp and the warp totals enter the FP64 solve (FP64
+        // products would add no accuracy here, and B300 runs FP64 at a small
+        // fraction of its FP32 rate: these dot products were most of the
+        // kernel's time)
         int warp = tid >> 5, lane = tid & 31;
-        int nprod = ns * ns + ns;
-        for (int e = warp; e < nprod; e += 3) {
+        const int nsym = ns * (ns + 1) / 2;
+        for (int e = warp; e < nsym + ns; e += 3) {
             int a, c;
             const R* wv;
-            if (e < ns * ns) {
-                a = e / ns;
-                c = e % ns;
+            if (e < nsym) {
+                a = 0;
+                int rem = e;
+                while (rem >= ns - a) {
+                    rem -= ns - a;
+                    ++a;
+                }
+                c = a + rem;
                 wv = Y[1 + c];
             } else {
-                a = e - ns * ns;
+                a = e - nsym;
                 c = -1;
                 wv = Y[0];
             }
-            double s = 0.0;
-            for (int i = lane; i < kBlk; i += 32) s += (double)rhs[1 + a][i] * (double)wv[i];
+            R s = 0;
+            for (int i = lane; i < kBlk; i += 32) s += rhs[1 + a][i] * wv[i];
             s = warp_sum(s);
             if (lane == 0) {
-                if (c >= 0)
-                    cap[a][c] = s + (a == c ? 1.0 : 0.0);
-                else
-                    cap[a][kMaxK] = s;
+                if (c >= 0) {
+                    cap[a][c] = (double)s + (a == c ? 1.0 : 0.0);
+                    cap[c][a] = cap[a][c];
+                } else {
+                    cap[a][kMaxK] = (double)s;
+                }
             }
         }
         __syncthreads();
         if (tid == 0) {
-            // Cholesky solve of the SPD capacitance system
+            // Cholesky solve of the SPD capacitance system, in place in cap
+            // (L below the diagonal, 1 / L_jj on it): one reciprocal square
+            // root per column and no divisions, since the serial FP64 chain
+            // of this thread holds up the whole CTA.
             // C = I + U^T B U is >= I in exact arithmetic, so every pivot is
             // >= 1; a pivot below 1/2 means B's rounding swamped a stiff
             // update direction and the correction is dropped (z_d = B g_d)
-            double L[kMaxK][kMaxK];
             bool good = true;
             for (int j = 0; j < ns; ++j) {
                 double d = cap[j][j];
-                for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+                for (int k = 0; k < j; ++k) d -= cap[j][k] * cap[j][k];
                 good = good && (d >= 0.5);
-                d = sqrt(fmax(d, 0.5));
-                L[j][j] = d;
+                const double il = rsqrt(fmax(d, 0.5));
+                cap[j][j] = il;
                 for (int i = j + 1; i < ns; ++i) {
                     double t = cap[i][j];
-                    for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-                    L[i][j] = t / d;
+                    for (int k = 0; k < j; ++k) t -= cap[i][k] * cap[j][k];
+                    cap[i][j] = t * il;
                 }
             }
             double y[kMaxK];
             for (int i = 0; i < ns; ++i) {
                 double t = cap[i][kMaxK];
-                for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
-                y[i] = t / L[i][i];
+                for (int k = 0; k < i; ++k) t -= cap[i][k] * y[k];
+                y[i] = t * cap[i][i];
             }
             for (int i = ns - 1; i >= 0; --i) {
                 double t = y[i];
-                for (int k = i + 1; k < ns; ++k) t -= L[k][i] * lam[k];
-                lam[i] = t / L[i][i];
+                for (int k = i + 1; k < ns; ++k) t -= cap[k][i] * lam[k];
+                lam[i] = t * cap[i][i];
             }
             // a non-finite capacitance solution (overflowing contact
             // stiffness) drops this subdomain's correction: z_d = B g_d
@@ -1214,8 +1228,9 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
         // <= g_d^T B g_d. A corrected z_d outside that range (FP32 inverses
         // of stiff blocks make the capacitance solve unstable) drops this
         // subdomain's correction.
-        double gi = (double)rhs[0][tid];
-        double qb = warp_sum(gi * (double)Y[0][tid]), qc = warp_sum(gi * o);
+        // (summed in R per warp: the test's tolerance is 1e-3 of qb)
+        const R gi = rhs[0][tid];
+        double qb = (double)warp_sum(gi * Y[0][tid]), qc = (double)warp_sum(gi * (R)o);
         __shared__ double qsum[2][3];
         if ((tid & 31) == 0) {
             qsum[0][tid >> 5] = qb;
