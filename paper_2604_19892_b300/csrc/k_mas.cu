@@ -1045,13 +1045,23 @@ __global__ void __launch_bounds__(96) k_block_apply_plain(Dev<R> D, const R* __r
 template <class R>
 __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z,
                                                     ContactBuf C, int woodbury) {
+    extern __shared__ __align__(128) unsigned char wsm[];  // the 96x96 block (bulk copy)
+    __shared__ __align__(8) uint64_t bar;
     __shared__ R rhs[1 + kMaxK][kBlk];
     __shared__ R Y[1 + kMaxK][kBlk];
     __shared__ double cap[kMaxK][kMaxK + 1];
     __shared__ double lam[kMaxK];
     __shared__ int sel[kMaxK];
     __shared__ int nsel;
+    const R* Bs = reinterpret_cast<const R*>(wsm);
     int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        constexpr uint32_t kBytes = kBlk * kBlk * sizeof(R);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, kBytes);
+        bulk_g2s(wsm, D.blocks + (size_t)b * kBlk * kBlk, kBytes, &bar);
+    }
     int l = 0;
     while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
     int grp = b - D.blk_off[l];
@@ -1092,56 +1102,43 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
         }
     }
     __syncthreads();
-    // Y = B [rhs]; B is symmetric, so column c of Y is row c of B times rhs.
-    // 16-byte loads: thread tid owns W = 16 / sizeof(R) consecutive columns
-    // (column group tid % NCG) and the rows j = tid / NCG (mod NRG); the NRG
-    // row-group partial sums are then added in shared memory.
-    constexpr int W = 16 / (int)sizeof(R);
-    constexpr int NCG = kBlk / W, NRG = kBlk / NCG;
-    using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-    const int cg = tid % NCG, rg = tid / NCG;
-    const V16* Bv = reinterpret_cast<const V16*>(D.blocks + (size_t)b * kBlk * kBlk) + cg;
-    R acc[1 + kMaxK][W];
+    // Y = B [rhs] from the staged block; B is symmetric, so thread c reads
+    // column c (consecutive threads, consecutive words) and forms row c of Y
+    const bool arrived = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!arrived)) {
+        // record, wait (bounded) for the copy in flight, leave z unwritten
+        if (tid == 0) {
+            D.S->async_timeout = 1;
+            mbar_wait(&bar, 0);
+        }
+        return;
+    }
+    {
+        R acc[1 + kMaxK];
 #pragma unroll
-    for (int a = 0; a < 1 + kMaxK; ++a)
-#pragma unroll
-        for (int w = 0; w < W; ++w) acc[a][w] = 0;
-    if (ns == 0) {
+        for (int a = 0; a < 1 + kMaxK; ++a) acc[a] = 0;
+        if (ns == 0) {
+            R a0 = 0, a1 = 0;
 #pragma unroll 8
-        for (int j = rg; j < kBlk; j += NRG) {
-            R e[W];
-            unpack16(Bv[(size_t)j * NCG], e);
-            const R r0 = rhs[0][j];
+            for (int j = 0; j < kBlk; j += 2) {
+                a0 += Bs[j * kBlk + tid] * rhs[0][j];
+                a1 += Bs[(j + 1) * kBlk + tid] * rhs[0][j + 1];
+            }
+            acc[0] = a0 + a1;
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < kBlk; ++j) {
+                const R e = Bs[j * kBlk + tid];
 #pragma unroll
-            for (int w = 0; w < W; ++w) acc[0][w] += e[w] * r0;
+                for (int a = 0; a < 1 + kMaxK; ++a)
+                    if (a <= ns) acc[a] += e * rhs[a][j];
+            }
         }
-    } else {
-#pragma unroll 4
-        for (int j = rg; j < kBlk; j += NRG) {
-            R e[W];
-            unpack16(Bv[(size_t)j * NCG], e);
 #pragma unroll
-            for (int a = 0; a < 1 + kMaxK; ++a)
-                if (a <= ns) {
-                    const R ra = rhs[a][j];
-#pragma unroll
-                    for (int w = 0; w < W; ++w) acc[a][w] += e[w] * ra;
-                }
-        }
+        for (int a = 0; a < 1 + kMaxK; ++a)
+            if (a <= ns) Y[a][tid] = acc[a];
     }
-#pragma unroll
-    for (int q = 0; q < NRG; ++q) {
-        if (rg == q)
-#pragma unroll
-            for (int a = 0; a < 1 + kMaxK; ++a)
-                if (a <= ns)
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        R* y = &Y[a][W * cg + w];
-                        *y = q == 0 ? acc[a][w] : *y + acc[a][w];
-                    }
-        __syncthreads();
-    }
+    __syncthreads();
     R out = Y[0][tid];
     if (ns > 0) {
         // capacitance I + U^T W (symmetric: the half a <= c) and r = U^T z_base.
@@ -1354,10 +1351,12 @@ void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool 
     if (!attr) {
         cudaFuncSetAttribute(k_block_apply_plain<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kBlk * kBlk * sizeof(R)));
+        cudaFuncSetAttribute(k_block_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kBlk * kBlk * sizeof(R)));
         attr = true;
     }
     if (woodbury)
-        KL(k_block_apply<R><<<D.blk_off[D.nlev], 96, 0, st>>>(D, g, z, C, 1));
+        KL(k_block_apply<R><<<D.blk_off[D.nlev], 96, kBlk * kBlk * sizeof(R), st>>>(D, g, z, C, 1));
     else
         KL(k_block_apply_plain<R><<<D.blk_off[D.nlev], 96, kBlk * kBlk * sizeof(R), st>>>(D, g, z));
 }
