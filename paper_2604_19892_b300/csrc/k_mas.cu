@@ -612,19 +612,23 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
         double d = src[r * kBlk + r];
         sc[r] = (mem[r / 3] < 0 || !(d > 0.0)) ? (T)1 : (T)(1.0 / sqrt(d));
     }
-    // thread t owns tile (ti, tj), ti >= tj, t = ti (ti + 1) / 2 + tj
+    // Cholesky: thread t owns tile (ti, tj), ti >= tj, the tiles ordered by
+    // column from the right (column 15, then 14, ...), so that the tiles still
+    // active at panel kt (columns >= kt) are the first (16 - kt)(17 - kt) / 2
+    // threads and the warps past them skip the panel's work
     const int t = threadIdx.x;
     const bool act = t < kNTiles;
     int ti = 0, tj = 0;
     if (act) {
-        int rem = t;
-        while (rem > ti) {
-            ++ti;
-            rem -= ti;
+        int rem = t, c = kNT - 1;
+        while (rem >= kNT - c) {
+            rem -= kNT - c;
+            --c;
         }
-        tj = rem;
+        tj = c;
+        ti = c + rem;
     }
-    const int r0 = kTile * ti, c0 = kTile * tj;
+    int r0 = kTile * ti, c0 = kTile * tj;
     __syncthreads();
     T a[kTile][kTile];
 #pragma unroll
@@ -710,6 +714,18 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
             if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
     __syncthreads();
 
+    // W = L^{-1} and W^T W: tiles in row order, t = ti (ti + 1) / 2 + tj
+    if (act) {
+        int rem = t;
+        ti = 0;
+        while (rem > ti) {
+            ++ti;
+            rem -= ti;
+        }
+        tj = rem;
+    }
+    r0 = kTile * ti;
+    c0 = kTile * tj;
     // ---- W = L^{-1}: row k of W is final once divided by L_kk; then every
     // later row r subtracts L_rk times it
 #pragma unroll
