@@ -300,6 +300,53 @@ int ipc_precond_apply_noalloc(ipc_scene* s, const void* g_dev, void* z_dev, void
 
 const char* ipc_last_error(void);
 
+/* ---- Serving: continuous batching of step requests over resident scenes
+ *
+ * No counterpart in the paper (the method steps one scene); this is the
+ * request loop of a simulation service. Scenes are created by the caller
+ * and stay resident on the device (positions, MAS hierarchy, contact sets);
+ * a request asks for n_steps timesteps of one scene. The server runs up to
+ * cfg.slots requests at once, each on its own CUDA stream and host thread,
+ * so their kernels overlap on the device. A queued request is admitted, in
+ * submission order among the admissible ones, when a slot is free, no other
+ * request of the same scene is running (a scene's steps stay in order) and
+ * the device has at least cfg.min_free_bytes free (cudaMemGetInfo), or when
+ * nothing else is running. Every timestep computes exactly what ipc_step
+ * computes alone. Cooperative launches of concurrent scenes are ordered on
+ * the device (no two grids that need full residency wait on each other).
+ *
+ * alloc is accepted for interface symmetry with ipc_scene_create and unused:
+ * the server allocates no device memory. Scenes must outlive the requests
+ * that name them and must not be stepped, queried or destroyed by the
+ * caller while a request of theirs is queued or running. */
+typedef struct ipc_server ipc_server;
+typedef struct ipc_server_cfg {
+    int slots;               /* requests running at once (>= 1) */
+    size_t min_free_bytes;   /* free device memory needed to admit a request */
+} ipc_server_cfg;
+
+/* Starts cfg->slots worker threads (each with a non-blocking stream on the
+ * current device). Returns IPC_OK or IPC_ERR_INVALID / IPC_ERR_CUDA. */
+int ipc_server_create(const ipc_server_cfg* cfg, const ipc_alloc_fns* alloc, ipc_server** out);
+
+/* Queues n_steps timesteps of scene; *ticket identifies the request. */
+int ipc_server_submit(ipc_server* srv, ipc_scene* scene, int n_steps, unsigned long long* ticket);
+
+/* IPC_PENDING while the request is queued or running; otherwise the return
+ * code of its ipc_step, with its statistics in *stats and the time from
+ * submission to completion in *latency_ms (both nullable); the ticket is
+ * then released. IPC_ERR_INVALID for an unknown ticket. */
+int ipc_server_poll(ipc_server* srv, unsigned long long ticket, ipc_step_stats* stats, double* latency_ms);
+
+/* As ipc_server_poll, but blocks until the request finishes or timeout_ms
+ * passes (IPC_PENDING then). */
+int ipc_server_wait(ipc_server* srv, unsigned long long ticket, double timeout_ms, ipc_step_stats* stats,
+                    double* latency_ms);
+
+/* Finishes every queued and running request, stops the workers, frees the
+ * server. */
+void ipc_server_destroy(ipc_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,8 @@
 // violation the uniform step min_d alpha_d is taken (never below it).
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "geom.cuh"
 #include "kernels.h"
 
@@ -888,21 +890,35 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
     }
 }
 
+// Cooperative launches of all scenes in the process are ordered on the GPU:
+// each one's stream first waits for the previous one (an event recorded after
+// it, on whatever stream it ran), so two grids that need all their blocks
+// resident at once never wait on each other's blocks when several scenes step
+// concurrently (ipc_server). Other kernels still overlap freely.
+std::mutex g_coop_mu;
+
 template <class R>
 void verify_groupings(const Dev<R>& D, const Grouping& sub, const Grouping& bod, cudaStream_t st) {
-    static int nblocks = 0;
-    if (nblocks == 0) {
+    static const int nblocks = [] {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_verify_all<R>, 256, 0);
-        nblocks = sms * (per < 2 ? per : 2);
-        if (nblocks < 1) nblocks = 1;
-    }
+        int n = sms * (per < 2 ? per : 2);
+        return n < 1 ? 1 : n;
+    }();
+    static cudaEvent_t last = [] {
+        cudaEvent_t e = nullptr;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        return e;
+    }();
     Dev<R> Dc = D;
     Grouping a = sub, b = bod;
     void* args[] = {&Dc, &a, &b};
+    std::lock_guard<std::mutex> lock(g_coop_mu);
+    if (last) cudaStreamWaitEvent(st, last, 0);
     KL(cudaLaunchCooperativeKernel((const void*)k_verify_all<R>, dim3(nblocks), dim3(256), args, 0, st));
+    if (last) cudaEventRecord(last, st);
 }
 
 }  // namespace

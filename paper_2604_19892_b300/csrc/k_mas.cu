@@ -1324,12 +1324,12 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
     // the blocks FP32 cannot carry
     const size_t smem_r = sizeof(R) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
     const size_t smem_d = sizeof(double) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static const bool attr_set = [&] {  // once per process, thread-safe
         cudaFuncSetAttribute(k_invert<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
         cudaFuncSetAttribute(k_invert<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
-        attr_set = true;
-    }
+        return true;
+    }();
+    (void)attr_set;
     if (sizeof(R) == 4) {
         // FP32 first; the blocks that floored or raised a pivot again in FP64
         KL(k_invert<R, R><<<nb, kInvThreads, smem_r, st>>>(D, D.invflag, 0));
@@ -1363,14 +1363,14 @@ void launch_restrict(const Dev<R>& D, const R* g, cudaStream_t st) {
 
 template <class R>
 void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool woodbury, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static const bool attr = [] {  // once per process, thread-safe
         cudaFuncSetAttribute(k_block_apply_plain<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kBlk * kBlk * sizeof(R)));
         cudaFuncSetAttribute(k_block_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kBlk * kBlk * sizeof(R)));
-        attr = true;
-    }
+        return true;
+    }();
+    (void)attr;
     if (woodbury)
         KL(k_block_apply<R><<<D.blk_off[D.nlev], 96, kBlk * kBlk * sizeof(R), st>>>(D, g, z, C, 1));
     else

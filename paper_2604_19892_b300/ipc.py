@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libipc_b300.so")
 
 IPC_OK = 0
 IPC_NOT_CONVERGED = 1
+IPC_PENDING = 2
 IPC_ERR_INVALID = -1
 IPC_ERR_CAPACITY = -7
 IPC_PREC_FP64 = 0
@@ -45,6 +46,10 @@ class Params(C.Structure):
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [("slots", C.c_int), ("min_free_bytes", C.c_size_t)]
 
 
 class AllocFns(C.Structure):
@@ -95,6 +100,12 @@ EXPORTS = {
     "ipc_profile_replay": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
                                      C.POINTER(C.c_double)]),
     "ipc_last_error": (C.c_char_p, []),
+    "ipc_server_create": (C.c_int, [C.POINTER(ServerCfg), C.POINTER(AllocFns), C.POINTER(C.c_void_p)]),
+    "ipc_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_ulonglong)]),
+    "ipc_server_poll": (C.c_int, [C.c_void_p, C.c_ulonglong, C.POINTER(StepStats), C.POINTER(C.c_double)]),
+    "ipc_server_wait": (C.c_int, [C.c_void_p, C.c_ulonglong, C.c_double, C.POINTER(StepStats),
+                                  C.POINTER(C.c_double)]),
+    "ipc_server_destroy": (None, [C.c_void_p]),
     "ipc_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ipc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "ipc_kernel_launches": (C.c_longlong, []),
@@ -405,3 +416,59 @@ class Scene:
         _check(self.lib.ipc_eval_ccd(self.h, _dp(x), _dp(p), _dp(a), C.byref(passes), _dp(ab), C.byref(pb),
                                      _stream_handle(self.stream)))
         return a, passes.value, ab, pb.value
+
+
+class Server:
+    """Continuous batching of step requests over resident scenes
+    (ipc_server_*): up to `slots` requests run at once, each on its own
+    stream and host thread of the library. Scenes given to it should use the
+    library's own allocator (Scene(..., use_torch_allocator=False)): their
+    steps then run on the server's threads without calling back into Python.
+    """
+
+    def __init__(self, slots: int = 4, min_free_bytes: int = 0):
+        self.lib = load()
+        cfg = ServerCfg(int(slots), int(min_free_bytes))
+        h = C.c_void_p()
+        _check(self.lib.ipc_server_create(C.byref(cfg), None, C.byref(h)))
+        self.h = h
+
+    def submit(self, scene: "Scene", n: int = 1) -> int:
+        t = C.c_ulonglong()
+        _check(self.lib.ipc_server_submit(self.h, scene.h, int(n), C.byref(t)))
+        return int(t.value)
+
+    def _result(self, code, st, lat):
+        if code == IPC_PENDING:
+            return None
+        _check(code)
+        out = {f: getattr(st, f) for f, _ in StepStats._fields_}
+        out["status"] = code
+        out["latency_ms"] = lat.value
+        return out
+
+    def poll(self, ticket: int):
+        """None while pending, else the step statistics and latency_ms."""
+        st, lat = StepStats(), C.c_double()
+        return self._result(self.lib.ipc_server_poll(self.h, C.c_ulonglong(ticket), C.byref(st), C.byref(lat)), st,
+                            lat)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        st, lat = StepStats(), C.c_double()
+        code = self.lib.ipc_server_wait(self.h, C.c_ulonglong(ticket), float(timeout_s) * 1e3, C.byref(st),
+                                        C.byref(lat))
+        r = self._result(code, st, lat)
+        if r is None:
+            raise TimeoutError(f"request {ticket} still pending after {timeout_s} s")
+        return r
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.ipc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
