@@ -101,6 +101,12 @@ typedef struct ipc_params {
                                 (built at the query's own positions where
                                 needed).  All three give the same contact and
                                 CCD candidate sets. */
+    int graphs;              /* 1 (default): the per-iteration launch sequences
+                                (preconditioner, forms and direction; cached-
+                                list CCD and first trial) replay as CUDA graphs,
+                                captured the second time each configuration
+                                occurs; 0: every kernel launched one by one.
+                                Both run the same kernels on the same data. */
 } ipc_params;
 
 /* Device allocator used for all scene memory; NULL functions = cudaMalloc. */

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "dev.cuh"
@@ -154,6 +156,18 @@ struct ipc_scene {
     bool cand_ok = false;
     double cand_delta = 0.0;
     double cand_bound = 0.0;
+    // CUDA graphs of the per-iteration launch sequences, keyed by the bytes of
+    // the device-state struct (which changes with the buffer swaps) and the
+    // sequence's host flags; a key is captured the second time it occurs
+    std::unordered_map<unsigned long long, cudaGraphExec_t> graphs;
+    std::unordered_set<unsigned long long> seen, uncapturable;
+    cudaStream_t own = nullptr;  // used when the caller passes the legacy default stream
+    cudaEvent_t own_ev = nullptr;
+    ~ipc_scene() {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        if (own_ev) cudaEventDestroy(own_ev);
+        if (own) cudaStreamDestroy(own);
+    }
 };
 
 namespace {
@@ -503,6 +517,52 @@ int setup_dev(ipc_scene* s) {
     return 0;
 }
 
+// Launches seq() on st as a CUDA graph when the scene allows it: replayed
+// when this key (device-state bytes, variant) has a graph, captured when the
+// key is seen for the second time (the first run warms one-time setup and
+// allocations), launched directly otherwise. A sequence that cannot be
+// captured is launched directly from then on.
+template <class R, class F>
+int run_seq(ipc_scene* s, const Dev<R>& D, cudaStream_t st, unsigned long long variant, F&& seq) {
+    if (!s->prm.graphs || s->prof.on) {
+        seq();
+        return 0;
+    }
+    unsigned long long key = 1469598103934665603ULL ^ (variant * 0x9E3779B97F4A7C15ULL);
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&D);
+    for (size_t i = 0; i < sizeof(Dev<R>); ++i) key = (key ^ b[i]) * 1099511628211ULL;
+    auto it = s->graphs.find(key);
+    if (it != s->graphs.end()) {
+        CUDA_TRY(cudaGraphLaunch(it->second, st));
+        return 0;
+    }
+    if (s->uncapturable.count(key) || s->seen.insert(key).second) {
+        seq();
+        return 0;
+    }
+    if (s->graphs.size() >= 64) {  // bound the cache (buffers regrown many times)
+        for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+        s->graphs.clear();
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        seq();
+        if (cudaStreamEndCapture(st, &g) == cudaSuccess && g &&
+            cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+            cudaGraphDestroy(g);
+            s->graphs[key] = ex;
+            CUDA_TRY(cudaGraphLaunch(ex, st));
+            return 0;
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();  // clear the capture failure
+    s->uncapturable.insert(key);
+    seq();  // nothing of the failed capture ran
+    return 0;
+}
+
 template <class R>
 int read_view(ipc_scene* s, const Dev<R>& D, cudaStream_t st) {
     CUDA_TRY(cudaMemcpyAsync(&s->hv->S, D.S, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -688,39 +748,41 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         memset(&rec, 0, sizeof rec);
         rec.restart = restart ? 1 : 0;
         rec.n_contacts = s->hv->nC;
-        if (restart) {
-            Stage t(s, 0, st);
-            launch_restart(D, D.x, D.C, st);
-            ++restarts;
-        } else {
-            Stage t(s, 1, st);
-            launch_classify(D, D.C, st);
-        }
-        {
-            Stage t(s, 7, st);
-            launch_restrict(D, D.g, st);
-        }
-        {
-            Stage t(s, 2, st);
-            launch_blocks(D, D.g, D.z, D.C, !restart, st);
-        }
-        {
-            Stage t(s, 7, st);
-            launch_prolong(D, D.z, st);
-        }
-        {
-            Stage t(s, 3, st);
-            launch_forms(D, D.C, restart, st);
-        }
-        {
-            Stage t(s, 4, st);
-            launch_direction(D, restart, st);
-        }
+        if (restart) ++restarts;
+        run_seq(s, D, st, restart ? 1 : 2, [&] {
+            if (restart) {
+                Stage t(s, 0, st);
+                launch_restart(D, D.x, D.C, st);
+            } else {
+                Stage t(s, 1, st);
+                launch_classify(D, D.C, st);
+            }
+            {
+                Stage t(s, 7, st);
+                launch_restrict(D, D.g, st);
+            }
+            {
+                Stage t(s, 2, st);
+                launch_blocks(D, D.g, D.z, D.C, !restart, st);
+            }
+            {
+                Stage t(s, 7, st);
+                launch_prolong(D, D.z, st);
+            }
+            {
+                Stage t(s, 3, st);
+                launch_forms(D, D.C, restart, st);
+            }
+            {
+                Stage t(s, 4, st);
+                launch_direction(D, restart, st);
+            }
+            // g.z, max|p| and the list drift of this iteration
+            cudaMemcpyAsync(&s->hv->S.gz, &D.S->gz, sizeof(double), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(&s->hv->S.pmax, &D.S->pmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        });
         bool use_list = false;
         double bound_after = INFINITY;
-        // g.z, max|p| and the list drift of this iteration
-        CUDA_TRY(cudaMemcpyAsync(&s->hv->S.gz, &D.S->gz, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CUDA_TRY(cudaMemcpyAsync(&s->hv->S.pmax, &D.S->pmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         if (!restart && !(s->hv->S.gz > 0.0)) {
             // the Woodbury-patched preconditioner is not positive at g (FP32
@@ -736,16 +798,32 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         {
             Stage t(s, 5, st);
             if (int e = choose_broad_phase(s, D, st, &use_list, &bound_after)) return e;
-            if (use_list)
-                launch_ccd_list(D, st);
-            else
+            if (use_list) {
+                run_seq(s, D, st, 3, [&] { launch_ccd_list(D, st, 1); });
+                launch_ccd_list(D, st, 2);
+            } else {
                 launch_ccd(D, st);
+            }
         }
-        {
-            Stage t(s, 6, st);
-            eval_trial(D, 0, 0.0, st, use_list);
+        if (use_list) {
+            run_seq(s, D, st, 4, [&] {
+                {
+                    Stage t(s, 6, st);
+                    eval_trial(D, 0, 0.0, st, true);
+                }
+                cudaMemcpyAsync(&s->hv->S, D.S, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(&s->hv->nC, D.C.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+                cudaMemcpyAsync(&s->hv->nCt, D.Ct.count, sizeof(int), cudaMemcpyDeviceToHost, st);
+            });
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (s->prof.on) s->prof.resolve();
+        } else {
+            {
+                Stage t(s, 6, st);
+                eval_trial(D, 0, 0.0, st, false);
+            }
+            if (int e = read_view(s, D, st)) return e;
         }
-        if (int e = read_view(s, D, st)) return e;
         Scalars S = s->hv->S;
         if (S.async_timeout) return fail(IPC_ERR_TIMEOUT, "a bulk copy into shared memory did not complete");
         if (S.nan_flag || !(S.gz == S.gz))
@@ -841,21 +919,40 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
 }
 
 template <class R>
-int step_impl(ipc_scene* s, int n, cudaStream_t st, ipc_step_stats* out) {
+int step_impl(ipc_scene* s, int n, cudaStream_t caller, ipc_step_stats* out) {
+    // CUDA graphs cannot be captured on the legacy default stream: the work
+    // then runs on a stream of the scene's own, after everything queued on
+    // the caller's stream and before anything queued there later
+    cudaStream_t st = caller;
+    if (caller == nullptr || caller == cudaStreamLegacy) {
+        if (!s->own) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking));
+            CUDA_TRY(cudaEventCreateWithFlags(&s->own_ev, cudaEventDisableTiming));
+        }
+        CUDA_TRY(cudaEventRecord(s->own_ev, caller));
+        CUDA_TRY(cudaStreamWaitEvent(s->own, s->own_ev, 0));
+        st = s->own;
+    }
     ipc_step_stats acc;
     memset(&acc, 0, sizeof acc);
     int worst = IPC_OK;
+    int rc = IPC_OK;
     for (int i = 0; i < n; ++i) {
         int r = run_timestep<R>(s, st, &acc);
         if (r < 0) {
-            if (out) *out = acc;
-            return r;
+            rc = r;
+            break;
         }
         if (r > worst) worst = r;
     }
+    if (st != caller) {
+        cudaEventRecord(s->own_ev, st);
+        cudaStreamWaitEvent(caller, s->own_ev, 0);
+    }
+    if (out) *out = acc;
+    if (rc < 0) return rc;
     CUDA_TRY(cudaStreamSynchronize(st));
     CUDA_TRY(cudaGetLastError());
-    if (out) *out = acc;
     return worst;
 }
 
@@ -1178,6 +1275,7 @@ void ipc_default_params(ipc_params* p) {
     p->precision = IPC_PREC_FP64;
     p->contact_capacity = 0;
     p->broad_phase = 0;
+    p->graphs = 1;
 }
 
 const char* ipc_last_error(void) { return g_err.c_str(); }

@@ -990,21 +990,25 @@ void launch_detect_list(const Dev<R>& D, const double* x, const ContactBuf& C, c
 }
 
 template <class R>
-void launch_ccd_list(const Dev<R>& D, cudaStream_t st) {
+void launch_ccd_list(const Dev<R>& D, cudaStream_t st, int part) {
     int ng = D.ngroups[0];
-    KL(k_ccd_begin<R><<<1, 1, 0, st>>>(D));
-    KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
-    KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
-    if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
-    KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D));
-    KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D));
-    if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
-    Scalars* S = D.S;
-    Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
-                 &S->alpha_min, &S->alpha_max, &S->vstat[0], &S->vstat[1]};
-    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
-                 &S->ccd_passes_b, &S->alpha_bmin, &S->alpha_bmax, &S->vstat[2], &S->vstat[3]};
-    verify_groupings(D, sub, bod, st);
+    if (part != 2) {  // per-pair bounds (capturable in a graph)
+        KL(k_ccd_begin<R><<<1, 1, 0, st>>>(D));
+        KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
+        KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
+        if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
+        KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D));
+        KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D));
+        if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
+    }
+    if (part != 1) {  // verification: one cooperative launch, ordered across scenes
+        Scalars* S = D.S;
+        Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
+                     &S->alpha_min, &S->alpha_max, &S->vstat[0], &S->vstat[1]};
+        Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
+                     &S->ccd_passes_b, &S->alpha_bmin, &S->alpha_bmax, &S->vstat[2], &S->vstat[3]};
+        verify_groupings(D, sub, bod, st);
+    }
 }
 
 #define INST(R)                                                                               \
@@ -1012,7 +1016,7 @@ void launch_ccd_list(const Dev<R>& D, cudaStream_t st) {
     template void launch_ccd<R>(const Dev<R>&, cudaStream_t);                                  \
     template void launch_cand_build<R>(const Dev<R>&, const double*, double, cudaStream_t);    \
     template void launch_detect_list<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t); \
-    template void launch_ccd_list<R>(const Dev<R>&, cudaStream_t);
+    template void launch_ccd_list<R>(const Dev<R>&, cudaStream_t, int);
 INST(double)
 INST(float)
 #undef INST
