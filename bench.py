@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--replays", type=int, default=30, help="L2-flushed replays per stage for the roofline")
     ap.add_argument("--profile-replays", action="store_true",
                     help="call cudaProfilerStart/Stop around the roofline replays (ncu --profile-from-start off)")
+    ap.add_argument("--serve", type=int, default=16,
+                    help="scenes in the serving measurement (ipc_server, 0 = skip)")
     ap.add_argument("--profile-from-step", type=int, default=-1,
                     help="call cudaProfilerStart before this timed step (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -203,6 +205,71 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, ipc, S, steps_per_scene=6, slots=8):
+    """Continuous batching through ipc_server: one closed-loop client per
+    scene (it submits one timestep, and the next when that one returns), for
+    `args.serve` scenes of 500-20k vertices (log-uniform), FP32 bulk. Against
+    it, the same timesteps with each scene stepped alone one after another,
+    in the plain FP64 form and in FP32."""
+    import torch
+    scs = S.batched_scenes(n_scenes=args.serve, seed=2)
+    nv = [int(sc["x0"].shape[0]) for sc in scs]
+
+    def make(prec):
+        return [ipc.Scene(sc, precision=prec, use_torch_allocator=False) for sc in scs]
+
+    def sequential(scenes):
+        for g, sc in zip(scenes, scs):  # warm-up: one-time setup and graph captures
+            g.set_state(sc["x0"], sc["v0"])
+            g.step(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for g, sc in zip(scenes, scs):
+            g.set_state(sc["x0"], sc["v0"])
+            g.step(steps_per_scene)
+        torch.cuda.synchronize()
+        return len(scs) * steps_per_scene / (time.perf_counter() - t0)
+
+    plain = make(ipc.IPC_PREC_FP64)
+    seq64 = sequential(plain)
+    for g in plain:
+        g.close()
+    mixed = make(ipc.IPC_PREC_FP32)
+    seq32 = sequential(mixed)
+    for g, sc in zip(mixed, scs):
+        g.set_state(sc["x0"], sc["v0"])
+    srv = ipc.Server(slots=slots)
+    left = [steps_per_scene] * len(scs)
+    lat = []
+    t0 = time.perf_counter()
+    live = {srv.submit(g, 1): i for i, g in enumerate(mixed)}
+    while live:
+        done = []
+        for tk, i in live.items():
+            r = srv.poll(tk)
+            if r is not None:
+                lat.append(r["latency_ms"])
+                done.append((tk, i))
+        for tk, i in done:
+            del live[tk]
+            left[i] -= 1
+            if left[i] > 0:
+                live[srv.submit(mixed[i], 1)] = i
+        if not done:
+            time.sleep(2e-4)
+    wall = time.perf_counter() - t0
+    srv.close()
+    for g in mixed:
+        g.close()
+    served = len(scs) * steps_per_scene / wall
+    lat.sort()
+    return {"scenes": len(scs), "vertices": f"{min(nv)}..{max(nv)} (total {sum(nv)})",
+            "timesteps_per_scene": steps_per_scene, "slots": slots, "unit": "timesteps/s",
+            "served_fp32": served, "sequential_fp32": seq32, "sequential_plain_fp64": seq64,
+            "speedup_vs_plain": served / seq64, "latency_ms_p50": lat[len(lat) // 2],
+            "latency_ms_p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -238,7 +305,6 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    scene.profile(True)
     launches0 = ipc.kernel_launches()
     iters = 0
     status = []
@@ -256,8 +322,6 @@ def main():
     if args.profile_from_step >= 0:
         torch.cuda.profiler.stop()
     launches = ipc.kernel_launches() - launches0
-    prof = scene.profile_read()
-    scene.profile(False)
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -282,22 +346,38 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
     for stg, sid in (("mas_blocks", 2), ("forms", 3)):
-        avg_ms = scene.profile_replay(sid, args.replays, flush=flush, stream=stream)
+        # median of single-launch replays (robust to the odd slow launch)
+        avg_ms = statistics.median(scene.profile_replay(sid, 1, flush=flush, stream=stream)
+                                   for _ in range(args.replays))
         ach = by[stg] / (avg_ms / 1e3) / 1e9
-        n = prof[stg]["launches"]
-        in_loop_us = 1e3 * prof[stg]["ms"] / n if n else None
         tr = TRAFFIC.get((stg, args.precision))
         traffic = tr["bytes_per_block"] * nblocks if tr and stg == "mas_blocks" else (
             tr["bytes_per_tet"] * nt if tr else None)
         roof[stg] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                      "traffic": traffic, "bytes_per_launch": by[stg], "avg_us": avg_ms * 1e3,
-                     "timing": f"{args.replays} replays on the final state, 256 MB read before each (L2 evicted), CUDA events",
-                     "in_loop_avg_us": in_loop_us, "in_loop_launches": n,
+                     "timing": f"median of {args.replays} replays on the final state, 256 MB read before each (L2 evicted), CUDA events",
                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     if args.profile_replays:
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     dominant = "mas_blocks"
+
+    # stage breakdown: a separate profiled pass over the first timesteps (the
+    # per-stage events need the kernels launched one by one, so the timed
+    # loop above runs without them and with its CUDA graphs)
+    n_prof = min(args.steps, 8)
+    scene.set_state(sc["x0"], sc["v0"])
+    scene.profile(True)
+    for _ in range(n_prof):
+        scene.step(1)
+    prof = scene.profile_read()
+    scene.profile(False)
+    for stg in roof:
+        n = prof[stg]["launches"]
+        roof[stg]["in_loop_avg_us"] = 1e3 * prof[stg]["ms"] / n if n else None
+        roof[stg]["in_loop_launches"] = n
+
+    serving = run_serving(args, ipc, S) if args.serve > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
     # host -> device, the step runs, positions come back device -> host
@@ -382,6 +462,8 @@ def main():
         "roofline": roof.get(dominant) if dominant else None,
         "roofline_stages": roof,
         "stage_ms": {k: v["ms"] for k, v in prof.items()},
+        "stage_ms_timesteps": f"0..{n_prof - 1}, a separate profiled pass (kernels launched one by one)",
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
