@@ -50,6 +50,8 @@ def parse():
                     help="call cudaProfilerStart/Stop around the roofline replays (ncu --profile-from-start off)")
     ap.add_argument("--serve", type=int, default=16,
                     help="scenes in the serving measurement (ipc_server, 0 = skip)")
+    ap.add_argument("--ablation", type=int, default=0,
+                    help="timesteps of the ablation runs (MAS maintenance, CCD step; 0 = skip)")
     ap.add_argument("--profile-from-step", type=int, default=-1,
                     help="call cudaProfilerStart before this timed step (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -203,6 +205,31 @@ def run_reference(args):
         "e2e": {"value": iters_per_s, "unit": "PNCG iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_ablation(args, ipc, S, prec):
+    """The paper's ablations on the same kernels: MAS maintenance (Woodbury
+    updates, full rebuild every iteration, frozen between restarts) and the
+    CCD step (per subdomain, global), `args.ablation` timesteps of the
+    workload each."""
+    import torch
+    sc = S.sphere_pile()
+    out = {}
+    for name, prm in (("woodbury_per_subdomain", {}), ("full_rebuild", {"mas_mode": 1}), ("freeze", {"mas_mode": 2}),
+                      ("global_alpha", {"ccd_mode": 1})):
+        g = ipc.Scene(sc, params=prm, precision=prec)
+        g.step(1)  # one-time setup and graph captures
+        g.set_state(sc["x0"], sc["v0"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.step(args.ablation)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"timesteps": args.ablation, "iters_per_step": st["iters"] / args.ablation,
+                     "rebuilds_per_step": st["restarts"] / args.ablation, "ms_per_step": 1e3 * dt / args.ablation,
+                     "converged": st["converged"]}
+        g.close()
+    return out
 
 
 def run_serving(args, ipc, S, steps_per_scene=6, slots=8):
@@ -378,6 +405,7 @@ def main():
         roof[stg]["in_loop_launches"] = n
 
     serving = run_serving(args, ipc, S) if args.serve > 0 and world == 1 else None
+    ablation = run_ablation(args, ipc, S, prec) if args.ablation > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
     # host -> device, the step runs, positions come back device -> host
@@ -464,6 +492,7 @@ def main():
         "stage_ms": {k: v["ms"] for k, v in prof.items()},
         "stage_ms_timesteps": f"0..{n_prof - 1}, a separate profiled pass (kernels launched one by one)",
         "serving": serving,
+        "ablation": ablation,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

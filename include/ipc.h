@@ -101,6 +101,16 @@ typedef struct ipc_params {
                                 (built at the query's own positions where
                                 needed).  All three give the same contact and
                                 CCD candidate sets. */
+    int mas_mode;            /* MAS maintenance between restarts (Sec. 4.3 and
+                                its ablation): 0 Sparse-Input Woodbury updates
+                                (default); 1 full rebuild, every iteration
+                                reassembles and reinverts the blocks at the
+                                current positions and contacts (the PNCG
+                                recurrence goes on: not a restart); 2 freeze,
+                                the preconditioner and H_base of the last
+                                restart serve unchanged */
+    int ccd_mode;            /* 0 per-subdomain step bounds alpha_d (Sec. 4.4,
+                                default); 1 one global step min_d alpha_d */
     int graphs;              /* 1 (default): the per-iteration launch sequences
                                 (preconditioner, forms and direction; cached-
                                 list CCD and first trial) replay as CUDA graphs,

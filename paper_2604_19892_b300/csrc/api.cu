@@ -748,12 +748,17 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         memset(&rec, 0, sizeof rec);
         rec.restart = restart ? 1 : 0;
         rec.n_contacts = s->hv->nC;
-        if (restart) ++restarts;
-        run_seq(s, D, st, restart ? 1 : 2, [&] {
-            if (restart) {
+        // MAS maintenance between restarts: Woodbury updates, a full rebuild
+        // (the blocks and H_base at the current state; not a PNCG restart) or
+        // nothing (frozen)
+        const bool rebuild = restart || P.mas_mode == 1;
+        const bool woodbury = !restart && P.mas_mode == 0;
+        if (rebuild) ++restarts;
+        run_seq(s, D, st, restart ? 1 : (P.mas_mode == 1 ? 5 : P.mas_mode == 2 ? 6 : 2), [&] {
+            if (rebuild) {
                 Stage t(s, 0, st);
                 launch_restart(D, D.x, D.C, st);
-            } else {
+            } else if (woodbury) {
                 Stage t(s, 1, st);
                 launch_classify(D, D.C, st);
             }
@@ -763,7 +768,7 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
             }
             {
                 Stage t(s, 2, st);
-                launch_blocks(D, D.g, D.z, D.C, !restart, st);
+                launch_blocks(D, D.g, D.z, D.C, woodbury, st);
             }
             {
                 Stage t(s, 7, st);
@@ -804,6 +809,7 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
             } else {
                 launch_ccd(D, st);
             }
+            if (P.ccd_mode == 1) launch_global_alpha(D, st);  // one step for every subdomain
         }
         if (use_list) {
             run_seq(s, D, st, 4, [&] {
@@ -1275,6 +1281,8 @@ void ipc_default_params(ipc_params* p) {
     p->precision = IPC_PREC_FP64;
     p->contact_capacity = 0;
     p->broad_phase = 0;
+    p->mas_mode = 0;
+    p->ccd_mode = 0;
     p->graphs = 1;
 }
 

@@ -698,6 +698,21 @@ __global__ void k_ccd_ee_list(Dev<R> D) {
     }
 }
 
+// global-step ablation: every subdomain and body takes the smallest step
+// bound (alpha_min after verification), and the line search's tiers see no
+// per-subdomain or per-body spread
+template <class R>
+__global__ void k_global_alpha(Dev<R> D) {
+    const double a = D.S->alpha_min;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < D.ngroups[0]; g += gridDim.x * blockDim.x) D.alpha[g] = a;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < D.nbody; b += gridDim.x * blockDim.x) D.alpha_b[b] = a;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        D.S->alpha_max = a;
+        D.S->alpha_bmin = a;
+        D.S->alpha_bmax = a;
+    }
+}
+
 template <class R>
 __global__ void k_fill(Dev<R> D, double* a, int n, double v) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1011,12 +1026,18 @@ void launch_ccd_list(const Dev<R>& D, cudaStream_t st, int part) {
     }
 }
 
+template <class R>
+void launch_global_alpha(const Dev<R>& D, cudaStream_t st) {
+    KL(k_global_alpha<R><<<nblk(std::max(D.ngroups[0], D.nbody)), kT, 0, st>>>(D));
+}
+
 #define INST(R)                                                                               \
     template void launch_detect<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t); \
     template void launch_ccd<R>(const Dev<R>&, cudaStream_t);                                  \
     template void launch_cand_build<R>(const Dev<R>&, const double*, double, cudaStream_t);    \
     template void launch_detect_list<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t); \
-    template void launch_ccd_list<R>(const Dev<R>&, cudaStream_t, int);
+    template void launch_ccd_list<R>(const Dev<R>&, cudaStream_t, int);          \
+    template void launch_global_alpha<R>(const Dev<R>&, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

@@ -50,6 +50,7 @@ template <class R> void launch_cand_build(const Dev<R>& D, const double* x, doub
 template <class R> void launch_detect_list(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st);
 // part 0: all; 1: the per-pair bounds only; 2: the verification only
 template <class R> void launch_ccd_list(const Dev<R>& D, cudaStream_t st, int part = 0);
+template <class R> void launch_global_alpha(const Dev<R>& D, cudaStream_t st);
 // S->accepted = E_try <= E_k
 template <class R> void launch_accept(const Dev<R>& D, cudaStream_t st);
 // H_base-only forms for evaluation entry points
