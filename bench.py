@@ -52,6 +52,8 @@ def parse():
                     help="scenes in the serving measurement (ipc_server, 0 = skip)")
     ap.add_argument("--ablation", type=int, default=0,
                     help="timesteps of the ablation runs (MAS maintenance, CCD step; 0 = skip)")
+    ap.add_argument("--scale", type=int, default=5,
+                    help="timesteps of the large-scene run (512 spheres in a 2.5 x 2 x 2.5 m box; 0 = skip)")
     ap.add_argument("--profile-from-step", type=int, default=-1,
                     help="call cudaProfilerStart before this timed step (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -232,6 +234,37 @@ def run_ablation(args, ipc, S, prec):
     return out
 
 
+def run_scale(args, ipc, S, prec, rsize, flush, stream, peak):
+    """The same method on a scene 8x the workload's: 512 spheres in a
+    2.5 x 2 x 2.5 m box, `args.scale` timesteps, plus the roofline replays of
+    the MAS apply and the forms at that size."""
+    import torch
+    sc = S.sphere_pile(n_balls=512, box=(2.5, 2.0, 2.5))
+    t0 = time.perf_counter()
+    g = ipc.Scene(sc, precision=prec)
+    setup_s = time.perf_counter() - t0
+    nv, nt = sc["x0"].shape[0], sc["tets"].shape[0]
+    nblocks = sum(int(q.max()) + 1 for q, _ in g.levels())
+    g.step(1)
+    g.set_state(sc["x0"], sc["v0"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = g.step(args.scale)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    by = stage_bytes(nv, nt, nblocks, rsize)
+    roof = {}
+    for stg, sid in (("mas_blocks", 2), ("forms", 3)):
+        ms = statistics.median(g.profile_replay(sid, 1, flush=flush, stream=stream) for _ in range(args.replays))
+        roof[stg] = {"avg_us": ms * 1e3, "achieved_GBs": by[stg] / (ms / 1e3) / 1e9,
+                     "frac": by[stg] / (ms / 1e3) / 1e9 / peak, "bytes_per_launch": by[stg]}
+    g.close()
+    return {"scene": "sphere_pile(n_balls=512, box=(2.5, 2, 2.5))", "vertices": int(nv), "tets": int(nt),
+            "blocks": nblocks, "timesteps": args.scale, "timesteps_per_s": args.scale / dt,
+            "iters_per_s": st["iters"] / dt, "iters_per_step": st["iters"] / args.scale,
+            "converged": st["converged"], "setup_s": setup_s, "roofline": roof}
+
+
 def run_serving(args, ipc, S, steps_per_scene=6, slots=8):
     """Continuous batching through ipc_server: one closed-loop client per
     scene (it submits one timestep, and the next when that one returns), for
@@ -406,6 +439,7 @@ def main():
 
     serving = run_serving(args, ipc, S) if args.serve > 0 and world == 1 else None
     ablation = run_ablation(args, ipc, S, prec) if args.ablation > 0 and world == 1 else None
+    scale = run_scale(args, ipc, S, prec, rsize, flush, stream, peak) if args.scale > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
     # host -> device, the step runs, positions come back device -> host
@@ -493,6 +527,7 @@ def main():
         "stage_ms_timesteps": f"0..{n_prof - 1}, a separate profiled pass (kernels launched one by one)",
         "serving": serving,
         "ablation": ablation,
+        "scale": scale,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

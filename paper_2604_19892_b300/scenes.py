@@ -216,16 +216,17 @@ def _rsa_centres(rng, count, radius, lo, hi, min_gap, max_tries=200000):
     return pts
 
 
-def sphere_pile(n_balls=64, radius=0.1, cells=8, seed=1, h=1.0 / 60, nu=0.4, rho=1000.0):
-    """Balls of the given radius at random non-overlapping centres in a 1 m box.
+def sphere_pile(n_balls=64, radius=0.1, cells=8, seed=1, h=1.0 / 60, nu=0.4, rho=1000.0, box=(1.0, 1.0, 1.0)):
+    """Balls of the given radius at random non-overlapping centres in a box
+    (1 m by default).
 
     Each ball is a cells^3 cube-to-ball mapped grid with 6 tets per cell; E is
     drawn log-uniform in [1e4, 1e6] per body.  The box spans y in
-    [0.05, 1.05] above the ground plane y=0.
+    [0.05, 0.05 + box[1]] above the ground plane y=0.
     """
     rng = np.random.default_rng(seed)
     lo = np.array([0.0, 0.05, 0.0])
-    hi = np.array([1.0, 1.05, 1.0])
+    hi = np.array([box[0], 0.05 + box[1], box[2]])
     centres = _rsa_centres(rng, n_balls, radius, lo, hi, 0.01)
     Es = np.exp(rng.uniform(math.log(1e4), math.log(1e6), size=n_balls))
     bodies = []
