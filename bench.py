@@ -66,6 +66,29 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(v, world):
+    """The largest v over the ranks of the process group (v itself alone):
+    the whole job takes as long as its slowest replica. The tensor lives on
+    the device the group's backend reduces on (GPU for NCCL, host for gloo)."""
+    if world <= 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rates(total_ms, world, steps, iters):
+    """Timesteps/s and PNCG iterations/s of the whole job: every rank steps
+    its own replica, so the work is world x (steps, iters) in the slowest
+    rank's time (iters taken from this rank's replica: the replicas are
+    the same scene)."""
+    secs = total_ms / 1e3
+    return world * steps / secs, world * iters / secs
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -386,13 +409,8 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    steps_per_s = world * args.steps / (total_ms / 1e3)
-    iters_per_s = world * iters / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    steps_per_s, iters_per_s = whole_job_rates(total_ms, world, args.steps, iters)
 
     # roofline of the two per-iteration HBM-bound stages (MAS block apply,
     # H~ quadratic forms): their kernels replayed on the final state of the
