@@ -760,6 +760,13 @@ __device__ __forceinline__ bool pair_violated(const Dev<R>& D, const Grouping& G
     v[3] = q.w;
     const int g0 = G.of[v[0]];
     if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) return false;
+    // groups with one common step a move the pair uniformly by a p, and each
+    // group's a is at most this pair's own safe fraction (the minimum over
+    // the pairs touching it, this one included): safe
+    {
+        const double a0 = a[g0];
+        if (a[G.of[v[1]]] == a0 && a[G.of[v[2]]] == a0 && a[G.of[v[3]]] == a0) return false;
+    }
     const int kind = D.str_t[k];
     {
         // the FP64 walk returns exactly 1 where the FP32 distance bound
