@@ -84,16 +84,12 @@ __global__ void k_elastic(Dev<R> D, const double* __restrict__ x, R* __restrict_
                 for (int j = 0; j < 3; ++j) s += (X[j + 1][r] - X[0][r]) * B[j][c];
                 F[r][c] = s;
             }
-        // columns f0, f1, f2 and cofactor columns
-        double C[3][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            int a = (c + 1) % 3, b = (c + 2) % 3;
-            C[0][c] = F[1][a] * F[2][b] - F[2][a] * F[1][b];
-            C[1][c] = F[2][a] * F[0][b] - F[0][a] * F[2][b];
-            C[2][c] = F[0][a] * F[1][b] - F[1][a] * F[0][b];
-        }
-        double J = F[0][0] * C[0][0] + F[1][0] * C[1][0] + F[2][0] * C[2][0];
+        // J = f0 . (f1 x f2): the first cofactor column in FP64 (the energy
+        // check needs J - 1 to FP64 accuracy); the gradient's cofactors are
+        // formed in R below
+        const double C0[3] = {F[1][1] * F[2][2] - F[2][1] * F[1][2], F[2][1] * F[0][2] - F[0][1] * F[2][2],
+                              F[0][1] * F[1][2] - F[1][1] * F[0][2]};
+        double J = F[0][0] * C0[0] + F[1][0] * C0[1] + F[2][0] * C0[2];
         double Ic = 0.0;
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -104,11 +100,23 @@ __global__ void k_elastic(Dev<R> D, const double* __restrict__ x, R* __restrict_
         e = h2V * (0.5 * mu * (Ic - 3.0) - mu * (J - 1.0) + 0.5 * lam * (J - 1.0) * (J - 1.0));
         if (g) {
             R s = (R)(lam * (J - 1.0) - mu);
+            R Fr[3][3], Cr[3][3];  // F and its cofactor matrix (columns f_a x f_b) in R
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Fr[r][c] = (R)F[r][c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int a = (c + 1) % 3, b = (c + 2) % 3;
+                Cr[0][c] = Fr[1][a] * Fr[2][b] - Fr[2][a] * Fr[1][b];
+                Cr[1][c] = Fr[2][a] * Fr[0][b] - Fr[0][a] * Fr[2][b];
+                Cr[2][c] = Fr[0][a] * Fr[1][b] - Fr[1][a] * Fr[0][b];
+            }
             R Pm[3][3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) Pm[r][c] = (R)mu * (R)F[r][c] + s * (R)C[r][c];
+                for (int c = 0; c < 3; ++c) Pm[r][c] = (R)mu * Fr[r][c] + s * Cr[r][c];
             R G[3][3];  // h^2 V P B^T: column j -> gradient of vertex j+1
 #pragma unroll
             for (int r = 0; r < 3; ++r)
