@@ -454,6 +454,7 @@ int setup_dev(ipc_scene* s) {
     D.gtmp = A.arr<int>(std::max(D.nbuckets, m.ngroups[0]) / 1024 + 16);
     D.pbox = A.arr<float4>(2 * (size_t)nprim);
     D.xf = A.arr<float4>(m.nv);
+    D.xsplit = sizeof(R) == 4 ? A.arr<float4>(2 * (size_t)m.nv) : nullptr;
     D.xpf = A.arr<float4>(m.nv);
     D.cellinv = A.arr<float>(1);
     D.cellsz = A.arr<double>(1);

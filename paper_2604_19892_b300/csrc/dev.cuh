@@ -173,6 +173,7 @@ struct Dev {
     float4* pbox;                          // per stored primitive: FP32 lo, hi (grown by the error bounds)
     float4* xf;                            // FP32 surface positions at the evaluation point (.w: error bound)
     float4* xpf;                           // FP32 surface positions at x + p (CCD), else a copy of xf
+    float4* xsplit;                        // 2 nv: FP32 hi and lo parts of the energy point (FP32 bulk)
     float* cellinv;                        // 1 / cell size, FP32
     double* cellsz;                        // scalar: cell size of the current build
     // cached candidate pairs (built at xref with margin delta): every PT / EE

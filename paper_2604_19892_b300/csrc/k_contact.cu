@@ -35,11 +35,13 @@ namespace {
 
 constexpr int kT = 128;
 constexpr int kMaxCells = 64;
-// Grid queries: kSplit threads per query primitive share its bucket entries
-// (and the large-box and brute-force lists) round-robin, so one crowded
+// Grid queries: S threads per query primitive share its bucket entries (and
+// the large-box and brute-force lists) round-robin, so one crowded
 // neighbourhood is not one thread's serial walk; every entry is still visited
-// by exactly one of them.
-constexpr int kSplit = 8;
+// by exactly one of them. Swept (CCD) and candidate-list boxes cover more
+// cells and entries than the proximity boxes, so they take a whole warp.
+constexpr int kSplitProx = 8;
+constexpr int kSplitSwept = 32;
 constexpr int kCcdPasses = 8;   // verification passes before the uniform fallback
 
 inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
@@ -161,8 +163,8 @@ __device__ __forceinline__ float pair_dist_lb(const Dev<R>& D, int kind, const i
 // the query walks its own cells and keeps a pair only in the cell holding
 // the low corner of the two boxes' intersection; boxes too large for the
 // grid are in a short list, and a query box too large for it scans all
-// nstored. Thread sub of kSplit takes every kSplit-th entry.
-template <class R, class F>
+// nstored. Thread sub of S takes every S-th entry.
+template <int S, class R, class F>
 __device__ __forceinline__ void grid_query(const Dev<R>& D, const float lo[3], const float hi[3], int nstored, int sub,
                                            F&& visit) {
     const float inv = *D.cellinv;
@@ -172,7 +174,7 @@ __device__ __forceinline__ void grid_query(const Dev<R>& D, const float lo[3], c
     if (!(nc > 0) || !box_in_range(lo, hi, inv)) nc = kMaxCells + 1;
     float blo[3], bhi[3];
     if (nc > kMaxCells) {
-        for (int j = sub; j < nstored; j += kSplit) {
+        for (int j = sub; j < nstored; j += S) {
             load_box(D, j, blo, bhi);
             if (overlap(lo, hi, blo, bhi)) visit(j);
         }
@@ -183,7 +185,7 @@ __device__ __forceinline__ void grid_query(const Dev<R>& D, const float lo[3], c
             for (int c = k0; c <= k1; ++c) {
                 const unsigned long long cc = pack_cell(a, bb, c);
                 const int bk = bucket_of(cc, D.nbuckets);
-                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += kSplit) {
+                for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += S) {
                     if (D.gcell[e] != cc) continue;
                     const int j = D.gentry[e];
                     load_box(D, j, blo, bhi);
@@ -195,7 +197,7 @@ __device__ __forceinline__ void grid_query(const Dev<R>& D, const float lo[3], c
                 }
             }
     const int nl = *D.gnlarge;
-    for (int k = sub; k < nl; k += kSplit) {
+    for (int k = sub; k < nl; k += S) {
         const int j = D.glarge[k];
         load_box(D, j, blo, bhi);
         if (overlap(lo, hi, blo, bhi)) visit(j);
@@ -368,23 +370,23 @@ __device__ void ee_try(const Dev<R>& D, const double* x, const ContactBuf& C, in
 template <class R>
 __global__ void k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
+    const int qi = (int)(gid / kSplitProx), sub = (int)(gid % kSplitProx);
     if (qi >= D.nsv) return;
     const int pv = D.sv[qi];
     float lo[3], hi[3];
     prim_box(D, &pv, 1, 0.f, lo, hi);
-    grid_query(D, lo, hi, D.nsf, sub, [&](int f) { pt_try(D, x, C, pv, f); });
+    grid_query<kSplitProx>(D, lo, hi, D.nsf, sub, [&](int f) { pt_try(D, x, C, pv, f); });
 }
 
 template <class R>
 __global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int* gin) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
+    const int i = (int)(gid / kSplitProx), sub = (int)(gid % kSplitProx);
     if (i >= D.nse) return;
     const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
     float lo[3], hi[3];
     prim_box(D, vid, 2, 0.f, lo, hi);
-    grid_query(D, lo, hi, D.nse, sub, [&](int j) {
+    grid_query<kSplitProx>(D, lo, hi, D.nse, sub, [&](int j) {
         if (j > i) ee_try(D, x, C, i, j);
     });
 }
@@ -545,12 +547,12 @@ __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
 template <class R>
 __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
+    const int qi = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
     if (qi >= D.nsv) return;
     const int pv = D.sv[qi];
     float lo[3], hi[3];
     prim_box(D, &pv, 1, 0.f, lo, hi);
-    grid_query(D, lo, hi, D.nsf, sub, [&](int f) {
+    grid_query<kSplitSwept>(D, lo, hi, D.nsf, sub, [&](int f) {
         int v[4] = {pv, D.sf[3 * f], D.sf[3 * f + 1], D.sf[3 * f + 2]};
         if (pv == v[1] || pv == v[2] || pv == v[3]) return;
         ccd_pair(D, 0, v);
@@ -560,12 +562,12 @@ __global__ void k_ccd_pt(Dev<R> D, const int* gin) {
 template <class R>
 __global__ void k_ccd_ee(Dev<R> D, const int* gin) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
+    const int i = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
     if (i >= D.nse) return;
     const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
     float lo[3], hi[3];
     prim_box(D, vid, 2, 0.f, lo, hi);
-    grid_query(D, lo, hi, D.nse, sub, [&](int j) {
+    grid_query<kSplitSwept>(D, lo, hi, D.nse, sub, [&](int j) {
         if (j <= i) return;
         int v[4] = {vid[0], vid[1], D.se[2 * j], D.se[2 * j + 1]};
         if (v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3]) return;
@@ -617,12 +619,12 @@ __device__ __forceinline__ void append_pair(int2* list, int* count, int cap, int
 template <class R>
 __global__ void k_cand_pt(Dev<R> D, const double* __restrict__ x) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int qi = (int)(gid / kSplit), sub = (int)(gid % kSplit);
+    const int qi = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
     if (qi >= D.nsv) return;
     const int pv = D.sv[qi];
     float lo[3], hi[3];
     prim_box(D, &pv, 1, 4.f * D.xf[pv].w, lo, hi);
-    grid_query(D, lo, hi, D.nsf, sub, [&](int f) {
+    grid_query<kSplitSwept>(D, lo, hi, D.nsf, sub, [&](int f) {
         if (pv == D.sf[3 * f] || pv == D.sf[3 * f + 1] || pv == D.sf[3 * f + 2]) return;
         append_pair(D.cand_pt, &D.cand_n[0], D.cand_cap, pv, f);
     });
@@ -637,12 +639,12 @@ __device__ __forceinline__ bool edges_adjacent(const Dev<R>& D, int i, int j) {
 template <class R>
 __global__ void k_cand_ee(Dev<R> D, const double* __restrict__ x) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int i = (int)(gid / kSplit), sub = (int)(gid % kSplit);
+    const int i = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
     if (i >= D.nse) return;
     const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
     float lo[3], hi[3];
     prim_box(D, vid, 2, 4.f * fmaxf(D.xf[vid[0]].w, D.xf[vid[1]].w), lo, hi);
-    grid_query(D, lo, hi, D.nse, sub, [&](int j) {
+    grid_query<kSplitSwept>(D, lo, hi, D.nse, sub, [&](int j) {
         if (j > i && !edges_adjacent(D, i, j)) append_pair(D.cand_ee, &D.cand_n[1], D.cand_cap, i, j);
     });
 }
@@ -952,9 +954,9 @@ void launch_detect(const Dev<R>& D, const double* x, const ContactBuf& C, cudaSt
     int* gin = D.gin;
     const float dh = round_up_f(D.dhat);
     build_grid<R>(D, D.sf, 3, D.nsf, dh, gin, false, st);
-    if (D.nsv) KL(k_prox_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, x, C));
+    if (D.nsv) KL(k_prox_pt<R><<<nblk((long long)D.nsv * kSplitProx), kT, 0, st>>>(D, x, C));
     build_grid<R>(D, D.se, 2, D.nse, dh, gin, false, st);
-    if (D.nse) KL(k_prox_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, x, C, gin));
+    if (D.nse) KL(k_prox_ee<R><<<nblk((long long)D.nse * kSplitProx), kT, 0, st>>>(D, x, C, gin));
     if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
 }
 
@@ -967,9 +969,9 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
     int* gin = D.gin;
     build_grid<R>(D, D.sf, 3, D.nsf, 0.f, gin, true, st);
-    if (D.nsv) KL(k_ccd_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, gin));
+    if (D.nsv) KL(k_ccd_pt<R><<<nblk((long long)D.nsv * kSplitSwept), kT, 0, st>>>(D, gin));
     build_grid<R>(D, D.se, 2, D.nse, 0.f, gin, true, st);
-    if (D.nse) KL(k_ccd_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, gin));
+    if (D.nse) KL(k_ccd_ee<R><<<nblk((long long)D.nse * kSplitSwept), kT, 0, st>>>(D, gin));
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     Scalars* S = D.S;
     Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
@@ -996,8 +998,8 @@ void launch_cand_build(const Dev<R>& D, const double* x, double delta, cudaStrea
         if (nprim > 0) KL(k_grid_count<R><<<nblk(nprim), kT, 0, st>>>(D, prims, nper, nprim, round_up_f(infl), gin));
         scan_exclusive(D.gcount, D.gstart, D.nbuckets, D.gtmp, st);
         if (nprim > 0) KL(k_grid_fill<R><<<nblk(nprim), kT, 0, st>>>(D, nprim, gin));
-        if (pass == 0 && D.nsv) KL(k_cand_pt<R><<<nblk((long long)D.nsv * kSplit), kT, 0, st>>>(D, x));
-        if (pass == 1 && D.nse) KL(k_cand_ee<R><<<nblk((long long)D.nse * kSplit), kT, 0, st>>>(D, x));
+        if (pass == 0 && D.nsv) KL(k_cand_pt<R><<<nblk((long long)D.nsv * kSplitSwept), kT, 0, st>>>(D, x));
+        if (pass == 1 && D.nse) KL(k_cand_ee<R><<<nblk((long long)D.nse * kSplitSwept), kT, 0, st>>>(D, x));
     }
     cudaMemcpyAsync(D.xref, x, sizeof(double) * 3 * (size_t)D.nv, cudaMemcpyDeviceToDevice, st);
 }

@@ -4,7 +4,10 @@
 // Elastic energy density (reading of the SNH the paper cites):
 //   Psi(F) = mu/2 (|F|^2 - 3) - mu (J - 1) + lambda/2 (J - 1)^2,
 //   P = mu F + (lambda (J - 1) - mu) cof(F),  F = Ds B,  grad_{x_j} = V P B^T e_j.
-// Energies are accumulated in FP64; gradients in R.
+// Energies are accumulated in FP64; gradients in R. With an FP32 bulk the
+// elastic energy is formed in double-float arithmetic (about 48 significant
+// bits) on the FP32 pipes: the FP64 pipe of this GPU is a small fraction of
+// its FP32 rate and was the bound of the all-FP64 form.
 #include "kernels.h"
 
 namespace ipcb {
@@ -33,12 +36,63 @@ __global__ void k_trial(Dev<R> D, int mode, double c) {
     D.xtry[i] = D.x[i] + a * (double)D.p[i];
 }
 
-// g = M (x - x~), E += 1/2 (x - x~)^T M (x - x~)
+// Double-float values (Dekker, "A floating-point technique for extending the
+// available precision", 1971; Knuth, TAOCP vol. 2, Sec. 4.2.2): an unevaluated
+// sum hi + lo of two floats with |lo| <= ulp(hi) / 2. two_sum and two_prod
+// are error-free; df_add is the short form whose error is a few units of
+// 2^-47 times the larger operand, which is the size of the inputs' own
+// representation error here. The _rn intrinsics are never fused into an FMA,
+// which the error-free steps rely on.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, {-b.hi, -b.lo}); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);  // exact residual of the product
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ double df_val(df a) { return (double)a.hi + (double)a.lo; }
+
+// g = M (x - x~), E += 1/2 (x - x~)^T M (x - x~). With an FP32 bulk it also
+// stores x as float hi / lo parts for the elastic pass that follows.
 template <class R>
 __global__ void k_inertia(Dev<R> D, const double* __restrict__ x, R* __restrict__ g, double* E) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     double e = 0.0;
     if (v < D.nv) {
+        if constexpr (sizeof(R) == 4) {
+            float hi[3], lo[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double xv = x[3 * v + r];
+                hi[r] = (float)xv;
+                lo[r] = (float)(xv - (double)hi[r]);  // xv - hi is exact
+            }
+            D.xsplit[2 * (size_t)v] = make_float4(hi[0], hi[1], hi[2], 0.f);
+            D.xsplit[2 * (size_t)v + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+        }
         double m = D.massd[v];
         double d0 = x[3 * v] - D.xt[3 * v];
         double d1 = x[3 * v + 1] - D.xt[3 * v + 1];
@@ -58,6 +112,92 @@ __device__ __forceinline__ void load_B(const Dev<R>& D, int t, double B[3][3]) {
     const R* base = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
 #pragma unroll
     for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = (double)base[c * kPack];
+}
+
+// Elastic energy and gradient with an FP32 bulk: Ds, F, |F|^2 and J in
+// double-float from the hi / lo positions k_inertia stored (B is exact in
+// FP32); the energy line in FP64; the gradient from F's leading floats.
+__global__ void k_elastic_df(Dev<float> D, float* __restrict__ g, double* E) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (t < D.nt) {
+        const int4 q = D.tets[t];
+        const int vid[4] = {q.x, q.y, q.z, q.w};
+        df X[4][3];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 h = D.xsplit[2 * (size_t)vid[j]], l = D.xsplit[2 * (size_t)vid[j] + 1];
+            X[j][0] = {h.x, l.x};
+            X[j][1] = {h.y, l.y};
+            X[j][2] = {h.z, l.z};
+        }
+        float B[3][3];
+        const float* base = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = base[c * kPack];
+        df Ds[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Ds[r][j] = df_sub(X[j + 1][r], X[0][r]);
+        df F[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                F[r][c] = df_add(df_add(df_mulf(Ds[r][0], B[0][c]), df_mulf(Ds[r][1], B[1][c])),
+                                 df_mulf(Ds[r][2], B[2][c]));
+        const df C00 = df_sub(df_mul(F[1][1], F[2][2]), df_mul(F[2][1], F[1][2]));
+        const df C01 = df_sub(df_mul(F[2][1], F[0][2]), df_mul(F[0][1], F[2][2]));
+        const df C02 = df_sub(df_mul(F[0][1], F[1][2]), df_mul(F[1][1], F[0][2]));
+        const df J = df_add(df_add(df_mul(F[0][0], C00), df_mul(F[1][0], C01)), df_mul(F[2][0], C02));
+        df Ic = {-3.f, 0.f};
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Ic = df_add(Ic, df_mul(F[r][c], F[r][c]));
+        const double Jm1 = df_val(df_add(J, {-1.f, 0.f})), Ic3 = df_val(Ic);
+        const double mu = D.tet_mu[t], lam = D.tet_lam[t], V = D.tet_vol[t];
+        const double h2V = D.h * D.h * V;
+        e = h2V * (0.5 * mu * Ic3 - mu * Jm1 + 0.5 * lam * Jm1 * Jm1);
+        if (g) {
+            const float s = (float)(lam * Jm1 - mu);
+            float Fr[3][3], Cr[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Fr[r][c] = F[r][c].hi;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int a = (c + 1) % 3, b = (c + 2) % 3;
+                Cr[0][c] = Fr[1][a] * Fr[2][b] - Fr[2][a] * Fr[1][b];
+                Cr[1][c] = Fr[2][a] * Fr[0][b] - Fr[0][a] * Fr[2][b];
+                Cr[2][c] = Fr[0][a] * Fr[1][b] - Fr[1][a] * Fr[0][b];
+            }
+            const float muf = (float)mu, hvf = (float)h2V;
+            float Pm[3][3], G[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Pm[r][c] = muf * Fr[r][c] + s * Cr[r][c];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc += Pm[r][c] * B[j][c];
+                    G[r][j] = hvf * acc;
+                }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                atomicAdd(&g[3 * vid[0] + r], -(G[r][0] + G[r][1] + G[r][2]));
+#pragma unroll
+                for (int j = 0; j < 3; ++j) atomicAdd(&g[3 * vid[j + 1] + r], G[r][j]);
+            }
+        }
+    }
+    warp_add_to(E, e);
 }
 
 template <class R>
@@ -264,7 +404,10 @@ template <class R>
 void launch_energy_grad(const Dev<R>& D, const double* x, const ContactBuf& C, R* g, double* E, cudaStream_t st) {
     cudaMemsetAsync(E, 0, sizeof(double), st);
     KL(k_inertia<R><<<nblk(D.nv), kT, 0, st>>>(D, x, g, E));
-    KL(k_elastic<R><<<nblk(D.nt), kT, 0, st>>>(D, x, g, E));
+    if constexpr (sizeof(R) == 4)
+        KL(k_elastic_df<<<nblk(D.nt), kT, 0, st>>>(D, g, E));
+    else
+        KL(k_elastic<R><<<nblk(D.nt), kT, 0, st>>>(D, x, g, E));
     KL(k_barrier<R><<<1184, kT, 0, st>>>(D, C, g, E));
 }
 
