@@ -281,6 +281,7 @@ int setup_dev(ipc_scene* s) {
     double* d_vol = A.arr<double>(m.nt);
     double* d_mu = A.arr<double>(m.nt);
     double* d_lam = A.arr<double>(m.nt);
+    float2* d_ec = sizeof(R) == 4 ? A.arr<float2>(3 * (size_t)m.nt) : nullptr;
     std::vector<R> massr(m.mass.begin(), m.mass.end());
     R* d_mass = A.arr<R>(m.nv);
     double* d_massd = A.arr<double>(m.nv);
@@ -471,6 +472,7 @@ int setup_dev(ipc_scene* s) {
     D.tet_vol = d_vol;
     D.tet_mu = d_mu;
     D.tet_lam = d_lam;
+    D.tet_ec = d_ec;
     D.mass = d_mass;
     D.massd = d_massd;
     D.sv = d_sv;
@@ -489,6 +491,19 @@ int setup_dev(ipc_scene* s) {
     CUDA_TRY(cudaMemcpy(d_vol, m.vol.data(), sizeof(double) * m.nt, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_mu, m.mu.data(), sizeof(double) * m.nt, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_lam, m.lam.data(), sizeof(double) * m.nt, cudaMemcpyHostToDevice));
+    if (d_ec) {
+        // the elastic energy's coefficients as float pairs hi + lo (to ~2^-48)
+        std::vector<float2> ec(3 * (size_t)m.nt);
+        for (int t = 0; t < m.nt; ++t) {
+            const double h2V = p.h * p.h * m.vol[t];
+            const double c[3] = {0.5 * h2V * m.mu[t], h2V * m.mu[t], 0.5 * h2V * m.lam[t]};
+            for (int k = 0; k < 3; ++k) {
+                const float hi = (float)c[k];
+                ec[3 * (size_t)t + k] = make_float2(hi, (float)(c[k] - (double)hi));
+            }
+        }
+        CUDA_TRY(cudaMemcpy(d_ec, ec.data(), sizeof(float2) * ec.size(), cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(cudaMemcpy(d_mass, massr.data(), sizeof(R) * m.nv, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_massd, m.mass.data(), sizeof(double) * m.nv, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(d_mdiag, mdiag.data(), sizeof(double) * mdiag.size(), cudaMemcpyHostToDevice));

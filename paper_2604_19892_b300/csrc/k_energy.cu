@@ -114,12 +114,14 @@ __device__ __forceinline__ void load_B(const Dev<R>& D, int t, double B[3][3]) {
     for (int c = 0; c < 9; ++c) B[c / 3][c % 3] = (double)base[c * kPack];
 }
 
-// Elastic energy and gradient with an FP32 bulk: Ds, F, |F|^2 and J in
-// double-float from the hi / lo positions k_inertia stored (B is exact in
-// FP32); the energy line in FP64; the gradient from F's leading floats.
+// Elastic energy and gradient with an FP32 bulk: Ds, F, |F|^2, J and the
+// energy in double-float from the hi / lo positions k_inertia stored (B is
+// exact in FP32; the coefficients h^2 V mu / 2, h^2 V mu, h^2 V lam / 2 are
+// float pairs), summed per warp in double-float and added to E in FP64 once
+// per warp; the gradient in FP32 from F's leading floats.
 __global__ void k_elastic_df(Dev<float> D, float* __restrict__ g, double* E) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double e = 0.0;
+    df e = {0.f, 0.f};
     if (t < D.nt) {
         const int4 q = D.tets[t];
         const int vid[4] = {q.x, q.y, q.z, q.w};
@@ -156,12 +158,14 @@ __global__ void k_elastic_df(Dev<float> D, float* __restrict__ g, double* E) {
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c) Ic = df_add(Ic, df_mul(F[r][c], F[r][c]));
-        const double Jm1 = df_val(df_add(J, {-1.f, 0.f})), Ic3 = df_val(Ic);
-        const double mu = D.tet_mu[t], lam = D.tet_lam[t], V = D.tet_vol[t];
-        const double h2V = D.h * D.h * V;
-        e = h2V * (0.5 * mu * Ic3 - mu * Jm1 + 0.5 * lam * Jm1 * Jm1);
+        const df Jm1 = df_add(J, {-1.f, 0.f});
+        const float2 e0 = D.tet_ec[3 * (size_t)t], e1 = D.tet_ec[3 * (size_t)t + 1], e2 = D.tet_ec[3 * (size_t)t + 2];
+        const df ca = {e0.x, e0.y}, cb = {e1.x, e1.y}, cc = {e2.x, e2.y};
+        // h^2 V (mu/2 (|F|^2 - 3) - mu (J - 1) + lam/2 (J - 1)^2)
+        e = df_add(df_sub(df_mul(ca, Ic), df_mul(cb, Jm1)), df_mul(df_mul(cc, Jm1), Jm1));
         if (g) {
-            const float s = (float)(lam * Jm1 - mu);
+            // h^2 V P = cb F + (2 cc (J - 1) - cb) cof(F)
+            const float s = 2.f * cc.hi * Jm1.hi - cb.hi;
             float Fr[3][3], Cr[3][3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
@@ -174,12 +178,11 @@ __global__ void k_elastic_df(Dev<float> D, float* __restrict__ g, double* E) {
                 Cr[1][c] = Fr[2][a] * Fr[0][b] - Fr[0][a] * Fr[2][b];
                 Cr[2][c] = Fr[0][a] * Fr[1][b] - Fr[1][a] * Fr[0][b];
             }
-            const float muf = (float)mu, hvf = (float)h2V;
             float Pm[3][3], G[3][3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) Pm[r][c] = muf * Fr[r][c] + s * Cr[r][c];
+                for (int c = 0; c < 3; ++c) Pm[r][c] = cb.hi * Fr[r][c] + s * Cr[r][c];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -187,7 +190,7 @@ __global__ void k_elastic_df(Dev<float> D, float* __restrict__ g, double* E) {
                     float acc = 0.f;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) acc += Pm[r][c] * B[j][c];
-                    G[r][j] = hvf * acc;
+                    G[r][j] = acc;
                 }
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
@@ -197,7 +200,10 @@ __global__ void k_elastic_df(Dev<float> D, float* __restrict__ g, double* E) {
             }
         }
     }
-    warp_add_to(E, e);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        e = df_add(e, {__shfl_xor_sync(0xffffffffu, e.hi, o), __shfl_xor_sync(0xffffffffu, e.lo, o)});
+    if ((threadIdx.x & 31) == 0 && e.hi != 0.f) atomicAdd(E, df_val(e));
 }
 
 template <class R>

@@ -571,6 +571,29 @@ __device__ __forceinline__ void lds6(const T* p, T v[kTile]) {
         v[2 * i + 1] = w.y;
     }
 }
+// s_r x s_c as FP32 with x FP64. x is rounded to FP32 (nearest, ties to
+// even) on the integer pipes: the IEEE 754 binary64 fields are re-packed as
+// binary32 (exponent bias 1023 -> 127, the 52-bit fraction rounded to 23
+// bits; a carry out of the fraction raises the exponent, as the format
+// intends), then scaled in FP32. Zeros and magnitudes within 2^+-100 take this
+// path; anything else (no assembled Hessian entry in practice) is scaled in
+// FP64 before rounding, so an entry beyond the FP32 range still maps to its
+// finite scaled value. B300's FP64 pipe is a small fraction of its integer
+// rate, and 9,216 FP64 scalings per block were the FP32 inversion's largest
+// single cost.
+__device__ __forceinline__ float scaled_f32(double x, float sr, float sc) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned ex = (unsigned)(bits >> 52) & 0x7FFu;
+    if ((bits << 1) == 0ULL) return 0.f;
+    if (ex < 1023u - 100u || ex > 1023u + 100u) return (float)(x * (double)sr * (double)sc);
+    const unsigned long long frac = bits & ((1ULL << 52) - 1ULL);
+    unsigned m = (unsigned)(frac >> 29);
+    const unsigned rest = (unsigned)frac & ((1u << 29) - 1u);
+    const unsigned half = 1u << 28;
+    m += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
+    const unsigned fb = ((unsigned)(bits >> 32) & 0x80000000u) + ((ex - 1023u + 127u) << 23) + m;
+    return __uint_as_float(fb) * (sr * sc);
+}
 __device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
 // non-negative floats and doubles order like their bit patterns
@@ -640,6 +663,8 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
             if (act) {
                 if (mem[r / 3] < 0 || mem[c / 3] < 0)
                     v = (r == c) ? (T)1 : (T)0;
+                else if constexpr (sizeof(T) == 4)
+                    v = scaled_f32(src[r * kBlk + c], sc[r], sc[c]);
                 else
                     v = (T)(src[r * kBlk + c] * (double)sc[r] * (double)sc[c]);
             }
