@@ -117,6 +117,12 @@ typedef struct ipc_params {
                                 captured the second time each configuration
                                 occurs; 0: every kernel launched one by one.
                                 Both run the same kernels on the same data. */
+    double fp32_pivot_floor; /* FP32 bulk only: a block whose FP32 Cholesky
+                                of the unit-diagonal scaled block meets a pivot
+                                at or below this value (or a column entry
+                                L_rk^2 > 1) is inverted again in FP64 with the
+                                pivot rules (Sec. 4.2). Default 1e-6; 1 sends
+                                every block to FP64. */
 } ipc_params;
 
 /* Device allocator used for all scene memory; NULL functions = cudaMalloc. */
@@ -181,7 +187,13 @@ typedef enum ipc_query_kind {
     IPC_Q_LEVEL_MAP = 9,     /* per level: group and slot of each node (see
                                 ipc_query_level) */
     IPC_Q_BBOX_DIAG = 10,    /* double */
-    IPC_Q_N_BODIES = 11      /* int: connected bodies of the mesh */
+    IPC_Q_N_BODIES = 11,     /* int: connected bodies of the mesh */
+    IPC_Q_FP64_BLOCKS = 12   /* int: subdomain blocks the last restart inverted
+                                in FP64. FP32 bulk: the blocks whose FP32
+                                factorisation would floor a pivot or raise one
+                                (Sec. 4.2 inverse with the row-norm bound), 0
+                                before the first restart; FP64 bulk: every
+                                block. */
 } ipc_query_kind;
 
 /* Copy a piece of state into host memory dst (dst_bytes long). */

@@ -251,6 +251,7 @@ int setup_dev(ipc_scene* s) {
     D.upd_cap = D.cap;
     D.straddle_cap = 32 * (D.nsf + D.nse) + 4096;  // 20 bytes per candidate
     D.h = p.h;
+    D.piv32 = (float)(p.fp32_pivot_floor > 0.0 ? p.fp32_pivot_floor : 1e-6);
     D.dhat = p.dhat;
     D.kappa = p.kappa;
     D.eps_conv = p.tol * p.h * m.bbox_diag;
@@ -525,6 +526,7 @@ int setup_dev(ipc_scene* s) {
     CUDA_TRY(cudaMemcpy(D.x, m.x0.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(D.v, m.v0.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(D.S, 0, sizeof(Scalars)));
+    CUDA_TRY(cudaMemset(D.invflag, 0, sizeof(int) * std::max(D.blk_off[D.nlev], 1)));
     CUDA_TRY(cudaMemset(D.hess, 0, sizeof(R) * (size_t)D.ntp * kH * kPack));
     CUDA_TRY(cudaMemset(D.Cb.count, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(D.C.count, 0, sizeof(int)));
@@ -1300,6 +1302,7 @@ void ipc_default_params(ipc_params* p) {
     p->mas_mode = 0;
     p->ccd_mode = 0;
     p->graphs = 1;
+    p->fp32_pivot_floor = 1e-6;
 }
 
 const char* ipc_last_error(void) { return g_err.c_str(); }
@@ -1444,6 +1447,21 @@ int ipc_query(ipc_scene* s, int what, void* dst, size_t bytes, void* stream) {
             if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
             *(int*)dst = s->hm.nbody;
             return IPC_OK;
+        case IPC_Q_FP64_BLOCKS: {
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            const int nb = f64 ? s->dd.blk_off[s->dd.nlev] : s->df.blk_off[s->df.nlev];
+            if (f64) {
+                *(int*)dst = nb;
+                return IPC_OK;
+            }
+            std::vector<int> fl(std::max(nb, 1));
+            CUDA_TRY(cudaMemcpyAsync(fl.data(), s->df.invflag, sizeof(int) * nb, cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            int n = 0;
+            for (int i = 0; i < nb; ++i) n += fl[i] != 0;
+            *(int*)dst = n;
+            return IPC_OK;
+        }
         case IPC_Q_BBOX_DIAG:
             if (!need(sizeof(double))) return fail(IPC_ERR_INVALID, "destination too small");
             *(double*)dst = s->hm.bbox_diag;

@@ -102,6 +102,7 @@ struct Dev {
     const double* tet_vol;                 // V
     const double* tet_mu;
     const double* tet_lam;
+    float piv32;                           // FP32 inversion: pivot floor that sends a block to FP64
     const float2* tet_ec;                  // FP32 bulk: [nt][3] h^2 V mu / 2, h^2 V mu, h^2 V lam / 2 as float hi, lo
     const R* mass;
     const double* massd;

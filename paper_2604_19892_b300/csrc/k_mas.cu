@@ -828,6 +828,245 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
         }
 }
 
+// FP32 first pass of the block inversion, blocked by the same 6x6 tiles: per
+// panel of 6 columns, the diagonal tile's thread factors its tile in
+// registers, the tiles below solve against it (L_ik = A_ik L_kk^-T), and every
+// trailing tile takes the rank-6 update A_ij -= L_ik L_jk^T from a shared
+// panel buffer; W = L^-1 follows by tile rows the same way. Two barriers per
+// panel and one per W row block replace one per column, and the updates are
+// runs of 36 FMAs on operands from shared memory. The pivot rules of k_invert
+// are not reproduced here: a block whose factorisation would floor a pivot
+// or raise one (some L_rk^2 > 1) is flagged and returned early, and the FP64
+// pass inverts it with those rules; every other block is an unmodified
+// Cholesky factorisation, which is what k_invert computes for it too.
+template <class R>
+__global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* flags) {
+    static_assert(sizeof(R) == 4, "FP32 first pass");
+    extern __shared__ unsigned char smem_raw[];
+    float* buf = reinterpret_cast<float*>(smem_raw);  // 96 x 96: L^T, then W
+    float* pan = buf + kBlk * kBlk;                    // 2 x 6 x 96: panel columns of L, then row blocks of W
+    float* sc = pan + 2 * kTile * kBlk;                // diagonal scaling s
+    float* idg = sc + kBlk;                            // 1 / L_kk
+    __shared__ int s_bad;
+    const float eps_piv = D.piv32;
+    const int b = blockIdx.x;
+    int l = 0;
+    while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
+    const int grp = b - D.blk_off[l];
+    const int* mem = D.members[l] + (size_t)grp * kSub;
+    const double* src = l == 0 ? D.asmb + (size_t)b * kBlk * kBlk
+                               : D.asmbc + (size_t)(b - D.blk_off[1]) * kBlk * kBlk;
+    if (threadIdx.x == 0) s_bad = 0;
+    for (int r = threadIdx.x; r < kBlk; r += blockDim.x) {
+        const double d = src[r * kBlk + r];
+        sc[r] = (mem[r / 3] < 0 || !(d > 0.0)) ? 1.f : (float)(1.0 / sqrt(d));
+    }
+    // Cholesky: tiles ordered by column from the right, as in k_invert
+    const int t = threadIdx.x;
+    const bool act = t < kNTiles;
+    int ti = 0, tj = 0;
+    if (act) {
+        int rem = t, c = kNT - 1;
+        while (rem >= kNT - c) {
+            rem -= kNT - c;
+            --c;
+        }
+        tj = c;
+        ti = c + rem;
+    }
+    int r0 = kTile * ti, c0 = kTile * tj;
+    __syncthreads();
+    float a[kTile][kTile];
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) {
+            const int r = r0 + rr, c = c0 + cc;
+            float v = 0.f;
+            if (act) {
+                if (mem[r / 3] < 0 || mem[c / 3] < 0)
+                    v = (r == c) ? 1.f : 0.f;
+                else
+                    v = scaled_f32(src[r * kBlk + c], sc[r], sc[c]);
+            }
+            a[rr][cc] = v;
+        }
+    bool bad = false;
+    for (int kt = 0; kt < kNT; ++kt) {
+        float* P = pan + (kt & 1) * (kTile * kBlk);  // P[m * 96 + row] = L[row][6 kt + m]
+        if (act && ti == kt && tj == kt) {
+#pragma unroll
+            for (int c = 0; c < kTile; ++c) {
+                float piv = a[c][c];
+                if (!(piv > eps_piv)) {
+                    piv = eps_piv;
+                    bad = true;
+                }
+                const float isq = rsqrtf(piv);
+                a[c][c] = piv * isq;
+                idg[kTile * kt + c] = isq;
+#pragma unroll
+                for (int r = c + 1; r < kTile; ++r) {
+                    a[r][c] *= isq;
+                    if (!(a[r][c] * a[r][c] <= 1.f)) bad = true;  // NaN too
+                }
+#pragma unroll
+                for (int r = c + 1; r < kTile; ++r)
+#pragma unroll
+                    for (int q = c + 1; q <= r; ++q) a[r][q] -= a[r][c] * a[q][c];
+            }
+#pragma unroll
+            for (int m = 0; m < kTile; ++m)
+#pragma unroll
+                for (int r = 0; r < kTile; ++r) P[m * kBlk + r0 + r] = (r >= m) ? a[r][m] : 0.f;
+        }
+        __syncthreads();
+        if (act && ti > kt && tj == kt) {
+            float Lk[kTile][kTile], il[kTile];  // L_kk (strictly lower part used) and 1 / diag
+#pragma unroll
+            for (int c = 0; c < kTile; ++c) {
+                il[c] = idg[kTile * kt + c];
+#pragma unroll
+                for (int m = 0; m < c; ++m) Lk[c][m] = P[m * kBlk + kTile * kt + c];
+            }
+#pragma unroll
+            for (int c = 0; c < kTile; ++c)
+#pragma unroll
+                for (int r = 0; r < kTile; ++r) {
+                    float x = a[r][c];
+#pragma unroll
+                    for (int m = 0; m < c; ++m) x -= a[r][m] * Lk[c][m];
+                    x *= il[c];
+                    a[r][c] = x;
+                    if (!(x * x <= 1.f)) bad = true;
+                }
+#pragma unroll
+            for (int m = 0; m < kTile; ++m)
+#pragma unroll
+                for (int r = 0; r < kTile; ++r) P[m * kBlk + r0 + r] = a[r][m];
+        }
+        __syncthreads();
+        if (act && tj > kt) {
+#pragma unroll
+            for (int m = 0; m < kTile; ++m) {
+                float vr[kTile], vc[kTile];
+                lds6(P + m * kBlk + r0, vr);
+                lds6(P + m * kBlk + c0, vc);
+#pragma unroll
+                for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+                    for (int cc = 0; cc < kTile; ++cc) a[rr][cc] -= vr[rr] * vc[cc];
+            }
+        }
+    }
+    if (bad) s_bad = 1;
+    // L^T -> shared memory (lower entries only)
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc)
+            if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
+    __syncthreads();
+    if (s_bad) {  // uniform over the CTA: the FP64 pass inverts this block
+        if (threadIdx.x == 0) flags[b] = 1;
+        return;
+    }
+
+    // W = L^-1 by tile rows, tiles in row order: at step kt, row block kt is
+    // solved against L_kk; every later row block subtracts L_i,kt W_kt,j
+    if (act) {
+        int rem = t;
+        ti = 0;
+        while (rem > ti) {
+            ++ti;
+            rem -= ti;
+        }
+        tj = rem;
+    }
+    r0 = kTile * ti;
+    c0 = kTile * tj;
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (act && ti == tj && rr == cc) ? 1.f : 0.f;
+    for (int kt = 0; kt < kNT; ++kt) {
+        float* Q = pan + (kt & 1) * (kTile * kBlk);  // Q[m * 96 + col] = W[6 kt + m][col]
+        if (act && ti == kt) {
+            const int k0 = kTile * kt;
+#pragma unroll
+            for (int r = 0; r < kTile; ++r) {
+                float Lr[kTile];
+#pragma unroll
+                for (int m = 0; m < r; ++m) Lr[m] = buf[(k0 + m) * kBlk + k0 + r];
+                const float ir = idg[k0 + r];
+#pragma unroll
+                for (int cc = 0; cc < kTile; ++cc) {
+                    float x = a[r][cc];
+#pragma unroll
+                    for (int m = 0; m < r; ++m) x -= Lr[m] * a[m][cc];
+                    a[r][cc] = x * ir;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < kTile; ++m)
+#pragma unroll
+                for (int cc = 0; cc < kTile; ++cc) Q[m * kBlk + c0 + cc] = a[m][cc];
+        }
+        __syncthreads();
+        if (act && ti > kt && tj <= kt) {
+#pragma unroll
+            for (int m = 0; m < kTile; ++m) {
+                float lr[kTile], wc[kTile];
+                lds6(buf + (kTile * kt + m) * kBlk + r0, lr);
+                lds6(Q + m * kBlk + c0, wc);
+#pragma unroll
+                for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+                    for (int cc = 0; cc < kTile; ++cc) a[rr][cc] -= lr[rr] * wc[cc];
+            }
+        }
+    }
+    __syncthreads();
+    // W -> shared memory, row-major; tiles above the diagonal are zero
+    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
+        const int r = i / kBlk, c = i % kBlk;
+        if (r / kTile < c / kTile) buf[i] = 0.f;
+    }
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc)
+            if (act) buf[(r0 + rr) * kBlk + c0 + cc] = a[rr][cc];
+    __syncthreads();
+    if (threadIdx.x == 0) flags[b] = 0;
+    if (!act) return;
+    // B = s W^T W s; tile (ti, tj) needs rows k >= 6 ti of W only
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = 0.f;
+    for (int k = r0; k < kBlk; ++k) {
+        const float* Wk = buf + k * kBlk;
+        float wr[kTile], wc[kTile];
+        lds6(Wk + r0, wr);
+        lds6(Wk + c0, wc);
+#pragma unroll
+        for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < kTile; ++cc) a[rr][cc] += wr[rr] * wc[cc];
+    }
+    R* dst = D.blocks + (size_t)b * kBlk * kBlk;
+#pragma unroll
+    for (int rr = 0; rr < kTile; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < kTile; ++cc) {
+            const int r = r0 + rr, c = c0 + cc;
+            const R v = (R)(a[rr][cc] * sc[r] * sc[c]);
+            dst[r * kBlk + c] = v;
+            dst[c * kBlk + r] = v;
+        }
+}
+
 // ------------------------------------------------------ C_base snapshot
 
 template <class R>
@@ -1349,15 +1588,18 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
     // the blocks FP32 cannot carry
     const size_t smem_r = sizeof(R) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
     const size_t smem_d = sizeof(double) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
+    const size_t smem_t = sizeof(float) * ((size_t)kBlk * kBlk + 2 * kTile * kBlk + 2 * kBlk);
     static const bool attr_set = [&] {  // once per process, thread-safe
         cudaFuncSetAttribute(k_invert<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
         cudaFuncSetAttribute(k_invert<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
+        if (sizeof(R) == 4)
+            cudaFuncSetAttribute(k_invert_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t);
         return true;
     }();
     (void)attr_set;
     if (sizeof(R) == 4) {
         // FP32 first; the blocks that floored or raised a pivot again in FP64
-        KL(k_invert<R, R><<<nb, kInvThreads, smem_r, st>>>(D, D.invflag, 0));
+        if constexpr (sizeof(R) == 4) KL(k_invert_tiled<R><<<nb, kInvThreads, smem_t, st>>>(D, D.invflag));
         KL(k_invert<R, double><<<nb, kInvThreads, smem_d, st>>>(D, D.invflag, 1));
     } else {
         KL(k_invert<R, R><<<nb, kInvThreads, smem_r, st>>>(D, nullptr, 0));

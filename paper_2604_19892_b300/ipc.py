@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("eps_sing", C.c_double), ("eps_abs", C.c_double), ("K", C.c_int), ("iter_max", C.c_int),
                 ("levels_max", C.c_int), ("ls_max", C.c_int), ("precision", C.c_int),
                 ("contact_capacity", C.c_int), ("broad_phase", C.c_int), ("mas_mode", C.c_int),
-                ("ccd_mode", C.c_int), ("graphs", C.c_int)]
+                ("ccd_mode", C.c_int), ("graphs", C.c_int), ("fp32_pivot_floor", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -79,7 +79,7 @@ class Profile(C.Structure):
 STAGES = ["restart", "classify", "mas_blocks", "forms", "direction", "ccd", "trial_eval", "other"]
 
 Q_POSITIONS, Q_VELOCITIES, Q_N_VERTS, Q_N_CONTACTS, Q_SUBDOMAIN_ALPHA, Q_N_SUBDOMAINS, Q_TRACE_LEN, Q_TRACE, \
-    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG, Q_N_BODIES = range(12)
+    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG, Q_N_BODIES, Q_FP64_BLOCKS = range(13)
 
 _lib = None
 
@@ -189,7 +189,8 @@ def default_params(sc_params: dict, precision: int = IPC_PREC_FP64) -> Params:
     p = Params()
     lib.ipc_default_params(C.byref(p))
     for k in ("h", "dhat", "kappa", "tol", "delta", "eps_rot_deg", "ccd_shrink", "eps_sing", "eps_abs", "K",
-              "iter_max", "levels_max", "ls_max", "broad_phase", "mas_mode", "ccd_mode", "graphs"):
+              "iter_max", "levels_max", "ls_max", "broad_phase", "mas_mode", "ccd_mode", "graphs",
+              "fp32_pivot_floor"):
         if k in sc_params:
             setattr(p, k, type(getattr(p, k))(sc_params[k]))
     p.precision = precision
@@ -298,6 +299,11 @@ class Scene:
 
     def bbox_diag(self):
         return float(self._query_array(Q_BBOX_DIAG, 1)[0])
+
+    def fp64_blocks(self):
+        """Subdomain blocks the last restart inverted in FP64 (FP32 bulk: the
+        blocks whose FP32 factorisation would floor or raise a pivot)."""
+        return int(self._query_array(Q_FP64_BLOCKS, 1, np.int32)[0])
 
     def trace(self):
         n = int(self._query_array(Q_TRACE_LEN, 1, np.int32)[0])

@@ -145,6 +145,29 @@ def test_preconditioner_fp32(lib, name):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
+def test_fp32_inversion_hands_blocks_to_fp64(lib, name):
+    """The FP32 first pass of the block inversion hands a block to the FP64
+    pass (Sec. 4.2 inverse with the pivot rules) when a pivot of its scaled
+    Cholesky falls to fp32_pivot_floor. Scaled pivots are at most 1, so a
+    floor of 1 sends every block: the count equals the FP64 form's, and the
+    preconditioner follows the FP64 oracle to the FP32 storage of exact
+    inverses. At the default floor these contact states send none."""
+    import oracle as O
+    sc = SCENES[name]
+    xb = contact_state(sc, 0.9)
+    grad = RNG.normal(size=xb.shape)
+    zo = O.Scene(sc).precond_apply(xb, grad)
+    nb = lib.Scene(sc, precision=0).fp64_blocks()
+    for floor, expect in ((1.0, nb), (None, 0)):
+        g = lib.Scene(sc, precision=1, params=None if floor is None else {"fp32_pivot_floor": floor})
+        zg = g.precond_apply(xb, grad)
+        assert g.fp64_blocks() == expect, (floor, g.fp64_blocks(), nb)
+        rel = np.linalg.norm(zg - zo) / np.linalg.norm(zo)
+        assert rel <= (1e-5 if floor else 1e-3), (floor, rel)
+        assert float(np.sum(zg * grad)) > 0
+
+
+@pytest.mark.parametrize("name", list(SCENES))
 def test_forms_parity(lib, name):
     sc = SCENES[name]
     g, o = _pair(lib, sc)
