@@ -123,6 +123,11 @@ typedef struct ipc_params {
                                 L_rk^2 > 1) is inverted again in FP64 with the
                                 pivot rules (Sec. 4.2). Default 1e-6; 1 sends
                                 every block to FP64. */
+    int grid_pair_capacity;  /* pairs a grid query may hand to the list
+                                kernels per query pass (0: 16 per surface
+                                primitive + 4096). A pass that finds more
+                                runs its FP64 tests inside the query instead:
+                                same results, slower. */
 } ipc_params;
 
 /* Device allocator used for all scene memory; NULL functions = cudaMalloc. */

@@ -465,6 +465,9 @@ int setup_dev(ipc_scene* s) {
     D.cand_pt = A.arr<int2>(D.cand_cap);
     D.cand_ee = A.arr<int2>(D.cand_cap);
     D.cand_n = A.arr<int>(2);
+    D.gpair_cap = p.grid_pair_capacity > 0 ? p.grid_pair_capacity : 16 * (D.nsv + D.nse) + 4096;
+    D.gpair = A.arr<int2>(D.gpair_cap);
+    D.gpair_n = A.arr<int>(2);
     D.S = A.arr<Scalars>(1);
     if (!A.ok) return fail(IPC_ERR_OOM, "scene: device allocation failed");
 
@@ -1303,6 +1306,7 @@ void ipc_default_params(ipc_params* p) {
     p->ccd_mode = 0;
     p->graphs = 1;
     p->fp32_pivot_floor = 1e-6;
+    p->grid_pair_capacity = 0;
 }
 
 const char* ipc_last_error(void) { return g_err.c_str(); }

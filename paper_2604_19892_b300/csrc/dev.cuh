@@ -186,6 +186,11 @@ struct Dev {
     int2* cand_ee;                         // (edge i, edge j), i < j
     int* cand_n;                           // device: [0] PT count, [1] EE count
     int cand_cap;                          // capacity of each list
+    // pairs a grid query found and screened in FP32, finished by the list
+    // kernels: one thread per pair instead of the query's thread
+    int2* gpair;
+    int* gpair_n;                          // device: [0] pairs appended, [1] 1 if the list overflowed
+    int gpair_cap;
     // scalars
     Scalars* S;
 };

@@ -289,6 +289,22 @@ void build_grid(const Dev<R>& D, const int* prims, int nper, int nprim, float in
     if (nprim > 0) KL(k_grid_fill<R><<<nblk(nprim), kT, 0, st>>>(D, nprim, gin));
 }
 
+// Appends (a, b) to list (warp-aggregated); false when the list is full and
+// the pair was not stored.
+__device__ __forceinline__ bool append_ok(int2* list, int* count, int cap, int a, int b) {
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    int base = cap;
+    if (lane == leader && *(volatile int*)count < cap) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    const int k = base + rank;
+    if (k >= cap) return false;
+    list[k] = make_int2(a, b);
+    return true;
+}
+
 // ------------------------------------------------------------ contact write
 
 __device__ __forceinline__ void put_contact(const ContactBuf& C, int cap, int type, int4 v, unsigned long long key,
@@ -320,6 +336,21 @@ __device__ __forceinline__ void put_contact(const ContactBuf& C, int cap, int ty
         atomicMinPos(&S->min_dist, d);
     else
         S->nonpos = 1;  // touching or penetrating (bit-pattern min is only valid for d > 0)
+}
+
+// The FP32 prefilters of pt_try / ee_try: false when the pair cannot be
+// within dhat (or shares a vertex), so the FP64 test is not needed.
+template <class R>
+__device__ __forceinline__ bool pt_needed(const Dev<R>& D, int pv, int f) {
+    const int v[4] = {pv, D.sf[3 * f], D.sf[3 * f + 1], D.sf[3 * f + 2]};
+    if (pv == v[1] || pv == v[2] || pv == v[3]) return false;
+    return pair_dist_lb(D, 0, v) < D.dhat;
+}
+template <class R>
+__device__ __forceinline__ bool ee_needed(const Dev<R>& D, int i, int j) {
+    const int v[4] = {D.se[2 * i], D.se[2 * i + 1], D.se[2 * j], D.se[2 * j + 1]};
+    if (v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3]) return false;
+    return pair_dist_lb(D, 1, v) < D.dhat;
 }
 
 template <class R>
@@ -367,28 +398,50 @@ __device__ void ee_try(const Dev<R>& D, const double* x, const ContactBuf& C, in
 
 // ------------------------------------------------------------ proximity
 
-template <class R>
-__global__ void k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
-    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int qi = (int)(gid / kSplitProx), sub = (int)(gid % kSplitProx);
-    if (qi >= D.nsv) return;
-    const int pv = D.sv[qi];
-    float lo[3], hi[3];
-    prim_box(D, &pv, 1, 0.f, lo, hi);
-    grid_query<kSplitProx>(D, lo, hi, D.nsf, sub, [&](int f) { pt_try(D, x, C, pv, f); });
+// Grid queries. kFused = false (the default pass): a query screens every
+// pair it finds in FP32 and appends the ones that need the FP64 test to the
+// scratch list gpair, which the list kernels finish one thread per pair; a
+// full list sets gpair_n[1]. The query kernel then holds no FP64 code, so its
+// chains of dependent grid loads run at full occupancy. kFused = true: the
+// query runs the FP64 test itself, grid-stride, and only when the list
+// overflowed (the list kernels then skip it), so every pair is handled once.
+template <class R, bool kFused>
+__global__ void __launch_bounds__(kT, kFused ? 1 : 8) k_prox_pt(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
+    if (kFused && !D.gpair_n[1]) return;
+    const long long n = (long long)D.nsv * kSplitProx;
+    for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < n;
+         gid += (long long)gridDim.x * blockDim.x) {
+        const int qi = (int)(gid / kSplitProx), sub = (int)(gid % kSplitProx);
+        const int pv = D.sv[qi];
+        float lo[3], hi[3];
+        prim_box(D, &pv, 1, 0.f, lo, hi);
+        grid_query<kSplitProx>(D, lo, hi, D.nsf, sub, [&](int f) {
+            if constexpr (kFused)
+                pt_try(D, x, C, pv, f);
+            else if (pt_needed(D, pv, f) && !append_ok(D.gpair, D.gpair_n, D.gpair_cap, pv, f))
+                D.gpair_n[1] = 1;
+        });
+    }
 }
 
-template <class R>
-__global__ void k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int* gin) {
-    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int i = (int)(gid / kSplitProx), sub = (int)(gid % kSplitProx);
-    if (i >= D.nse) return;
-    const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
-    float lo[3], hi[3];
-    prim_box(D, vid, 2, 0.f, lo, hi);
-    grid_query<kSplitProx>(D, lo, hi, D.nse, sub, [&](int j) {
-        if (j > i) ee_try(D, x, C, i, j);
-    });
+template <class R, bool kFused>
+__global__ void __launch_bounds__(kT, kFused ? 1 : 8) k_prox_ee(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
+    if (kFused && !D.gpair_n[1]) return;
+    const long long n = (long long)D.nse * kSplitProx;
+    for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < n;
+         gid += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(gid / kSplitProx), sub = (int)(gid % kSplitProx);
+        const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+        float lo[3], hi[3];
+        prim_box(D, vid, 2, 0.f, lo, hi);
+        grid_query<kSplitProx>(D, lo, hi, D.nse, sub, [&](int j) {
+            if (j <= i) return;
+            if constexpr (kFused)
+                ee_try(D, x, C, i, j);
+            else if (ee_needed(D, i, j) && !append_ok(D.gpair, D.gpair_n, D.gpair_cap, i, j))
+                D.gpair_n[1] = 1;
+        });
+    }
 }
 
 template <class R>
@@ -474,53 +527,72 @@ __device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const do
     return a;
 }
 
+// FP32 screen of a CCD pair. A pair whose distance exceeds any relative
+// displacement the step can make, with every vertex scaled anywhere in
+// [0, 1], keeps alpha = 1 and can never be violated by mixed per-subdomain
+// steps: 0, nothing to do (FP32 lower bound on d0, sum of the two
+// primitives' largest |p|).
+//
+// Otherwise its own step bound alpha_l = (1 - s) d0 / l uses l, the largest
+// relative displacement between a vertex of one primitive and one of the
+// other: where FP32 bounds already give d0 (1 - s) > l, the FP64 walk would
+// return exactly 1 (CUBICSAFE starts at alpha_l >= 1), so it is not run (1).
+// A pair inside one subdomain and one body moves with one common scale t in
+// [0, 1] under every step the line search tries (per subdomain, per body,
+// uniform), so that bound alone also keeps it safe and it needs no
+// verification (0). 2: the FP64 walk is needed.
+template <class R>
+__device__ int ccd_screen(const Dev<R>& D, int kind, const int v[4], bool one_scale) {
+    float P[4][3];
+    float pa = 0.f, pb = 0.f;
+    for (int j = 0; j < 4; ++j) {
+        const R* q = D.p + 3 * v[j];
+        P[j][0] = (float)q[0];
+        P[j][1] = (float)q[1];
+        P[j][2] = (float)q[2];
+        float m = sqrtf(P[j][0] * P[j][0] + P[j][1] * P[j][1] + P[j][2] * P[j][2]);
+        if ((kind == 0 && j == 0) || (kind == 1 && j < 2))
+            pa = fmaxf(pa, m);
+        else
+            pb = fmaxf(pb, m);
+    }
+    const float lim = pair_dist_lb(D, kind, v) * (1.f - (float)D.ccd_shrink);
+    if (lim > 1.001f * (pa + pb)) return 0;
+    // primitive A: vertex 0 (PT) or 0, 1 (EE); B: the rest
+    float lr = 0.f;
+    for (int i = 0; i < (kind == 0 ? 1 : 2); ++i)
+        for (int j = (kind == 0 ? 1 : 2); j < 4; ++j) {
+            const float dx = P[i][0] - P[j][0], dy = P[i][1] - P[j][1], dz = P[i][2] - P[j][2];
+            lr = fmaxf(lr, sqrtf(dx * dx + dy * dy + dz * dz));
+        }
+    // FP32 rounding of p and of the differences: a margin of 1e-3 of the
+    // absolute displacements covers it many times over
+    const bool whole_step = lim > 1.001f * lr + 1e-3f * (pa + pb);
+    if (whole_step) return one_scale ? 0 : 1;
+    return 2;
+}
+
+template <class R>
+__device__ __forceinline__ bool one_scale_of(const Dev<R>& D, const int v[4]) {
+    const int g0 = D.grp0[v[0]], b0 = D.body[v[0]];
+    return D.grp0[v[1]] == g0 && D.grp0[v[2]] == g0 && D.grp0[v[3]] == g0 && D.body[v[1]] == b0 &&
+           D.body[v[2]] == b0 && D.body[v[3]] == b0;
+}
+
+// true when ccd_pair would do more than the FP32 screen
+template <class R>
+__device__ __forceinline__ bool ccd_needed(const Dev<R>& D, int kind, const int v[4]) {
+    return ccd_screen(D, kind, v, one_scale_of(D, v)) != 0;
+}
+
 template <class R>
 __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
-    // A pair whose distance exceeds any relative displacement the step can
-    // make, with every vertex scaled anywhere in [0, 1], keeps alpha = 1 and
-    // can never be violated by mixed per-subdomain steps: it is skipped
-    // (FP32 lower bound on d0, sum of the two primitives' largest |p|).
-    //
-    // Otherwise its own step bound alpha_l = (1 - s) d0 / l uses l, the
-    // largest relative displacement between a vertex of one primitive and one
-    // of the other: where FP32 bounds already give d0 (1 - s) > l, the FP64
-    // walk would return exactly 1 (CUBICSAFE starts at alpha_l >= 1), so it is
-    // not run. A pair inside one subdomain and one body moves with one common
-    // scale t in [0, 1] under every step the line search tries (per subdomain,
-    // per body, uniform), so that bound alone also keeps it safe and it needs
-    // no verification.
     const int g0 = D.grp0[v[0]], g1 = D.grp0[v[1]], g2 = D.grp0[v[2]], g3 = D.grp0[v[3]];
     const int b0 = D.body[v[0]], b1 = D.body[v[1]], b2 = D.body[v[2]], b3 = D.body[v[3]];
     const bool one_scale = g1 == g0 && g2 == g0 && g3 == g0 && b1 == b0 && b2 == b0 && b3 == b0;
-    bool whole_step = false;
-    {
-        float P[4][3];
-        float pa = 0.f, pb = 0.f;
-        for (int j = 0; j < 4; ++j) {
-            const R* q = D.p + 3 * v[j];
-            P[j][0] = (float)q[0];
-            P[j][1] = (float)q[1];
-            P[j][2] = (float)q[2];
-            float m = sqrtf(P[j][0] * P[j][0] + P[j][1] * P[j][1] + P[j][2] * P[j][2]);
-            if ((kind == 0 && j == 0) || (kind == 1 && j < 2))
-                pa = fmaxf(pa, m);
-            else
-                pb = fmaxf(pb, m);
-        }
-        const float lim = pair_dist_lb(D, kind, v) * (1.f - (float)D.ccd_shrink);
-        if (lim > 1.001f * (pa + pb)) return;
-        // primitive A: vertex 0 (PT) or 0, 1 (EE); B: the rest
-        float lr = 0.f;
-        for (int i = 0; i < (kind == 0 ? 1 : 2); ++i)
-            for (int j = (kind == 0 ? 1 : 2); j < 4; ++j) {
-                const float dx = P[i][0] - P[j][0], dy = P[i][1] - P[j][1], dz = P[i][2] - P[j][2];
-                lr = fmaxf(lr, sqrtf(dx * dx + dy * dy + dz * dz));
-            }
-        // FP32 rounding of p and of the differences: a margin of 1e-3 of the
-        // absolute displacements covers it many times over
-        whole_step = lim > 1.001f * lr + 1e-3f * (pa + pb);
-        if (one_scale && whole_step) return;
-    }
+    const int scr = ccd_screen(D, kind, v, one_scale);
+    if (scr == 0) return;
+    const bool whole_step = scr == 1;
     const double a = whole_step ? 1.0 : pair_alpha(D, kind, v, D.x, D.p, nullptr);
     if (a < 1.0) {
         atomicMinPos(&D.alpha[g0], a);
@@ -544,35 +616,47 @@ __device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
     }
 }
 
-template <class R>
-__global__ void k_ccd_pt(Dev<R> D, const int* gin) {
-    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int qi = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
-    if (qi >= D.nsv) return;
-    const int pv = D.sv[qi];
-    float lo[3], hi[3];
-    prim_box(D, &pv, 1, 0.f, lo, hi);
-    grid_query<kSplitSwept>(D, lo, hi, D.nsf, sub, [&](int f) {
-        int v[4] = {pv, D.sf[3 * f], D.sf[3 * f + 1], D.sf[3 * f + 2]};
-        if (pv == v[1] || pv == v[2] || pv == v[3]) return;
-        ccd_pair(D, 0, v);
-    });
+template <class R, bool kFused>
+__global__ void __launch_bounds__(kT, kFused ? 1 : 7) k_ccd_pt(Dev<R> D) {
+    if (kFused && !D.gpair_n[1]) return;
+    const long long n = (long long)D.nsv * kSplitSwept;
+    for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < n;
+         gid += (long long)gridDim.x * blockDim.x) {
+        const int qi = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
+        const int pv = D.sv[qi];
+        float lo[3], hi[3];
+        prim_box(D, &pv, 1, 0.f, lo, hi);
+        grid_query<kSplitSwept>(D, lo, hi, D.nsf, sub, [&](int f) {
+            int v[4] = {pv, D.sf[3 * f], D.sf[3 * f + 1], D.sf[3 * f + 2]};
+            if (pv == v[1] || pv == v[2] || pv == v[3]) return;
+            if constexpr (kFused)
+                ccd_pair(D, 0, v);
+            else if (ccd_needed(D, 0, v) && !append_ok(D.gpair, D.gpair_n, D.gpair_cap, pv, f))
+                D.gpair_n[1] = 1;
+        });
+    }
 }
 
-template <class R>
-__global__ void k_ccd_ee(Dev<R> D, const int* gin) {
-    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const int i = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
-    if (i >= D.nse) return;
-    const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
-    float lo[3], hi[3];
-    prim_box(D, vid, 2, 0.f, lo, hi);
-    grid_query<kSplitSwept>(D, lo, hi, D.nse, sub, [&](int j) {
-        if (j <= i) return;
-        int v[4] = {vid[0], vid[1], D.se[2 * j], D.se[2 * j + 1]};
-        if (v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3]) return;
-        ccd_pair(D, 1, v);
-    });
+template <class R, bool kFused>
+__global__ void __launch_bounds__(kT, kFused ? 1 : 7) k_ccd_ee(Dev<R> D) {
+    if (kFused && !D.gpair_n[1]) return;
+    const long long n = (long long)D.nse * kSplitSwept;
+    for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < n;
+         gid += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(gid / kSplitSwept), sub = (int)(gid % kSplitSwept);
+        const int vid[2] = {D.se[2 * i], D.se[2 * i + 1]};
+        float lo[3], hi[3];
+        prim_box(D, vid, 2, 0.f, lo, hi);
+        grid_query<kSplitSwept>(D, lo, hi, D.nse, sub, [&](int j) {
+            if (j <= i) return;
+            int v[4] = {vid[0], vid[1], D.se[2 * j], D.se[2 * j + 1]};
+            if (v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3]) return;
+            if constexpr (kFused)
+                ccd_pair(D, 1, v);
+            else if (ccd_needed(D, 1, v) && !append_ok(D.gpair, D.gpair_n, D.gpair_cap, i, j))
+                D.gpair_n[1] = 1;
+        });
+    }
 }
 
 template <class R>
@@ -656,29 +740,39 @@ __global__ void k_set_cell_cand(Dev<R> D, double infl) {
     *D.cellinv = (float)(1.0 / cs);
 }
 
+// The list kernels take the cached candidate lists, or the pairs a grid
+// query screened (one thread per pair either way).
 template <class R>
-__global__ void k_prox_pt_list(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
-    int n = min(D.cand_n[0], D.cand_cap);
+__global__ void k_prox_pt_list(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int2* list, const int* cnt,
+                               int cap,
+                              const int* skip) {
+    if (skip && *skip) return;  // the fused query handles an overflowed list
+    int n = min(*cnt, cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int2 q = D.cand_pt[k];
+        int2 q = list[k];
         pt_try(D, x, C, q.x, q.y);
     }
 }
 
 template <class R>
-__global__ void k_prox_ee_list(Dev<R> D, const double* __restrict__ x, ContactBuf C) {
-    int n = min(D.cand_n[1], D.cand_cap);
+__global__ void k_prox_ee_list(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int2* list, const int* cnt,
+                               int cap,
+                              const int* skip) {
+    if (skip && *skip) return;  // the fused query handles an overflowed list
+    int n = min(*cnt, cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int2 q = D.cand_ee[k];
+        int2 q = list[k];
         ee_try(D, x, C, q.x, q.y);
     }
 }
 
 template <class R>
-__global__ void k_ccd_pt_list(Dev<R> D) {
-    int n = min(D.cand_n[0], D.cand_cap);
+__global__ void k_ccd_pt_list(Dev<R> D, const int2* list, const int* cnt, int cap,
+                              const int* skip) {
+    if (skip && *skip) return;  // the fused query handles an overflowed list
+    int n = min(*cnt, cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int2 q = D.cand_pt[k];
+        int2 q = list[k];
         int v[4] = {q.x, D.sf[3 * q.y], D.sf[3 * q.y + 1], D.sf[3 * q.y + 2]};
         float lo[3], hi[3], tlo[3], thi[3];
         prim_box(D, v, 1, 0.f, lo, hi);
@@ -688,10 +782,12 @@ __global__ void k_ccd_pt_list(Dev<R> D) {
 }
 
 template <class R>
-__global__ void k_ccd_ee_list(Dev<R> D) {
-    int n = min(D.cand_n[1], D.cand_cap);
+__global__ void k_ccd_ee_list(Dev<R> D, const int2* list, const int* cnt, int cap,
+                              const int* skip) {
+    if (skip && *skip) return;  // the fused query handles an overflowed list
+    int n = min(*cnt, cap);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int2 q = D.cand_ee[k];
+        int2 q = list[k];
         int v[4] = {D.se[2 * q.x], D.se[2 * q.x + 1], D.se[2 * q.y], D.se[2 * q.y + 1]};
         float lo[3], hi[3], blo[3], bhi[3];
         prim_box(D, v, 2, 0.f, lo, hi);
@@ -954,9 +1050,19 @@ void launch_detect(const Dev<R>& D, const double* x, const ContactBuf& C, cudaSt
     int* gin = D.gin;
     const float dh = round_up_f(D.dhat);
     build_grid<R>(D, D.sf, 3, D.nsf, dh, gin, false, st);
-    if (D.nsv) KL(k_prox_pt<R><<<nblk((long long)D.nsv * kSplitProx), kT, 0, st>>>(D, x, C));
+    cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+    if (D.nsv) {
+        KL(k_prox_pt<R, false><<<nblk((long long)D.nsv * kSplitProx), kT, 0, st>>>(D, x, C));
+        KL(k_prox_pt_list<R><<<1184, kT, 0, st>>>(D, x, C, D.gpair, D.gpair_n, D.gpair_cap, D.gpair_n + 1));
+        KL(k_prox_pt<R, true><<<1184, kT, 0, st>>>(D, x, C));
+    }
     build_grid<R>(D, D.se, 2, D.nse, dh, gin, false, st);
-    if (D.nse) KL(k_prox_ee<R><<<nblk((long long)D.nse * kSplitProx), kT, 0, st>>>(D, x, C, gin));
+    cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+    if (D.nse) {
+        KL(k_prox_ee<R, false><<<nblk((long long)D.nse * kSplitProx), kT, 0, st>>>(D, x, C));
+        KL(k_prox_ee_list<R><<<1184, kT, 0, st>>>(D, x, C, D.gpair, D.gpair_n, D.gpair_cap, D.gpair_n + 1));
+        KL(k_prox_ee<R, true><<<1184, kT, 0, st>>>(D, x, C));
+    }
     if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
 }
 
@@ -969,9 +1075,19 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
     int* gin = D.gin;
     build_grid<R>(D, D.sf, 3, D.nsf, 0.f, gin, true, st);
-    if (D.nsv) KL(k_ccd_pt<R><<<nblk((long long)D.nsv * kSplitSwept), kT, 0, st>>>(D, gin));
+    cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+    if (D.nsv) {
+        KL(k_ccd_pt<R, false><<<nblk((long long)D.nsv * kSplitSwept), kT, 0, st>>>(D));
+        KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D, D.gpair, D.gpair_n, D.gpair_cap, D.gpair_n + 1));
+        KL(k_ccd_pt<R, true><<<1184, kT, 0, st>>>(D));
+    }
     build_grid<R>(D, D.se, 2, D.nse, 0.f, gin, true, st);
-    if (D.nse) KL(k_ccd_ee<R><<<nblk((long long)D.nse * kSplitSwept), kT, 0, st>>>(D, gin));
+    cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+    if (D.nse) {
+        KL(k_ccd_ee<R, false><<<nblk((long long)D.nse * kSplitSwept), kT, 0, st>>>(D));
+        KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D, D.gpair, D.gpair_n, D.gpair_cap, D.gpair_n + 1));
+        KL(k_ccd_ee<R, true><<<1184, kT, 0, st>>>(D));
+    }
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     Scalars* S = D.S;
     Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
@@ -1008,8 +1124,8 @@ template <class R>
 void launch_detect_list(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
     KL(k_reset_detect<R><<<1, 1, 0, st>>>(D, C));
     if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, (const R*)nullptr));
-    KL(k_prox_pt_list<R><<<1184, kT, 0, st>>>(D, x, C));
-    KL(k_prox_ee_list<R><<<1184, kT, 0, st>>>(D, x, C));
+    KL(k_prox_pt_list<R><<<1184, kT, 0, st>>>(D, x, C, D.cand_pt, &D.cand_n[0], D.cand_cap, nullptr));
+    KL(k_prox_ee_list<R><<<1184, kT, 0, st>>>(D, x, C, D.cand_ee, &D.cand_n[1], D.cand_cap, nullptr));
     if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
 }
 
@@ -1021,8 +1137,8 @@ void launch_ccd_list(const Dev<R>& D, cudaStream_t st, int part) {
         KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
         KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
         if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
-        KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D));
-        KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D));
+        KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D, D.cand_pt, &D.cand_n[0], D.cand_cap, nullptr));
+        KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D, D.cand_ee, &D.cand_n[1], D.cand_cap, nullptr));
         if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     }
     if (part != 1) {  // verification: one cooperative launch, ordered across scenes

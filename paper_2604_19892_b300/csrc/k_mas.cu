@@ -38,6 +38,34 @@ __host__ __device__ __forceinline__ int pk(int i, int j) {  // packed upper inde
     return i * 9 - (i * (i - 1)) / 2 + (j - i);
 }
 
+// FP64 -> FP32, rounded to nearest (ties to even), on the integer pipes: the
+// IEEE 754 binary64 fields are re-packed as binary32 (exponent bias 1023 ->
+// 127, the 52-bit fraction rounded to 23 bits; a carry out of the fraction
+// raises the exponent, as the format intends). Handles zeros and magnitudes
+// within 2^+-100 and returns true; otherwise returns false and leaves f
+// unset. B300's FP64 pipe (conversions included) runs at a small fraction
+// of its integer rate.
+__device__ __forceinline__ bool f64_to_f32_rn(double x, float& f) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const unsigned ex = (unsigned)(bits >> 52) & 0x7FFu;
+    if ((bits << 1) == 0ULL) {
+        f = 0.f;
+        return true;
+    }
+    if (ex < 1023u - 100u || ex > 1023u + 100u) return false;
+    const unsigned long long frac = bits & ((1ULL << 52) - 1ULL);
+    unsigned m = (unsigned)(frac >> 29);
+    const unsigned rest = (unsigned)frac & ((1u << 29) - 1u);
+    const unsigned half = 1u << 28;
+    m += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
+    f = __uint_as_float(((unsigned)(bits >> 32) & 0x80000000u) + ((ex - 1023u + 127u) << 23) + m);
+    return true;
+}
+__device__ __forceinline__ float to_f32(double x) {
+    float f;
+    return f64_to_f32_rn(x, f) ? f : (float)x;
+}
+
 template <class R>
 __device__ __forceinline__ void load_B(const Dev<R>& D, int t, R B[3][3]) {
     const R* base = D.tetB + (size_t)(t / kPack) * 9 * kPack + (t % kPack);
@@ -127,14 +155,28 @@ __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __re
     R B[3][3];
     load_B(D, t, B);
     R F[3][3];
+    if constexpr (sizeof(R) == 4) {
+        // edge vectors exact in FP64, rounded to FP32; F in FP32 like the rest
+        // of this Hessian
+        float Ds[3][3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
+        for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double sacc = 0.0;
-            for (int j = 0; j < 3; ++j) sacc += (x[3 * vid[j + 1] + r] - x[3 * vid[0] + r]) * (double)B[j][c];
-            F[r][c] = (R)sacc;
-        }
+            for (int j = 0; j < 3; ++j) Ds[r][j] = to_f32(x[3 * vid[j + 1] + r] - x[3 * vid[0] + r]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) F[r][c] = Ds[r][0] * B[0][c] + Ds[r][1] * B[1][c] + Ds[r][2] * B[2][c];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double sacc = 0.0;
+                for (int j = 0; j < 3; ++j) sacc += (x[3 * vid[j + 1] + r] - x[3 * vid[0] + r]) * (double)B[j][c];
+                F[r][c] = (R)sacc;
+            }
+    }
     const R J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
                 F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
     // V, s^2 from F^T F, sorted descending, V a rotation
@@ -208,7 +250,8 @@ __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __re
         U[r][1] = u1[r];
         U[r][2] = u2[r];
     }
-    const R mu = (R)D.tet_mu[t], lam = (R)D.tet_lam[t];
+    const R mu = sizeof(R) == 4 ? (R)to_f32(D.tet_mu[t]) : (R)D.tet_mu[t];
+    const R lam = sizeof(R) == 4 ? (R)to_f32(D.tet_lam[t]) : (R)D.tet_lam[t];
     const R cJ = lam * (J - (R)1) - mu;
     R acc[kH];
 #pragma unroll
@@ -571,28 +614,14 @@ __device__ __forceinline__ void lds6(const T* p, T v[kTile]) {
         v[2 * i + 1] = w.y;
     }
 }
-// s_r x s_c as FP32 with x FP64. x is rounded to FP32 (nearest, ties to
-// even) on the integer pipes: the IEEE 754 binary64 fields are re-packed as
-// binary32 (exponent bias 1023 -> 127, the 52-bit fraction rounded to 23
-// bits; a carry out of the fraction raises the exponent, as the format
-// intends), then scaled in FP32. Zeros and magnitudes within 2^+-100 take this
-// path; anything else (no assembled Hessian entry in practice) is scaled in
-// FP64 before rounding, so an entry beyond the FP32 range still maps to its
-// finite scaled value. B300's FP64 pipe is a small fraction of its integer
-// rate, and 9,216 FP64 scalings per block were the FP32 inversion's largest
-// single cost.
+// s_r x s_c as FP32 with x FP64: x rounded by f64_to_f32_rn, then scaled in
+// FP32; x outside 2^+-100 is scaled in FP64 before rounding, so an entry
+// beyond the FP32 range still maps to its finite scaled value. 9,216 FP64
+// scalings per block were the FP32 inversion's largest single cost.
 __device__ __forceinline__ float scaled_f32(double x, float sr, float sc) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const unsigned ex = (unsigned)(bits >> 52) & 0x7FFu;
-    if ((bits << 1) == 0ULL) return 0.f;
-    if (ex < 1023u - 100u || ex > 1023u + 100u) return (float)(x * (double)sr * (double)sc);
-    const unsigned long long frac = bits & ((1ULL << 52) - 1ULL);
-    unsigned m = (unsigned)(frac >> 29);
-    const unsigned rest = (unsigned)frac & ((1u << 29) - 1u);
-    const unsigned half = 1u << 28;
-    m += (rest > half || (rest == half && (m & 1u))) ? 1u : 0u;
-    const unsigned fb = ((unsigned)(bits >> 32) & 0x80000000u) + ((ex - 1023u + 127u) << 23) + m;
-    return __uint_as_float(fb) * (sr * sc);
+    float f;
+    if (f64_to_f32_rn(x, f)) return f * (sr * sc);
+    return (float)(x * (double)sr * (double)sc);
 }
 __device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }

@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("eps_sing", C.c_double), ("eps_abs", C.c_double), ("K", C.c_int), ("iter_max", C.c_int),
                 ("levels_max", C.c_int), ("ls_max", C.c_int), ("precision", C.c_int),
                 ("contact_capacity", C.c_int), ("broad_phase", C.c_int), ("mas_mode", C.c_int),
-                ("ccd_mode", C.c_int), ("graphs", C.c_int), ("fp32_pivot_floor", C.c_double)]
+                ("ccd_mode", C.c_int), ("graphs", C.c_int), ("fp32_pivot_floor", C.c_double),
+                ("grid_pair_capacity", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -190,7 +191,7 @@ def default_params(sc_params: dict, precision: int = IPC_PREC_FP64) -> Params:
     lib.ipc_default_params(C.byref(p))
     for k in ("h", "dhat", "kappa", "tol", "delta", "eps_rot_deg", "ccd_shrink", "eps_sing", "eps_abs", "K",
               "iter_max", "levels_max", "ls_max", "broad_phase", "mas_mode", "ccd_mode", "graphs",
-              "fp32_pivot_floor"):
+              "fp32_pivot_floor", "grid_pair_capacity"):
         if k in sc_params:
             setattr(p, k, type(getattr(p, k))(sc_params[k]))
     p.precision = precision

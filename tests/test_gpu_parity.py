@@ -89,11 +89,18 @@ def test_energy_gradient_parity(lib, name, precision, gtol, etol):
     assert err <= gtol, err
 
 
-@pytest.mark.parametrize("bp", [1, 2])  # hashed grid, cached candidate lists
+# hashed grid (its screened pairs finished by the list kernels); the grid
+# with a one-pair scratch list, so every pass overflows to the fused query;
+# cached candidate lists
+BROAD_PHASES = [dict(broad_phase=1), dict(broad_phase=1, grid_pair_capacity=1), dict(broad_phase=2)]
+BP_IDS = ["grid", "grid-overflow", "lists"]
+
+
+@pytest.mark.parametrize("bp", BROAD_PHASES, ids=BP_IDS)
 @pytest.mark.parametrize("name", list(SCENES))
 def test_contact_set_parity(lib, name, bp):
     sc = SCENES[name]
-    g, o = _pair(lib, sc, broad_phase=bp)
+    g, o = _pair(lib, sc, **bp)
     x = contact_state(sc) + 2e-6 * RNG.normal(size=sc["x0"].shape)
     cg, co = g.contacts(x), o.contacts(x)
     kg = {(int(t), int(a), int(b)): i for i, (t, (a, b)) in enumerate(zip(cg["type"], cg["ids"]))}
@@ -195,11 +202,11 @@ def test_forms_fp32(lib, name):
         np.testing.assert_allclose(fg, fo, rtol=2e-5)
 
 
-@pytest.mark.parametrize("bp", [1, 2])  # hashed grid, cached candidate lists
+@pytest.mark.parametrize("bp", BROAD_PHASES, ids=BP_IDS)
 @pytest.mark.parametrize("name", list(SCENES))
 def test_ccd_parity(lib, name, bp):
     sc = SCENES[name]
-    g, o = _pair(lib, sc, broad_phase=bp)
+    g, o = _pair(lib, sc, **bp)
     x = contact_state(sc, 3.0)
     nv = x.shape[0] // 2
     for trial in range(3):
