@@ -447,7 +447,7 @@ int setup_dev(ipc_scene* s) {
     D.gcount = A.arr<int>(D.nbuckets + 1);
     D.gstart = A.arr<int>(D.nbuckets + 1);
     D.gfill = A.arr<int>(D.nbuckets);
-    D.gentry = A.arr<int>(D.gcap);
+    D.gbox = A.arr<float4>(2 * (size_t)D.gcap);
     D.gcell = A.arr<unsigned long long>(D.gcap);
     D.gtotal = A.arr<int>(1);
     D.glarge = A.arr<int>(nprim);

@@ -165,7 +165,7 @@ struct Dev {
     int* gcount;                           // bucket counts (nbuckets + 1)
     int* gstart;                           // bucket starts (nbuckets + 1)
     int* gfill;                            // fill cursor per bucket
-    int* gentry;                           // primitive id per entry
+    float4* gbox;                          // per entry: FP32 box lo (.w: primitive id bits), hi
     unsigned long long* gcell;             // packed cell of each entry
     int* gtotal;                           // scalar: entries used
     int* glarge;                           // primitives too large for the grid

@@ -187,8 +187,16 @@ __device__ __forceinline__ void grid_query(const Dev<R>& D, const float lo[3], c
                 const int bk = bucket_of(cc, D.nbuckets);
                 for (int e = D.gstart[bk] + sub; e < D.gstart[bk + 1]; e += S) {
                     if (D.gcell[e] != cc) continue;
-                    const int j = D.gentry[e];
-                    load_box(D, j, blo, bhi);
+                    // the entry carries its box: consecutive entries are
+                    // consecutive in memory, no gather through the id
+                    const float4 ea = D.gbox[2 * (size_t)e], eb = D.gbox[2 * (size_t)e + 1];
+                    const int j = __float_as_int(ea.w);
+                    blo[0] = ea.x;
+                    blo[1] = ea.y;
+                    blo[2] = ea.z;
+                    bhi[0] = eb.x;
+                    bhi[1] = eb.y;
+                    bhi[2] = eb.z;
                     if (!overlap(lo, hi, blo, bhi)) continue;
                     if (cellc(fmaxf(lo[0], blo[0]), inv) != a || cellc(fmaxf(lo[1], blo[1]), inv) != bb ||
                         cellc(fmaxf(lo[2], blo[2]), inv) != c)
@@ -263,7 +271,8 @@ __global__ void k_grid_fill(Dev<R> D, int nprim, const int* gin) {
                 unsigned long long cc = pack_cell(a, b, c);
                 int bk = bucket_of(cc, D.nbuckets);
                 int pos = D.gstart[bk] + atomicAdd(&D.gfill[bk], 1);
-                D.gentry[pos] = i;
+                D.gbox[2 * (size_t)pos] = make_float4(lo[0], lo[1], lo[2], __int_as_float(i));
+                D.gbox[2 * (size_t)pos + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
                 D.gcell[pos] = cc;
             }
 }
