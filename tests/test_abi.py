@@ -58,3 +58,21 @@ def _load_missing(ipc, path):
         ipc.load(path)
     finally:
         ipc._lib = saved
+
+
+def test_params_mirror_matches_the_header():
+    """ipc_default_params (host code only) fills the binding's ctypes mirror of
+    ipc_params: every field reads back its documented default, the last ones
+    included, so the two layouts agree (a field added on one side only would
+    shift the fields after it)."""
+    from paper_2604_19892_b300 import build, ipc
+    lib = ipc.load(build.build())
+    p = ipc.Params()
+    ctypes.memset(ctypes.byref(p), 0xAB, ctypes.sizeof(p))
+    lib.ipc_default_params(ctypes.byref(p))
+    assert (p.eps_rot_deg, p.ccd_shrink, p.eps_sing) == (25.0, 0.1, 1e-12)
+    assert (p.K, p.iter_max, p.levels_max, p.ls_max) == (8, 10000, 6, 20)
+    assert (p.precision, p.contact_capacity, p.broad_phase) == (ipc.IPC_PREC_FP64, 0, 0)
+    assert (p.mas_mode, p.ccd_mode, p.graphs) == (0, 0, 1)
+    assert p.fp32_pivot_floor == 1e-6
+    assert p.grid_pair_capacity == 0
