@@ -628,6 +628,12 @@ __device__ __forceinline__ void lds6(const T* p, T v[kTile]) {
 __device__ __forceinline__ float scaled_f32(double x, float sr, float sc) {
     float f;
     if (f64_to_f32_rn(x, f)) return f * (sr * sc);
+    // |x| < 2^-100 with s_r s_c <= 2^70: the scaled entry is below 2^-30,
+    // under FP32 resolution beside the unit diagonal, so it is 0 (near the
+    // rest state such residues of cancelling FP32 Hessian terms are common
+    // and would each take the FP64 path)
+    const unsigned ex = (unsigned)((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FFu;
+    if (ex < 1023u - 100u && sr * sc <= 0x1p70f) return 0.f;
     return (float)(x * (double)sr * (double)sc);
 }
 __device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
