@@ -1295,20 +1295,6 @@ __global__ void k_restrict_level(Dev<R> D, int l, const R* __restrict__ src) {
     }
 }
 
-// One CTA of 96 threads per block of any level.  Level 0 applies B_d to
-// [g_d, U_d] and the Woodbury correction; coarse levels apply M_l^-1 to the
-// restricted residual.
-__device__ __forceinline__ void unpack16(const float4& v, float e[4]) {
-    e[0] = v.x;
-    e[1] = v.y;
-    e[2] = v.z;
-    e[3] = v.w;
-}
-__device__ __forceinline__ void unpack16(const double2& v, double e[2]) {
-    e[0] = v.x;
-    e[1] = v.y;
-}
-
 // Block apply without Woodbury updates (restart iterations, coarse levels):
 // y_b = B_b r_b, one CTA of 96 threads per block. The whole 96 x 96 block
 // (36.9 KB in FP32) streams into shared memory as one bulk copy
