@@ -372,7 +372,8 @@ int ipc_server_submit(ipc_server* srv, ipc_scene* scene, int n_steps, unsigned l
 int ipc_server_poll(ipc_server* srv, unsigned long long ticket, ipc_step_stats* stats, double* latency_ms);
 
 /* As ipc_server_poll, but blocks until the request finishes or timeout_ms
- * passes (IPC_PENDING then). */
+ * passes (IPC_PENDING then). timeout_ms <= 0 or NaN does not block; values
+ * above 1e12 (about 30 years) are capped there. */
 int ipc_server_wait(ipc_server* srv, unsigned long long ticket, double timeout_ms, ipc_step_stats* stats,
                     double* latency_ms);
 

@@ -160,8 +160,11 @@ int ipc_server_poll(ipc_server* s, unsigned long long ticket, ipc_step_stats* st
 int ipc_server_wait(ipc_server* s, unsigned long long ticket, double timeout_ms, ipc_step_stats* stats,
                     double* latency_ms) {
     if (!s) return IPC_ERR_INVALID;
+    // NaN or <= 0: no wait; the cap keeps the conversion to microseconds
+    // defined (1e12 ms is about 30 years)
+    const double ms = timeout_ms > 0.0 ? (timeout_ms < 1e12 ? timeout_ms : 1e12) : 0.0;
     std::unique_lock<std::mutex> lk(s->mu);
-    const auto until = Clock::now() + std::chrono::microseconds((long long)(timeout_ms * 1e3));
+    const auto until = Clock::now() + std::chrono::microseconds((long long)(ms * 1e3));
     s->done_cv.wait_until(lk, until, [&] {
         auto it = s->results.find(ticket);
         return it == s->results.end() || it->second.done;
