@@ -101,6 +101,11 @@ def _lib_handle():
             "o_solve2x2": (None, [C.c_double] * 7 + [_D, _D]),
             "o_step": (C.c_int, [C.c_void_p, _D, _D, C.POINTER(OStepStats)]),
             "o_trace": (C.c_int, [C.c_void_p, C.POINTER(OIterRecord), C.c_int]),
+            "o_updates": (C.c_int, [C.c_void_p, C.c_int, _D, _I, _D]),
+            "o_topk": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _I]),
+            "o_chol_inverse": (C.c_int, [C.c_int, _D, _D]),
+            "o_chol_floors": (C.c_longlong, [C.c_int]),
+            "o_energy_tolerance": (C.c_double, [C.c_void_p, C.c_double]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -274,6 +279,24 @@ class Scene:
         stats = {f: getattr(st, f) for f, _ in OStepStats._fields_}
         return x, v, stats
 
+    def updates(self):
+        """Classified updates of the last precond_apply / hess_forms with
+        x_curr: dS, key (type, ida, idb) and u (12 values) of each."""
+        n = self.lib.o_updates(self.h, 0, None, None, None)
+        dS = np.zeros(n)
+        key = np.zeros((n, 3), np.int32)
+        u = np.zeros((n, 12))
+        self.lib.o_updates(self.h, n, dS.ctypes.data_as(_D), key.ctypes.data_as(_I), u.ctypes.data_as(_D))
+        return {"dS": dS, "key": key, "u": u}
+
+    def topk(self, group):
+        idx = np.zeros(64, np.int32)
+        n = self.lib.o_topk(self.h, int(group), 64, idx.ctypes.data_as(_I))
+        return idx[:min(n, 64)].copy()
+
+    def energy_tolerance(self, E):
+        return self.lib.o_energy_tolerance(self.h, float(E))
+
     def trace(self):
         n = self.lib.o_trace(self.h, None, 0)
         rec = (OIterRecord * max(n, 1))()
@@ -385,3 +408,17 @@ def solve2x2(A11, A12, A22, b1, b2, eps_sing=1e-12, eps_abs=1e-300):
     nu = C.c_double()
     _lib_handle().o_solve2x2(A11, A12, A22, b1, b2, eps_sing, eps_abs, C.byref(mu), C.byref(nu))
     return mu.value, nu.value
+
+
+def chol_inverse(A):
+    """A^-1 by the oracle's Cholesky (with its pivot floor) and the number of
+    floored pivots."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    out = np.zeros_like(A)
+    f = _lib_handle().o_chol_inverse(A.shape[0], A.ctypes.data_as(_D), out.ctypes.data_as(_D))
+    return out, f
+
+
+def chol_floors(reset=False):
+    """Pivots floored by every oracle Cholesky since the last reset."""
+    return int(_lib_handle().o_chol_floors(1 if reset else 0))

@@ -402,3 +402,31 @@ void o_hess_forms(OScene* s, const double* x_base, const double* x_curr, const d
     o_forms(s, z, p, out);
     o_clist_free(&C);
 }
+
+/* Classified updates of the last o_classify (through o_precond_apply or
+ * o_hess_forms with x_curr): their count; up to cap of them with dS, the
+ * contact key (type, ida, idb) and the 12-vector u.  Test access. */
+int o_updates(const OScene* s, int cap, double* dS, int* key3, double* u12) {
+    int n = s->nupd < cap ? s->nupd : cap;
+    for (int i = 0; i < n; ++i) {
+        const OUpdate* u = s->upd + i;
+        if (dS) dS[i] = u->dS;
+        if (key3) {
+            key3[3 * i] = u->type;
+            key3[3 * i + 1] = u->ida;
+            key3[3 * i + 2] = u->idb;
+        }
+        if (u12)
+            for (int j = 0; j < 12; ++j) u12[12 * i + j] = u->u[j];
+    }
+    return s->nupd;
+}
+
+/* Top-K list of level-0 subdomain g after the last o_classify: its length,
+ * and up to cap update indices (into o_updates' order), best first. */
+int o_topk(const OScene* s, int g, int cap, int* idx) {
+    if (!s->topk || g < 0 || g >= s->ngroups[0]) return 0;
+    int n = s->ntopk[g] < cap ? s->ntopk[g] : cap;
+    for (int i = 0; i < n; ++i) idx[i] = s->topk[g][i];
+    return s->ntopk[g];
+}

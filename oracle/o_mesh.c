@@ -31,45 +31,62 @@ const char* o_last_error(void) { return g_err; }
 
 /* ---------------------------------------------------------------- dense */
 
-/* Cholesky A = L L^T in place (lower).  Reading for numerically singular SPD
- * blocks (stiff rank-1 contact terms): each pivot (Schur-complement diagonal)
- * is floored at 1e-12 of the original diagonal entry, i.e. A plus a tiny
- * non-negative diagonal shift is factorised.  Returns the number of floored
- * pivots. */
+/* Cholesky A = L L^T in place (lower): the plain column algorithm.
+ * Reading for numerically singular SPD blocks (stiff rank-1 contact terms,
+ * the block inverse of supplement Sec. 1.1): a pivot (Schur-complement
+ * diagonal) at or below 1e-12 of the original diagonal entry is floored
+ * there, i.e. A plus a tiny non-negative diagonal shift is factorised.  An
+ * SPD block whose exact pivots all exceed that floor is factorised without
+ * change.  Every floored pivot is counted (o_chol_floors), so that tests can
+ * check that no parity state reaches the floor.  Returns the number of
+ * floored pivots of this call. */
+static long long g_chol_floors = 0;
+
+long long o_chol_floors(int reset) {
+    long long n = g_chol_floors;
+    if (reset) g_chol_floors = 0;
+    return n;
+}
+
 int o_chol(int n, double* A) {
     int floored = 0;
     for (int j = 0; j < n; ++j) {
         double a0 = A[j * n + j];
         double s = a0;
         for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
-        /* column j of the Schur complement, not yet divided by the pivot */
-        double th = 0.0;
-        for (int i = j + 1; i < n; ++i) {
-            double t = A[i * n + j];
-            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
-            A[i * n + j] = t;
-            /* for an SPD matrix the squared row norm of L equals the
-             * diagonal, so L_ij^2 <= A_ii; where rounding breaks that the
-             * pivot is raised until it holds (a diagonal shift, as in a
-             * modified Cholesky factorisation) */
-            double aii = A[i * n + i];
-            if (aii > 0.0 && t * t / aii > th) th = t * t / aii;
-        }
         double fl = 1e-12 * a0;
         if (!(s > fl)) {
             s = fl > 0.0 ? fl : 1.0;
             ++floored;
         }
-        if (s < th) {
-            s = th;
-            ++floored;
-        }
         double l = sqrt(s);
         A[j * n + j] = l;
-        for (int i = j + 1; i < n; ++i) A[i * n + j] /= l;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = t / l;
+        }
         for (int i = 0; i < j; ++i) A[i * n + j] = 0.0;
     }
+    g_chol_floors += floored;
     return floored;
+}
+
+/* Dense SPD inverse through o_chol (test access to the factorisation):
+ * out = A^-1 column by column; returns the floored pivots. */
+int o_chol_inverse(int n, const double* A, double* out) {
+    double* L = (double*)malloc(sizeof(double) * n * n);
+    double* e = (double*)malloc(sizeof(double) * n);
+    memcpy(L, A, sizeof(double) * n * n);
+    int f = o_chol(n, L);
+    for (int c = 0; c < n; ++c) {
+        for (int i = 0; i < n; ++i) e[i] = i == c ? 1.0 : 0.0;
+        o_chol_solve(n, L, e);
+        for (int i = 0; i < n; ++i) out[i * n + c] = e[i];
+    }
+    free(L);
+    free(e);
+    return f;
 }
 
 void o_chol_solve(int n, const double* L, double* b) {

@@ -17,15 +17,26 @@
  *    denominator forces a restart.
  *  - Energy check ("Line Search" stage of Table 2): the first trial is the
  *    per-subdomain step x + sum_d alpha_d S_d p; it is accepted if
- *    E(x_{k+1}) <= E(x_k).  Per-subdomain scaling of p is not in general a
- *    descent direction (it can stretch a body whose lower subdomains are
- *    clamped), so a rejected first trial falls back to per-body steps (each
+ *    E(x_{k+1}) <= E(x_k) + tau, where tau bounds the rounding of the two
+ *    computed energies: tau = 64 u (|E(x_k)| + 4 h^2 sum_t V_t mu_t), u =
+ *    2^-52.  The second term is the size of the elastic terms before they
+ *    cancel (mu/2 (|F|^2 - 3) - mu (J - 1) is a difference of O(mu) values
+ *    near the rest state); inertia and barrier terms are non-negative and
+ *    are covered by |E|.  Without tau, a step whose decrease is below the
+ *    resolution of E is accepted or rejected by rounding alone.
+ *    Per-subdomain scaling of p is not in general a descent direction (it
+ *    can stretch a body whose lower subdomains are clamped), so a rejected
+ *    first trial falls back to per-body steps (each
  *    connected body moves uniformly by its own verified alpha_b) scaled by
  *    1, 1/2, 1/4, 1/8 -- skipped when no body exceeds the uniform step --
  *    then to the uniform step beta = min_d alpha_d (safe by construction)
- *    halved until the energy does not increase, ls_max + 1 trials in all.
- *    If none is accepted, x does not move and the next iteration restarts; a
- *    rejection on a restart iteration ends the step unconverged.
+ *    halved until one is accepted, ls_max + 1 trials in all.
+ *    If none is accepted, x does not move and the next iteration restarts.
+ *  - Algorithm 1 tests convergence (restart and |z| <= eps) after the update
+ *    whatever the update was, so a restart iteration with |z| <= eps ends the
+ *    step converged even when no trial was accepted (the remaining step is
+ *    below the tolerance); a rejection on a restart iteration with |z| > eps
+ *    ends the step unconverged.
  *  - Velocity update v = (x^{t+1} - x^t) / h; x~ = x + h v + h^2 gravity.
  */
 #include "o_internal.h"
@@ -59,6 +70,12 @@ static double energy_with(OScene* s, const double* x, const double* xt, const OC
         Eb += s->prm.kappa * b[0];
     }
     return Ein + Eel + Eb;
+}
+
+double o_energy_tolerance(OScene* s, double E) {
+    double el = 0.0;
+    for (int t = 0; t < s->nt; ++t) el += s->vol[t] * s->mu[t];
+    return 64.0 * ldexp(1.0, -52) * (fabs(E) + 4.0 * s->prm.h * s->prm.h * el);
 }
 
 double o_energy(OScene* s, const double* x, const double* xtilde) {
@@ -227,7 +244,7 @@ int o_step(OScene* s, double* x, double* v, OStepStats* st) {
             }
             o_find_contacts(s, xtry, &Ctry);
             double Et = energy_with(s, xtry, xt, &Ctry);
-            if (Et <= Ek) {
+            if (Et <= Ek + o_energy_tolerance(s, Ek)) {
                 accepted = 1;
                 memcpy(xk, xtry, sizeof(double) * n3);
                 OContactList tmp = C;
@@ -245,14 +262,14 @@ int o_step(OScene* s, double* x, double* v, OStepStats* st) {
         if (!accepted) {
             S.ls_failures++;
             forced = 1;
-            if (restart) {
-                push_trace(s, &rec);
-                ++k;
-                break;
-            }
         }
         if (restart && zn <= eps) {
             S.converged = 1;
+            push_trace(s, &rec);
+            ++k;
+            break;
+        }
+        if (forced && restart) {
             push_trace(s, &rec);
             ++k;
             break;

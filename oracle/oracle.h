@@ -137,6 +137,25 @@ void o_precond_apply(OScene* s, const double* x_base, const double* x_curr,
 void o_hess_forms(OScene* s, const double* x_base, const double* x_curr,
                   const double* z, const double* p, double out[3]);
 
+/* Classification (Sec. 4.1.1) of the last o_precond_apply / o_hess_forms
+ * call with x_curr: number of updates (dS > 0); up to cap of them with dS,
+ * key (type, ida, idb) and u = sqrt(dS) n_curr over the contact's 4 vertices
+ * (12 doubles). */
+int o_updates(const OScene* s, int cap, double* dS, int* key3, double* u12);
+/* Top-K list of level-0 subdomain g after that call: its length and up to
+ * cap update indices, best first (dS descending, ties by key ascending). */
+int o_topk(const OScene* s, int g, int cap, int* idx);
+
+/* Dense Cholesky with the pivot floor used for every MAS block: out = A^-1
+ * (n x n, row-major); returns the pivots floored.  o_chol_floors returns the
+ * pivots floored by every factorisation since the last reset (reset != 0
+ * clears the count). */
+int o_chol_inverse(int n, const double* A, double* out);
+long long o_chol_floors(int reset);
+
+/* Rounding allowance of the energy check at energy E (see o_step). */
+double o_energy_tolerance(OScene* s, double E);
+
 /* ---- CCD -------------------------------------------------------------- */
 double o_cubic_safe(const double coef[4], double alpha_l);   /* d,c,b,a */
 /* safe fraction of one PT (kind 0: p, t0, t1, t2) or EE (kind 1) pair moving

@@ -70,3 +70,16 @@ def min_surface_distance(x, sv, sf, se):
         d = np.where(inc, np.inf, d)
         best = min(best, d.min())
     return best
+
+
+def contact_state(sc, frac=0.5):
+    """Positions of a two-cube scene with point-triangle, edge-edge and
+    point-ground contacts active: the upper cube lowered to within frac*dhat
+    of the lower one, the lower one frac*dhat above the ground."""
+    x = sc["x0"].copy()
+    nv = x.shape[0] // 2
+    dhat = sc["params"]["dhat"]
+    x[:nv, 1] -= x[:nv, 1].min() - frac * dhat
+    gap = x[nv:, 1].min() - x[:nv, 1].max()
+    x[nv:, 1] -= gap - frac * dhat
+    return x

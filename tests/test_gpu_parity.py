@@ -10,6 +10,8 @@ inputs, through the C-ABI.  Tolerances:
 import numpy as np
 import pytest
 
+from tests.geometry import contact_state
+
 pytestmark = pytest.mark.gpu
 
 RNG = np.random.default_rng(2024)
@@ -35,19 +37,6 @@ def _scenes():
 
 
 SCENES = _scenes()
-
-
-def contact_state(sc, frac=0.5):
-    """Positions with PT, EE and point-ground contacts active: the upper cube
-    lowered to within frac*dhat of the lower one, the lower one frac*dhat above
-    the ground."""
-    x = sc["x0"].copy()
-    nv = x.shape[0] // 2
-    dhat = sc["params"]["dhat"]
-    x[:nv, 1] -= x[:nv, 1].min() - frac * dhat
-    gap = x[nv:, 1].min() - x[:nv, 1].max()
-    x[nv:, 1] -= gap - frac * dhat
-    return x
 
 
 def _pair(lib, sc, precision=0, **kw):
