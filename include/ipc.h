@@ -128,6 +128,14 @@ typedef struct ipc_params {
                                 primitive + 4096). A pass that finds more
                                 runs its FP64 tests inside the query instead:
                                 same results, slower. */
+    int wait_polls;          /* polls of each bounded wait of a CTA on its
+                                bulk copy into shared memory (default 2^22,
+                                far above any copy's latency). A wait that
+                                runs out marks the call IPC_ERR_TIMEOUT; the
+                                CTA then still drains its copy before it
+                                exits. 0 makes every such wait report a
+                                timeout without polling (a test of the error
+                                path that needs no fault). */
 } ipc_params;
 
 /* Device allocator used for all scene memory; NULL functions = cudaMalloc. */
@@ -193,12 +201,16 @@ typedef enum ipc_query_kind {
                                 ipc_query_level) */
     IPC_Q_BBOX_DIAG = 10,    /* double */
     IPC_Q_N_BODIES = 11,     /* int: connected bodies of the mesh */
-    IPC_Q_FP64_BLOCKS = 12   /* int: subdomain blocks the last restart inverted
+    IPC_Q_FP64_BLOCKS = 12,  /* int: subdomain blocks the last restart inverted
                                 in FP64. FP32 bulk: the blocks whose FP32
                                 factorisation would floor a pivot or raise one
                                 (Sec. 4.2 inverse with the row-norm bound), 0
                                 before the first restart; FP64 bulk: every
                                 block. */
+    IPC_Q_PIVOT_FIXES = 13   /* int: blocks of the last restart whose final
+                                (FP64) factorisation floored or raised a
+                                pivot: 0 means every stored inverse is that of
+                                a plain Cholesky factorisation */
 } ipc_query_kind;
 
 /* Copy a piece of state into host memory dst (dst_bytes long). */
@@ -313,22 +325,30 @@ int ipc_eval_ccd(ipc_scene* s, const double* x, const double* p, double* alpha,
  *  - g_dev, z_dev: 3 n_verts values each in the scene's bulk precision
  *    (double for IPC_PREC_FP64, float for IPC_PREC_FP32), on the scene's
  *    device, which must be current; they must not overlap.  z need not be
- *    initialised.  The call only reads g and the scene and writes z.
- *  - Work is enqueued on `stream` and the call returns without waiting.
- *  - Scratch: the coarse residuals and solutions (levels >= 1) live in one
- *    static 256 KiB device array per device (2 x align256(3 x coarse nodes x
- *    sizeof(value)) bytes are used); nothing in it needs to start at zero.
- *    Calls that overlap in time on one device race on that array: order
- *    them on one stream or synchronise between them.
+ *    initialised.  The call reads g and the scene, writes z and the static
+ *    array below, and nothing of the scene.
+ *  - The work is enqueued on `stream`; the call then waits for that stream
+ *    (it reads the status of the bulk-copy waits back into host stack
+ *    memory), so z is complete when it returns IPC_OK.
+ *  - Scratch: a status record and the coarse residuals and solutions
+ *    (levels >= 1) live in one static 256 KiB device array per device
+ *    (align256(status) + 2 x align256(3 x coarse nodes x sizeof(value))
+ *    bytes are used).  The status record is cleared at the start of every
+ *    call, and every coarse value is written before it is read.  Calls that
+ *    overlap in time on one device race on that array: order them on one
+ *    stream or synchronise between them.
  *  - The first call on each device resolves the array's address
  *    (cudaGetSymbolAddress), which may load the library's device code on
  *    that device; make that first call before any stream capture begins.
- *  - Errors: IPC_ERR_INVALID for a null argument, host or foreign-device
- *    arrays, overlapping g and z, or another device current;
- *    IPC_ERR_CAPACITY when the coarse levels need more than the static
- *    array (above roughly 1.7e5 vertices in FP64, twice that in FP32);
- *    IPC_ERR_CUDA if a launch fails.  Only error paths allocate (host
- *    memory for the message). */
+ *    The address is kept for the life of the process: after a reset of the
+ *    device (cudaDeviceReset) this entry point must not be called again.
+ *  - Errors: IPC_ERR_INVALID for a null argument, a scene with no
+ *    RebuildMAS yet, host or foreign-device arrays, overlapping g and z, or
+ *    another device current; IPC_ERR_CAPACITY when the coarse levels need
+ *    more than the static array (above roughly 1.7e5 vertices in FP64, twice
+ *    that in FP32); IPC_ERR_TIMEOUT when a bounded wait on a bulk copy ran
+ *    out (z is then not defined); IPC_ERR_CUDA if a launch fails.  Only
+ *    error paths allocate (host memory for the message). */
 int ipc_precond_apply_noalloc(ipc_scene* s, const void* g_dev, void* z_dev, void* stream);
 
 const char* ipc_last_error(void);

@@ -161,6 +161,8 @@ struct ipc_scene {
     // sequence's host flags; a key is captured the second time it occurs
     std::unordered_map<unsigned long long, cudaGraphExec_t> graphs;
     std::unordered_set<unsigned long long> seen, uncapturable;
+    // set once a RebuildMAS has been enqueued: the MAS blocks hold inverses
+    bool mas_built = false;
     cudaStream_t own = nullptr;  // used when the caller passes the legacy default stream
     cudaEvent_t own_ev = nullptr;
     ~ipc_scene() {
@@ -262,6 +264,20 @@ int setup_dev(ipc_scene* s) {
     D.eps_abs = p.eps_abs;
     D.K = p.K;
     D.ls_max = p.ls_max;
+    D.wait_polls = p.wait_polls;
+    {
+        // rounding allowance of the energy check, tau = 64 u (|E_k| + 4 h^2
+        // sum_t V_t mu_t): the second term is the size of the elastic terms
+        // before they cancel near the rest state. u = 2^-52 for FP64
+        // energies; with an FP32 bulk the elastic energy is double-float
+        // from positions split to 2^-48 of their size, u = 2^-44 (a 16x
+        // allowance for coordinates far from the origin relative to edges)
+        double vmu = 0.0;
+        for (int t = 0; t < m.nt; ++t) vmu += m.vol[t] * m.mu[t];
+        const double u = sizeof(R) == 8 ? std::ldexp(1.0, -52) : std::ldexp(1.0, -44);
+        D.tau_rel = 64.0 * u;
+        D.tau_abs = 64.0 * u * 4.0 * p.h * p.h * vmu;
+    }
     for (int r = 0; r < 3; ++r) {
         D.gravity[r] = m.gravity[r];
         D.gn[r] = m.gn[r];
@@ -316,6 +332,7 @@ int setup_dev(ipc_scene* s) {
     const int nb0 = m.nlev > 1 ? D.blk_off[1] : nb;
     D.asmb = A.arr<double>((size_t)nb0 * kBlk * kBlk);
     D.invflag = A.arr<int>(std::max(nb, 1));
+    D.pivfix = A.arr<int>(1);
     D.asmbc = A.arr<double>((size_t)std::max(nb - nb0, 1) * kBlk * kBlk);
     // diagonal of each block's mass term: the lumped mass of the block's
     // nodes (sums of vertex masses at the coarse levels), fixed by the mesh
@@ -530,6 +547,7 @@ int setup_dev(ipc_scene* s) {
     CUDA_TRY(cudaMemcpy(D.v, m.v0.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(D.S, 0, sizeof(Scalars)));
     CUDA_TRY(cudaMemset(D.invflag, 0, sizeof(int) * std::max(D.blk_off[D.nlev], 1)));
+    CUDA_TRY(cudaMemset(D.pivfix, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(D.hess, 0, sizeof(R) * (size_t)D.ntp * kH * kPack));
     CUDA_TRY(cudaMemset(D.Cb.count, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(D.C.count, 0, sizeof(int)));
@@ -774,7 +792,10 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         // nothing (frozen)
         const bool rebuild = restart || P.mas_mode == 1;
         const bool woodbury = !restart && P.mas_mode == 0;
-        if (rebuild) ++restarts;
+        if (rebuild) {
+            ++restarts;
+            s->mas_built = true;
+        }
         run_seq(s, D, st, restart ? 1 : (P.mas_mode == 1 ? 5 : P.mas_mode == 2 ? 6 : 2), [&] {
             if (rebuild) {
                 Stage t(s, 0, st);
@@ -803,13 +824,17 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
                 Stage t(s, 4, st);
                 launch_direction(D, restart, st);
             }
-            // g.z, max|p| and the list drift of this iteration
+            // g.z, max|p|, the list drift and the bulk-copy status of this
+            // iteration
             cudaMemcpyAsync(&s->hv->S.gz, &D.S->gz, sizeof(double), cudaMemcpyDeviceToHost, st);
             cudaMemcpyAsync(&s->hv->S.pmax, &D.S->pmax, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(&s->hv->S.async_timeout, &D.S->async_timeout, sizeof(int), cudaMemcpyDeviceToHost, st);
         });
         bool use_list = false;
         double bound_after = INFINITY;
         CUDA_TRY(cudaStreamSynchronize(st));
+        // z is not defined after a timed-out block copy: stop before it is used
+        if (s->hv->S.async_timeout) return fail(IPC_ERR_TIMEOUT, "a bulk copy into shared memory did not complete");
         if (!restart && !(s->hv->S.gz > 0.0)) {
             // the Woodbury-patched preconditioner is not positive at g (FP32
             // inverses of very stiff blocks): no step; the iteration is
@@ -917,12 +942,15 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         bool forced = !accepted;
         if (forced) ++failures;
         s->trace.push_back(rec);
-        if (forced && restart) {
+        // Algorithm 1 tests convergence after the update whatever it was: a
+        // restart iteration with |z| <= eps ends the timestep converged even
+        // when no trial was accepted (what is left is below the tolerance)
+        if (restart && S.znorm <= D.eps_conv) {
+            converged = 1;
             ++k;
             break;
         }
-        if (restart && S.znorm <= D.eps_conv) {
-            converged = 1;
+        if (forced && restart) {
             ++k;
             break;
         }
@@ -1077,6 +1105,7 @@ int prepare_precond(ipc_scene* s, const double* x_base, const double* x_curr, cu
     KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
     launch_detect(E, E.x, E.C, st);
     launch_restart(E, E.x, E.C, st);
+    s->mas_built = true;
     *wood = false;
     if (x_curr) {
         CUDA_TRY(cudaMemcpyAsync(D.xs, x_curr, sizeof(double) * n3, cudaMemcpyHostToDevice, st));
@@ -1100,7 +1129,9 @@ int eval_precond_impl(ipc_scene* s, const double* xb, const double* xc, const do
     launch_precond(D, D.g, D.z, wood ? D.Ct : D.C, wood, st);
     std::vector<R> zr(n3);
     CUDA_TRY(cudaMemcpyAsync(zr.data(), D.z, sizeof(R) * n3, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&s->hv->S.async_timeout, &D.S->async_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    if (s->hv->S.async_timeout) return fail(IPC_ERR_TIMEOUT, "a bulk copy into shared memory did not complete");
     for (size_t i = 0; i < n3; ++i) z[i] = (double)zr[i];
     return IPC_OK;
 }
@@ -1185,6 +1216,7 @@ int replay_impl(ipc_scene* s, int stage, int reps, void* flush, size_t flush_byt
     }
     double tot = 0.0;
     int rc = IPC_OK;
+    KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
     for (int i = 0; i < reps && rc == IPC_OK; ++i) {
         if (stage == 3) launch_forms_prep(D, false, st);  // packing and zeroing, untimed
         if (flush && flush_bytes >= 16)
@@ -1203,7 +1235,11 @@ int replay_impl(ipc_scene* s, int stage, int reps, void* flush, size_t flush_byt
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (rc == IPC_OK) *ms = tot / reps;
+    if (rc == IPC_OK) {
+        CUDA_TRY(cudaMemcpy(&s->hv->S.async_timeout, &D.S->async_timeout, sizeof(int), cudaMemcpyDeviceToHost));
+        if (s->hv->S.async_timeout) return fail(IPC_ERR_TIMEOUT, "replay: a bulk copy into shared memory did not complete");
+        *ms = tot / reps;
+    }
     return rc;
 }
 
@@ -1215,11 +1251,12 @@ int replay_impl(ipc_scene* s, int stage, int reps, void* flush, size_t flush_byt
 // memory is owned by another allocator (a framework's caching pool), where
 // one more allocation can fail. The MAS apply (Sec. 3.3, additive over
 // levels) needs scratch only for the restricted residuals r_l and coarse
-// solutions y_l of levels l >= 1; here they live in one static device array
-// per device instead of the scene's arena. Nothing in it has to start at
-// zero: within a call every coarse residual and every coarse solution is
-// written before it is read. Calls that overlap in time on one device
-// (any scene, any stream) share this array and race.
+// solutions y_l of levels l >= 1, plus a status record for its bulk-copy
+// waits; here they live in one static device array per device instead of
+// the scene's arena, so the call writes nothing of the scene. The status
+// record is cleared at the start of every call; every coarse residual and
+// every coarse solution is written before it is read. Calls that overlap in
+// time on one device (any scene, any stream) share this array and race.
 constexpr size_t kNoAllocScratchBytes = 256 * 1024;
 constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -1239,6 +1276,10 @@ bool device_array_on(const void* p, int dev) {
 template <class R>
 int precond_noalloc_impl(ipc_scene* s, const void* g_dev, void* z_dev, cudaStream_t st) {
     const Dev<R>& D = dev_of<R>(s);
+    if (!s->mas_built)
+        return fail(IPC_ERR_INVALID,
+                    "ipc_precond_apply_noalloc: the scene has no preconditioner yet (no RebuildMAS has run: call "
+                    "ipc_step, ipc_eval_precond or ipc_eval_forms first)");
     int dev = -1;
     CUDA_TRY(cudaGetDevice(&dev));
     if (!device_array_on(D.blocks, dev))
@@ -1250,7 +1291,8 @@ int precond_noalloc_impl(ipc_scene* s, const void* g_dev, void* z_dev, cudaStrea
     const char* zb = static_cast<const char*>(z_dev);
     if (gb < zb + bytes && zb < gb + bytes) return fail(IPC_ERR_INVALID, "ipc_precond_apply_noalloc: g and z overlap");
     const size_t n_coarse = (size_t)D.coarse_off[D.nlev];
-    const size_t need = 2 * align256(sizeof(R) * n_coarse);
+    const size_t status = align256(sizeof(Scalars));
+    const size_t need = status + 2 * align256(sizeof(R) * n_coarse);
     if (need > kNoAllocScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof msg,
@@ -1267,11 +1309,22 @@ int precond_noalloc_impl(ipc_scene* s, const void* g_dev, void* z_dev, cudaStrea
         CUDA_TRY(cudaGetSymbolAddress(&base, g_noalloc_scratch));
         g_noalloc_addr[dev].store(base, std::memory_order_release);
     }
+    unsigned char* b = static_cast<unsigned char*>(base);
     Dev<R> E = D;
-    E.coarse_r = static_cast<R*>(base);
-    E.coarse_y = reinterpret_cast<R*>(static_cast<unsigned char*>(base) + align256(sizeof(R) * n_coarse));
+    E.S = reinterpret_cast<Scalars*>(b);
+    E.coarse_r = reinterpret_cast<R*>(b + status);
+    E.coarse_y = reinterpret_cast<R*>(b + status + align256(sizeof(R) * n_coarse));
+    CUDA_TRY(cudaMemsetAsync(E.S, 0, sizeof(Scalars), st));
     launch_precond(E, static_cast<const R*>(g_dev), static_cast<R*>(z_dev), E.C, false, st);
     CUDA_TRY(cudaGetLastError());
+    // the bounded bulk-copy waits report through the status record: read it
+    // (into host stack memory) once the apply has finished
+    int timed_out = 0;
+    CUDA_TRY(cudaMemcpyAsync(&timed_out, &E.S->async_timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (timed_out)
+        return fail(IPC_ERR_TIMEOUT, "ipc_precond_apply_noalloc: a bulk copy into shared memory did not complete; z is "
+                                     "not defined");
     return IPC_OK;
 }
 
@@ -1307,6 +1360,7 @@ void ipc_default_params(ipc_params* p) {
     p->graphs = 1;
     p->fp32_pivot_floor = 1e-6;
     p->grid_pair_capacity = 0;
+    p->wait_polls = 1 << 22;
 }
 
 const char* ipc_last_error(void) { return g_err.c_str(); }
@@ -1464,6 +1518,12 @@ int ipc_query(ipc_scene* s, int what, void* dst, size_t bytes, void* stream) {
             int n = 0;
             for (int i = 0; i < nb; ++i) n += fl[i] != 0;
             *(int*)dst = n;
+            return IPC_OK;
+        }
+        case IPC_Q_PIVOT_FIXES: {
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            CUDA_TRY(cudaMemcpyAsync(dst, f64 ? s->dd.pivfix : s->df.pivfix, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
             return IPC_OK;
         }
         case IPC_Q_BBOX_DIAG:

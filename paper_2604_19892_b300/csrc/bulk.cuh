@@ -43,10 +43,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// waits for the phase of the given parity; false after about 4M polls
-// (each poll may suspend for a hardware-bounded time)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i)
+// polls of a wait that drains a copy still in flight before its CTA exits
+// (never shortened: shared memory must not be released under a copy)
+constexpr int kDrainPolls = 1 << 22;
+
+// waits for the phase of the given parity; false after `polls` polls (each
+// poll may suspend for a hardware-bounded time); polls <= 0 returns false
+// without polling
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int polls = kDrainPolls) {
+    for (int i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

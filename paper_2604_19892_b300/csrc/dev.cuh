@@ -92,6 +92,10 @@ struct Dev {
     // parameters
     double h, dhat, kappa, eps_conv, delta, cos_rot, ccd_shrink, eps_sing, eps_abs;
     int K, ls_max;
+    // energy check: accept E_try <= E_k + tau_rel |E_k| + tau_abs (rounding
+    // allowance of the two computed energies)
+    double tau_rel, tau_abs;
+    int wait_polls;                        // polls of a bounded wait on a bulk copy
     double gravity[3];
     int has_ground;
     double gn[3], goff;
@@ -131,6 +135,7 @@ struct Dev {
     const int2* tcon;                      //   (slot in cval, vertex masks: bits 0-3 set i, 4-7 set j)
     const int4* item;                      // nitem + 1: global block, slot i, slot j | split << 8, first entry
     int* invflag;                          // level-0 blocks to re-invert in FP64
+    int* pivfix;                           // blocks whose final factorisation floored or raised a pivot (last restart)
     R* coarse_r;                           // restricted residuals, 3 * nnodes[l] per level, offsets coarse_off
     R* coarse_y;
     int coarse_off[kMaxLevels + 1];

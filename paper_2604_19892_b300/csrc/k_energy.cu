@@ -313,7 +313,9 @@ template <class R>
 __global__ void k_accept(Dev<R> D) {
     Scalars* S = D.S;
     double Et = S->E_try;
-    S->accepted = (Et <= S->E_k) ? 1 : 0;
+    const double Ek = S->E_k;
+    // E(x_try) <= E(x_k) up to the rounding of the two computed energies
+    S->accepted = (Et <= Ek + (D.tau_rel * fabs(Ek) + D.tau_abs)) ? 1 : 0;
     if (S->accepted) S->E_k = Et;
 }
 

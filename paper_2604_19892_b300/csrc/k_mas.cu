@@ -845,6 +845,9 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
 
     // ---- B = s W^T W s; tile (ti, tj) needs rows k >= 6 ti of W only
     if (pass == 0 && flags && threadIdx.x == 0) flags[b] = s_bad;
+    // the final factorisation of this block (FP64 form, or the FP64 redo)
+    // modified a pivot: counted for the parity checks
+    if ((pass == 1 || !flags) && threadIdx.x == 0 && s_bad && D.pivfix) atomicAdd(D.pivfix, 1);
     if (!act) return;
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
@@ -1326,12 +1329,12 @@ __global__ void __launch_bounds__(96) k_block_apply_plain(Dev<R> D, const R* __r
     else
         rhs[tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : (R)0;
     __syncthreads();  // rhs complete; the barrier's initialisation is visible
-    const bool arrived = mbar_wait(&bar, 0);
+    const bool arrived = mbar_wait(&bar, 0, D.wait_polls);
     if (__syncthreads_or(!arrived)) {
         // record, wait (bounded) for the copy in flight, leave z unwritten
         if (tid == 0) {
             D.S->async_timeout = 1;
-            mbar_wait(&bar, 0);
+            mbar_wait(&bar, 0, kDrainPolls);
         }
         return;
     }
@@ -1414,12 +1417,12 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
     __syncthreads();
     // Y = B [rhs] from the staged block; B is symmetric, so thread c reads
     // column c (consecutive threads, consecutive words) and forms row c of Y
-    const bool arrived = mbar_wait(&bar, 0);
+    const bool arrived = mbar_wait(&bar, 0, D.wait_polls);
     if (__syncthreads_or(!arrived)) {
         // record, wait (bounded) for the copy in flight, leave z unwritten
         if (tid == 0) {
             D.S->async_timeout = 1;
-            mbar_wait(&bar, 0);
+            mbar_wait(&bar, 0, kDrainPolls);
         }
         return;
     }
@@ -1603,6 +1606,7 @@ template <class R>
 void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
     int nb = D.blk_off[D.nlev];
     KL(k_clear_upd<R><<<1, 1, 0, st>>>(D));
+    if (D.pivfix) cudaMemsetAsync(D.pivfix, 0, sizeof(int), st);
     const int nb0 = D.nlev > 1 ? D.blk_off[1] : nb;
     KL(k_init_blocks<R><<<nblk((long long)nb * (kBlk * kBlk / 4), 256), 256, 0, st>>>(D, nb0, nb));
     KL(k_tet_hessian<R><<<nblk(D.nt, 64), 64, 0, st>>>(D, x));

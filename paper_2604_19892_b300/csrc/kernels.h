@@ -51,7 +51,7 @@ template <class R> void launch_detect_list(const Dev<R>& D, const double* x, con
 // part 0: all; 1: the per-pair bounds only; 2: the verification only
 template <class R> void launch_ccd_list(const Dev<R>& D, cudaStream_t st, int part = 0);
 template <class R> void launch_global_alpha(const Dev<R>& D, cudaStream_t st);
-// S->accepted = E_try <= E_k
+// S->accepted = E_try <= E_k + tau (the rounding allowance of the energies)
 template <class R> void launch_accept(const Dev<R>& D, cudaStream_t st);
 // H_base-only forms for evaluation entry points
 template <class R> void launch_zero_scalars(const Dev<R>& D, cudaStream_t st);

@@ -21,6 +21,7 @@ IPC_OK = 0
 IPC_NOT_CONVERGED = 1
 IPC_PENDING = 2
 IPC_ERR_INVALID = -1
+IPC_ERR_TIMEOUT = -5
 IPC_ERR_CAPACITY = -7
 IPC_PREC_FP64 = 0
 IPC_PREC_FP32 = 1
@@ -43,7 +44,7 @@ class Params(C.Structure):
                 ("levels_max", C.c_int), ("ls_max", C.c_int), ("precision", C.c_int),
                 ("contact_capacity", C.c_int), ("broad_phase", C.c_int), ("mas_mode", C.c_int),
                 ("ccd_mode", C.c_int), ("graphs", C.c_int), ("fp32_pivot_floor", C.c_double),
-                ("grid_pair_capacity", C.c_int)]
+                ("grid_pair_capacity", C.c_int), ("wait_polls", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -80,7 +81,7 @@ class Profile(C.Structure):
 STAGES = ["restart", "classify", "mas_blocks", "forms", "direction", "ccd", "trial_eval", "other"]
 
 Q_POSITIONS, Q_VELOCITIES, Q_N_VERTS, Q_N_CONTACTS, Q_SUBDOMAIN_ALPHA, Q_N_SUBDOMAINS, Q_TRACE_LEN, Q_TRACE, \
-    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG, Q_N_BODIES, Q_FP64_BLOCKS = range(13)
+    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG, Q_N_BODIES, Q_FP64_BLOCKS, Q_PIVOT_FIXES = range(14)
 
 _lib = None
 
@@ -191,7 +192,7 @@ def default_params(sc_params: dict, precision: int = IPC_PREC_FP64) -> Params:
     lib.ipc_default_params(C.byref(p))
     for k in ("h", "dhat", "kappa", "tol", "delta", "eps_rot_deg", "ccd_shrink", "eps_sing", "eps_abs", "K",
               "iter_max", "levels_max", "ls_max", "broad_phase", "mas_mode", "ccd_mode", "graphs",
-              "fp32_pivot_floor", "grid_pair_capacity"):
+              "fp32_pivot_floor", "grid_pair_capacity", "wait_polls"):
         if k in sc_params:
             setattr(p, k, type(getattr(p, k))(sc_params[k]))
     p.precision = precision
@@ -306,6 +307,11 @@ class Scene:
         blocks whose FP32 factorisation would floor or raise a pivot)."""
         return int(self._query_array(Q_FP64_BLOCKS, 1, np.int32)[0])
 
+    def pivot_fixes(self):
+        """Blocks of the last restart whose final (FP64) factorisation
+        floored or raised a pivot (0: plain Cholesky inverses throughout)."""
+        return int(self._query_array(Q_PIVOT_FIXES, 1, np.int32)[0])
+
     def trace(self):
         n = int(self._query_array(Q_TRACE_LEN, 1, np.int32)[0])
         rec = (IterRecord * max(n, 1))()
@@ -390,8 +396,8 @@ class Scene:
 
     def precond_apply_noalloc(self, g_dev, z_dev, stream=None):
         """z = P_base g on device tensors of shape (nv, 3) in the scene's bulk
-        precision, through the allocation-free entry point; enqueued on the
-        stream, not waited for."""
+        precision, through the allocation-free entry point; returns once z is
+        complete (the call waits for the stream)."""
         import torch
         want = torch.float64 if self.precision == IPC_PREC_FP64 else torch.float32
         for t in (g_dev, z_dev):

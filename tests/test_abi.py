@@ -76,3 +76,4 @@ def test_params_mirror_matches_the_header():
     assert (p.mas_mode, p.ccd_mode, p.graphs) == (0, 0, 1)
     assert p.fp32_pivot_floor == 1e-6
     assert p.grid_pair_capacity == 0
+    assert p.wait_polls == 1 << 22

@@ -106,19 +106,51 @@ def test_contact_set_parity(lib, name, bp):
 
 @pytest.mark.parametrize("name", list(SCENES))
 def test_preconditioner_parity(lib, name):
+    import oracle as O
     sc = SCENES[name]
     g, o = _pair(lib, sc)
     xb = contact_state(sc, 0.9)
     xc = contact_state(sc, 0.4) + 1e-6 * RNG.normal(size=xb.shape)
     grad = RNG.normal(size=xb.shape)
     # restart only: P_base
+    O.chol_floors(reset=True)
     zg = g.precond_apply(xb, grad)
     zo = o.precond_apply(xb, grad)
     assert np.linalg.norm(zg - zo) <= 1e-9 * np.linalg.norm(zo)
+    # both sides inverted every block by plain Cholesky (no pivot rule fired)
+    assert g.pivot_fixes() == 0 and O.chol_floors() == 0
     # Woodbury update (GPU) vs rebuilt level-0 inverses (oracle), Eq. 7
     zg = g.precond_apply(xb, grad, xc)
     zo = o.precond_apply(xb, grad, xc)
     assert np.linalg.norm(zg - zo) <= 1e-7 * np.linalg.norm(zo)
+    assert g.pivot_fixes() == 0 and O.chol_floors() == 0
+
+
+def test_preconditioner_parity_with_tied_updates(lib):
+    """A jitter-free cube dhat/2 above the ground: its bottom vertices' new
+    point-ground contacts all tie on dS, and K = 3 keeps fewer than tie in a
+    subdomain. The GPU's per-subdomain selection (ties by ascending key, Sec.
+    4.1.1 top-K) must pick the oracle's contacts for the Woodbury-patched
+    preconditioner to match the rebuilt one."""
+    import oracle as O
+    from paper_2604_19892_b300 import scenes as S
+    x, t = S.box_mesh(3, 0.1 / 3, (0.0, 0.5, 0.0))
+    sc = S._assemble([(x, t, 1e5, 0.4, 1000.0)])
+    sc["params"] = S.default_params(S.bbox_diag(x), 1.0 / 30, 1e5)
+    dhat = sc["params"]["dhat"]
+    g, o = _pair(lib, sc, K=3)
+    xb = sc["x0"].copy()                         # 0.5 m up: no contact
+    xc = sc["x0"] - [0.0, 0.5 - 0.5 * dhat, 0.0]
+    c = o.contacts(xc)
+    assert len(c["k"]) == 16 and np.all(c["k"] == c["k"][0])
+    grad = RNG.normal(size=xb.shape)
+    zg = g.precond_apply(xb, grad, xc)
+    zo = o.precond_apply(xb, grad, xc)
+    assert np.linalg.norm(zg - zo) <= 1e-7 * np.linalg.norm(zo)
+    # keeping every tied contact changes z far beyond the tolerance, so the
+    # comparison above sees which ones were kept
+    zo_all = O.Scene(sc, params={"K": 16}).precond_apply(xb, grad, xc)
+    assert np.linalg.norm(zo_all - zo) > 1e-4 * np.linalg.norm(zo)
 
 
 @pytest.mark.parametrize("name", list(SCENES))

@@ -1,0 +1,86 @@
+"""Timestep-level GPU checks through the C ABI: checkpoint / resume, the FP32
+bulk form against the FP64 oracle step by step, and the error path of the
+bounded bulk-copy waits (made to run out by a zero poll budget, which needs
+no fault: each CTA still drains its copy before it exits)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_19892_b300 import build, ipc
+    build.build()
+    ipc.load()
+    torch.cuda.set_device(0)
+    return ipc
+
+
+def test_checkpoint_resume_equals_an_uninterrupted_run(lib):
+    """N timesteps in one go equal k timesteps, a checkpoint (positions and
+    velocities queried to the host), a fresh scene resumed from it by
+    ipc_set_state, and N - k more timesteps: within 1e-6 of the bounding-box
+    diagonal on a scene whose steps have one minimiser each (tol 1e-7)."""
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.ground_drop(n=3, gap=0.003, drop_speed=0.5)
+    prm = {"tol": 1e-7}
+    N, k = 4, 2
+    a = lib.Scene(sc, params=prm)
+    sa = a.step(N)
+    assert sa["converged"] == 1
+    b = lib.Scene(sc, params=prm)
+    b.step(k)
+    x, v = b.positions(), b.velocities()
+    b.close()
+    c = lib.Scene(sc, params=prm)
+    c.set_state(x, v)
+    sc_ = c.step(N - k)
+    assert sc_["converged"] == 1
+    bbox = a.bbox_diag()
+    assert np.abs(a.positions() - c.positions()).max() / bbox <= 1e-6
+    assert np.abs(a.velocities() - c.velocities()).max() * sc["params"]["h"] / bbox <= 1e-6
+    assert sa["n_contacts"] > 0
+
+
+def test_fp32_bulk_steps_follow_the_fp64_oracle(lib):
+    """The FP32 bulk form, fed the oracle's state each timestep, converges to
+    the oracle's minimiser within 1e-5 of the bounding-box diagonal through an
+    impact (tol 1e-5 for the FP32 form, 1e-8 for the oracle): FP32 gradients
+    carry relative rounding of about 1e-7, so its converged iterate is known
+    only to about tol h bbox plus that rounding mapped through P."""
+    import oracle as O
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.ground_drop(n=3, gap=0.003, drop_speed=0.5)
+    o = O.Scene(sc, params={"tol": 1e-8})
+    g = lib.Scene(sc, precision=lib.IPC_PREC_FP32, params={"tol": 1e-5})
+    x, v = sc["x0"].copy(), sc["v0"].copy()
+    errs = []
+    for step in range(4):
+        g.set_state(x, v)
+        st = g.step(1)
+        assert st["converged"] == 1, (step, st)
+        xo, vo, so = o.step(x, v)
+        assert so["converged"] == 1
+        errs.append(float(np.abs(g.positions() - xo).max() / o.bbox_diag()))
+        x, v = xo, vo
+    assert max(errs) <= 1e-5, errs
+
+
+def test_exhausted_copy_wait_reports_timeout_and_leaves_the_context_usable(lib):
+    """wait_polls = 0: every bounded wait of the block-apply CTAs reports a
+    timeout without polling; ipc_step stops with IPC_ERR_TIMEOUT before z is
+    used. A second scene with the default budget then steps normally in the
+    same process (the CTAs drained their copies, nothing faulted)."""
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.ground_drop(n=3, gap=0.003, drop_speed=0.5)
+    bad = lib.Scene(sc, params={"wait_polls": 0})
+    with pytest.raises(lib.IPCError) as e:
+        bad.step(1)
+    assert e.value.code == lib.IPC_ERR_TIMEOUT and "bulk copy" in str(e.value)
+    good = lib.Scene(sc)
+    st = good.step(2)
+    assert st["converged"] == 1

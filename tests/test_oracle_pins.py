@@ -226,16 +226,16 @@ def test_topk_breaks_ties_by_ascending_key():
     """A jitter-free cube dhat/2 above the ground: every bottom vertex has the
     same point-ground distance, so all those new contacts tie on dS = k; each
     subdomain keeps the K of smallest key (vertex id)."""
-    x, t = S.box_mesh(3, 0.1 / 3, (0.0, 0.0, 0.0))
+    x, t = S.box_mesh(3, 0.1 / 3, (0.0, 0.5, 0.0))
     sc = S._assemble([(x, t, 1e5, 0.4, 1000.0)])
     sc["params"] = S.default_params(S.bbox_diag(x), 1.0 / 30, 1e5)
     dhat = sc["params"]["dhat"]
     K = 3
     o = O.Scene(sc, params={"K": K})
-    xb = sc["x0"] + [0.0, 0.5, 0.0]
-    xc = sc["x0"] + [0.0, 0.5 * dhat, 0.0]
+    xb = sc["x0"].copy()                         # 0.5 m up: no contact
+    xc = sc["x0"] - [0.0, 0.5 - 0.5 * dhat, 0.0]
     c = o.contacts(xc)
-    bottom = np.where(sc["x0"][:, 1] == 0.0)[0]
+    bottom = np.where(sc["x0"][:, 1] == 0.5)[0]
     assert len(c["type"]) == len(bottom) == 16 and np.all(c["type"] == 2)
     assert np.all(c["k"] == c["k"][0])   # exact ties
     o.precond_apply(xb, np.zeros_like(xb), xc)
