@@ -9,8 +9,10 @@ checks.  One bench step is one implicit-Euler timestep (Algorithm 1 to
 convergence).  Inputs are synthetic and resident in HBM when the timed region
 starts; L2 is flushed (256 MB write) before every timed step.
 
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead,
-on bounded samples of the same workload.
+Prints one JSON line whose `value` is PNCG iterations per second over the
+timed timesteps (timesteps/s beside it).  `--impl reference` times the FP64
+CPU oracle instead, on bounded samples of the same workload, in the same
+unit.
 """
 from __future__ import annotations
 
@@ -43,8 +45,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--plain-steps", type=int, default=12,
-                    help="timesteps of the plain FP64 form timed for the comparison (0 = skip)")
+    ap.add_argument("--plain-steps", type=int, default=-1,
+                    help="timesteps of the plain FP64 form timed for the comparison (-1 = as many as --steps, 0 = skip)")
+    ap.add_argument("--cpu-iters", type=int, default=4,
+                    help="PNCG iterations of timestep 0 in the oracle's cpu_baseline sample")
     ap.add_argument("--replays", type=int, default=30, help="L2-flushed replays per stage for the roofline")
     ap.add_argument("--profile-replays", action="store_true",
                     help="call cudaProfilerStart/Stop around the roofline replays (ncu --profile-from-start off)")
@@ -96,6 +100,20 @@ def load_peaks():
             pk = json.load(f)
         return pk.get("hbm_gbs", 6400.0), "measured"
     return 6400.0, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_count, sm_mhz):
+    """FP32 FMA peak of the GPU from its unit counts and clock: 128 FP32
+    lanes per SM, 2 flops per FMA."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def invert_flops(nblocks):
+    """Algorithmic flops of the batched block inversion: per 96 x 96 block a
+    Cholesky factorisation (n^3 / 3) and the triangular inverse W = L^-1
+    (n^3 / 3)."""
+    n = 96
+    return nblocks * 2 * n ** 3 / 3
 
 
 class ClockSampler:
@@ -153,40 +171,64 @@ class ClockSampler:
 def stage_bytes(nv, nt, nblocks, rsize):
     """Algorithmic bytes per launch of the two per-iteration HBM-bound stages.
 
-    mas_blocks: every 96x96 inverse block once (all levels) + g read + z write.
+    mas_blocks: every block factor once (all levels; packed lower triangle,
+    96 x 97 / 2 values) + g read + z write.
     forms: per tet the packed Hessian (45), rest inverse (9) and 4 indices;
     per vertex z and p read once.
     """
-    mas = nblocks * 96 * 96 * rsize + 2 * 3 * nv * rsize
+    mas = nblocks * (96 * 97 // 2) * rsize + 2 * 3 * nv * rsize
     forms = nt * (54 * rsize + 16) + 2 * 3 * nv * rsize + nv * 8
     return {"mas_blocks": mas, "forms": forms}
 
 
-# DRAM bytes per launch from ncu captures of the same kernels (unchanged
-# since), scaled by the units a launch processes: profiles/ holds the
-# summaries and commands
-TRAFFIC = {
-    ("mas_blocks", "fp32"): {"bytes_per_block": (56.330496e6 + 0.015872e6) / 1507},
-    ("forms", "fp32"): {"bytes_per_tet": (49.594880e6 + 0.052736e6) / 196608},
-}
+# DRAM bytes per launch (read + write) from one ncu capture of each kernel in
+# its current form on the same workload (profiles/ holds the summaries and
+# commands); None where the kernel changed since its last capture
+TRAFFIC = {}
 
 
-def run_cpu_baseline(sc, gpu_iters_per_step):
-    """The oracle as it stands, one PNCG iteration of timestep 0 (bounded sample)."""
+def host_cpu():
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_iters_per_s(sc, iters, threads):
+    """Wall time of the oracle's first `iters` PNCG iterations of timestep 0
+    (iter_max = iters), on `threads` host threads (its independent loops run
+    in parallel; results do not depend on the count)."""
     import oracle as O
-    o = O.Scene(sc, params={"iter_max": 1})
+    used = O.set_threads(threads)
+    o = O.Scene(sc, params={"iter_max": iters})
     t0 = time.perf_counter()
-    o.step(sc["x0"], sc["v0"])
+    _, _, st = o.step(sc["x0"], sc["v0"])
     dt = time.perf_counter() - t0
-    iters_per_s = 1.0 / dt
+    return st["iters"] / dt, dt, used, st["iters"]
+
+
+def run_cpu_baseline(sc, iters):
+    """The oracle as it stands on a bounded sample of the workload: the first
+    `iters` PNCG iterations of timestep 0, single thread and all host cores."""
+    ncpu, model = host_cpu()
+    v1, dt1, _, n1 = oracle_iters_per_s(sc, iters, 1)
+    vn, dtn, used, nn = oracle_iters_per_s(sc, iters, ncpu)
     return {
-        "value": iters_per_s / max(gpu_iters_per_step, 1e-9),
-        "unit": "timesteps/s",
-        "cores": 1,
+        "value": vn,
+        "unit": "PNCG iters/s",
+        "cores": used,
         "kind": "oracle",
-        "sample": (f"1 PNCG iteration of timestep 0 of the same workload ({dt:.2f} s, single thread); "
-                   f"timesteps/s = oracle iters/s / GPU mean iters per timestep ({gpu_iters_per_step:.1f})"),
-        "iters_per_s": iters_per_s,
+        "sample": (f"first {nn} PNCG iterations of timestep 0 of the same workload (FP64 oracle: level-0 "
+                   f"inverses rebuilt every iteration): {dtn:.1f} s on {used} threads, {dt1:.1f} s on 1 thread"),
+        "single_thread": {"value": v1, "unit": "PNCG iters/s", "cores": 1},
+        "nproc": ncpu,
+        "cpu_model": model,
     }
 
 
@@ -198,18 +240,21 @@ def run_reference(args):
     from paper_2604_19892_b300 import scenes as S
     import oracle as O
     sc = S.sphere_pile()
-    # each reference step: one PNCG iteration of the timestep, iterations chained
-    o = O.Scene(sc, params={"iter_max": 1})
-    x, v = sc["x0"].copy(), sc["v0"].copy()
+    ncpu, model = host_cpu()
+    used = O.set_threads(ncpu)
+    # each reference step: the first two PNCG iterations of timestep 0 (a
+    # restart and a Woodbury iteration), from the workload's initial state
+    o = O.Scene(sc, params={"iter_max": 2})
     for _ in range(args.warmup):
-        o.step(x, v)
-    times = []
+        o.step(sc["x0"], sc["v0"])
+    times, iters = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.step(x, v)
+        _, _, st = o.step(sc["x0"], sc["v0"])
         times.append(time.perf_counter() - t0)
+        iters += st["iters"]
     total = sum(times)
-    iters_per_s = args.steps / total
+    iters_per_s = iters / total
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -224,9 +269,10 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "each step = 1 PNCG iteration of timestep 0 (FP64 oracle)"},
-        "cpu_baseline": {"value": iters_per_s, "unit": "PNCG iters/s", "cores": 1, "kind": "oracle",
-                         "sample": "1 PNCG iteration of timestep 0 per step, single thread"},
+        "config": {"workload": WORKLOAD, "sample": "each step = the first 2 PNCG iterations of timestep 0 (FP64 oracle)"},
+        "cpu_baseline": {"value": iters_per_s, "unit": "PNCG iters/s", "cores": used, "kind": "oracle",
+                         "sample": f"first 2 PNCG iterations of timestep 0 per step, {used} host threads",
+                         "nproc": ncpu, "cpu_model": model},
         "e2e": {"value": iters_per_s, "unit": "PNCG iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -278,7 +324,7 @@ def run_scale(args, ipc, S, prec, rsize, flush, stream, peak):
     by = stage_bytes(nv, nt, nblocks, rsize)
     roof = {}
     for stg, sid in (("mas_blocks", 2), ("forms", 3)):
-        ms = statistics.median(g.profile_replay(sid, 1, flush=flush, stream=stream) for _ in range(args.replays))
+        ms = g.profile_replay(sid, args.replays, flush=flush, stream=stream)
         roof[stg] = {"avg_us": ms * 1e3, "achieved_GBs": by[stg] / (ms / 1e3) / 1e9,
                      "frac": by[stg] / (ms / 1e3) / 1e9 / peak, "bytes_per_launch": by[stg]}
     g.close()
@@ -412,47 +458,64 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), world)
     steps_per_s, iters_per_s = whole_job_rates(total_ms, world, args.steps, iters)
 
-    # roofline of the two per-iteration HBM-bound stages (MAS block apply,
-    # H~ quadratic forms): their kernels replayed on the final state of the
-    # timed run, 256 MB written before each replay to evict L2, a CUDA event
-    # pair on the launch stream around the stage's launches only (the
-    # in-loop stage events also catch host launch gaps; reported beside)
+    # roofline. The kernel with the largest device-time share on this
+    # workload is the batched block inversion of the restarts (an ALU-bound
+    # dense factorisation; profiles/launches_sphere_pile_fp32_step15.md); the
+    # per-iteration HBM-bound stages (MAS apply with and without the
+    # Woodbury update, H~ quadratic forms) are reported beside it. Each is
+    # replayed on the final state of the timed run: reps x (256 MB L2-evicting
+    # read, stage) minus reps x (read) between CUDA events on the launch
+    # stream, divided by reps.
     peak, peak_kind = load_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clk["sm_mhz"] or 2032.0
+    alu_peak = fp32_alu_peak_tflops(sm_count, sm_mhz)
     by = stage_bytes(nv, nt, nblocks, rsize)
-    roof = {}
     if args.profile_replays:
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-    for stg, sid in (("mas_blocks", 2), ("forms", 3)):
-        # median of single-launch replays (robust to the odd slow launch)
-        avg_ms = statistics.median(scene.profile_replay(sid, 1, flush=flush, stream=stream)
-                                   for _ in range(args.replays))
-        ach = by[stg] / (avg_ms / 1e3) / 1e9
-        tr = TRAFFIC.get((stg, args.precision))
-        traffic = tr["bytes_per_block"] * nblocks if tr and stg == "mas_blocks" else (
-            tr["bytes_per_tet"] * nt if tr else None)
-        roof[stg] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                     "traffic": traffic, "bytes_per_launch": by[stg], "avg_us": avg_ms * 1e3,
-                     "timing": f"median of {args.replays} replays on the final state, 256 MB read before each (L2 evicted), CUDA events",
-                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    stage_us = {}
+    for stg, sid in (("invert", 0), ("mas_blocks", 2), ("mas_woodbury", 4), ("forms", 3)):
+        stage_us[stg] = 1e3 * scene.profile_replay(sid, args.replays, flush=flush, stream=stream)
     if args.profile_replays:
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-    dominant = "mas_blocks"
+    fl = invert_flops(nblocks)
+    roof = {
+        "invert": {"bound": "alu", "achieved": fl / (stage_us["invert"] * 1e-6) / 1e12, "peak": alu_peak,
+                   "unit": "TFLOP/s", "frac": fl / (stage_us["invert"] * 1e-6) / 1e12 / alu_peak,
+                   "traffic": None, "flops_per_launch": fl, "avg_us": stage_us["invert"],
+                   "kernel": "k_invert_tiled" if prec == ipc.IPC_PREC_FP32 else "k_invert",
+                   "peak_source": (f"FP32 FMA peak from unit counts: {sm_count} SMs x 128 lanes x 2 flops x "
+                                   f"{sm_mhz:.0f} MHz (median SM clock of the timed region)")},
+    }
+    for stg, kern in (("mas_blocks", "k_block_apply_plain"), ("mas_woodbury", "k_block_apply"),
+                      ("forms", "k_forms_all")):
+        key = "mas_blocks" if stg == "mas_woodbury" else stg
+        ach = by[key] / (stage_us[stg] * 1e-6) / 1e9
+        roof[stg] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "traffic": TRAFFIC.get((stg, args.precision)), "bytes_per_launch": by[key],
+                     "avg_us": stage_us[stg], "kernel": kern,
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    for v in roof.values():
+        v["timing"] = (f"{args.replays} replays on the final state, 256 MB read before each (L2 evicted), "
+                       "difference of two CUDA-event-timed loops")
+    dominant = "invert"
 
-    # stage breakdown: a separate profiled pass over the first timesteps (the
+    # stage breakdown: a separate profiled pass over the same timesteps (the
     # per-stage events need the kernels launched one by one, so the timed
     # loop above runs without them and with its CUDA graphs)
-    n_prof = min(args.steps, 8)
+    n_prof = args.steps
     scene.set_state(sc["x0"], sc["v0"])
     scene.profile(True)
     for _ in range(n_prof):
         scene.step(1)
     prof = scene.profile_read()
     scene.profile(False)
-    for stg in roof:
-        n = prof[stg]["launches"]
-        roof[stg]["in_loop_avg_us"] = 1e3 * prof[stg]["ms"] / n if n else None
+    for stg, src in (("mas_blocks", "mas_blocks"), ("forms", "forms"), ("invert", "restart")):
+        n = prof[src]["launches"]
+        roof[stg]["in_loop_stage_avg_us"] = 1e3 * prof[src]["ms"] / n if n else None
+        roof[stg]["in_loop_stage"] = src
         roof[stg]["in_loop_launches"] = n
 
     serving = run_serving(args, ipc, S) if args.serve > 0 and world == 1 else None
@@ -460,57 +523,69 @@ def main():
     scale = run_scale(args, ipc, S, prec, rsize, flush, stream, peak) if args.scale > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
-    # host -> device, the step runs, positions come back device -> host
+    # host -> device, the step runs, positions and velocities come back
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(np.ascontiguousarray(sc["x0"])).pin_memory()
         vh = torch.from_numpy(np.ascontiguousarray(sc["v0"])).pin_memory()
         xo = torch.empty_like(xh).pin_memory()
         n_e2e = args.steps  # the same timesteps as the device-timed loop
+        it_e2e = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(n_e2e):
             scene.set_state(xh.numpy(), vh.numpy())
-            scene.step(1)
+            it_e2e += scene.step(1)["iters"]
             xo.copy_(torch.from_numpy(scene.positions()))
             vh.copy_(torch.from_numpy(scene.velocities()))
             xh.copy_(xo)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        e2e = {"value": world * n_e2e / dt, "unit": "timesteps/s", "h2d_bytes_per_step": 2 * 3 * nv * 8,
-               "d2h_bytes_per_step": 2 * 3 * nv * 8, "steps": n_e2e}
+        e2e = {"value": world * it_e2e / dt, "unit": "PNCG iters/s", "timesteps_per_s": world * n_e2e / dt,
+               "h2d_bytes_per_step": 2 * 3 * nv * 8, "d2h_bytes_per_step": 2 * 3 * nv * 8, "steps": n_e2e}
 
     # plain form: the same timesteps in FP64 on the GPU (the method without
-    # mixed precision), compared over the first plain_steps timesteps
+    # mixed precision). Each step the FP32 form is also run, untimed, from the
+    # plain form's state, and its positions compared with the plain form's
     plain = None
-    if args.plain_steps > 0 and prec == ipc.IPC_PREC_FP32:
-        m = min(args.plain_steps, args.steps)
+    m = args.steps if args.plain_steps < 0 else min(args.plain_steps, args.steps)
+    if m > 0 and prec == ipc.IPC_PREC_FP32:
         s64 = ipc.Scene(sc, precision=ipc.IPC_PREC_FP64)
+        s32 = ipc.Scene(sc, precision=ipc.IPC_PREC_FP32)
         for _ in range(args.warmup):
             s64.step(1)
+            s32.step(1)
         s64.set_state(sc["x0"], sc["v0"])
+        bbox = s64.bbox_diag()
         q0 = [torch.cuda.Event(enable_timing=True) for _ in range(m)]
         q1 = [torch.cuda.Event(enable_timing=True) for _ in range(m)]
-        it64 = 0
+        it64, errs = 0, []
         torch.cuda.synchronize()
         for k in range(m):
+            xk, vk = s64.positions(), s64.velocities()
             flush.fill_(float(k))
             q0[k].record(stream)
             it64 += s64.step(1)["iters"]
             q1[k].record(stream)
+            s32.set_state(xk, vk)
+            s32.step(1)
+            errs.append(float(np.abs(s32.positions() - s64.positions()).max() / bbox))
         torch.cuda.synchronize()
         ms64 = sum(a.elapsed_time(b) for a, b in zip(q0, q1))
         ms32 = sum(step_ms[:m])
         it32 = sum(st["iters"] for st in status[:m])
         plain = {"precision": "fp64", "timesteps": f"0..{m - 1}",
-                 "timesteps_per_s": m / (ms64 / 1e3), "iters_per_s": it64 / (ms64 / 1e3), "iters": it64,
-                 "mixed_timesteps_per_s": m / (ms32 / 1e3), "mixed_iters_per_s": it32 / (ms32 / 1e3),
-                 "mixed_iters": it32, "speedup_timesteps": (m / (ms32 / 1e3)) / (m / (ms64 / 1e3))}
-        del s64
+                 "iters_per_s": it64 / (ms64 / 1e3), "timesteps_per_s": m / (ms64 / 1e3), "iters": it64,
+                 "mixed_iters_per_s": it32 / (ms32 / 1e3), "mixed_timesteps_per_s": m / (ms32 / 1e3),
+                 "mixed_iters": it32, "speedup_iters_per_s": (it32 / ms32) / (it64 / ms64),
+                 "speedup_timesteps": ms64 / ms32,
+                 "fp32_step_err_max": max(errs), "fp32_step_err_median": statistics.median(errs),
+                 "fp32_step_err_unit": "max_v |x_fp32 - x_fp64| / bbox diagonal, one timestep from the same state"}
+        del s64, s32
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline(sc, iters / max(args.steps, 1))
+        cpu = run_cpu_baseline(sc, args.cpu_iters)
 
     if rank != 0:
         return
@@ -519,8 +594,8 @@ def main():
     p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
     line = {
         "metric": METRIC,
-        "value": steps_per_s,
-        "unit": "timesteps/s",
+        "value": iters_per_s,
+        "unit": "PNCG iters/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -533,13 +608,16 @@ def main():
         "config": {"workload": WORKLOAD, "scene": "sphere_pile(n_balls=64, cells=8, seed=1)",
                    "precision": args.precision, "timesteps": f"0..{args.steps - 1}",
                    "l2": "flushed before every timed step (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
-        "iters_per_s": iters_per_s,
+        "timesteps_per_s": steps_per_s,
         "mean_iters_per_step": iters / args.steps,
         "p50_ms": p50,
         "p99_ms": p99,
         "converged_steps": sum(s["converged"] for s in status),
+        "plain_fp64_iters_per_s": plain["iters_per_s"] if plain else None,
+        "plain_fp64_timesteps_per_s": plain["timesteps_per_s"] if plain else None,
+        "fp32_vs_fp64_step_err_max": plain["fp32_step_err_max"] if plain else None,
         "vs_plain_fp64": plain,
-        "roofline": roof.get(dominant) if dominant else None,
+        "roofline": dict(roof[dominant], kernel=roof[dominant]["kernel"]),
         "roofline_stages": roof,
         "stage_ms": {k: v["ms"] for k, v in prof.items()},
         "stage_ms_timesteps": f"0..{n_prof - 1}, a separate profiled pass (kernels launched one by one)",
@@ -551,8 +629,6 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
-    if dominant:
-        line["roofline"]["kernel"] = dominant
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

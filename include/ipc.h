@@ -243,17 +243,23 @@ typedef struct ipc_profile {
 int ipc_profile_enable(ipc_scene* s, int enable);
 int ipc_profile_read(ipc_scene* s, ipc_profile* out);
 
-/* Replays the kernels of one stage on the scene's current state `reps`
- * times and returns their mean device time in *ms_mean: stage 2 = MAS block
- * apply of level-0 and coarse blocks to the scene's gradient (no Woodbury
- * patch), stage 3 = the H~ quadratic forms (Eq. 6) of the scene's z and p
- * (the reduction kernel; the packing of z and p before it is not timed).
- * Before each replay, if flush != NULL, flush_bytes of that caller-owned
- * device buffer (16-byte aligned) are read, which evicts the stage's data
- * from L2 without leaving dirty lines; the timed region is a CUDA
- * event pair on `stream` around the stage's launches only.  Overwrites the
- * scene's z (stage 2) and its dot-product scalars; meant for use between
- * timesteps.  IPC_ERR_INVALID for another stage or reps < 1. */
+/* Replays the kernels of one stage on the scene's current state and returns
+ * their mean device time per launch in *ms_mean.  Stages: 0 = the batched
+ * inversion of the blocks assembled at the scene's last RebuildMAS (FP32
+ * pass and FP64 redo of flagged blocks; it rewrites the same factors), 2 =
+ * MAS block apply of level-0 and coarse blocks to the scene's gradient (no
+ * Woodbury patch), 3 = the H~ quadratic forms (Eq. 6) of the scene's z and p
+ * (the reduction kernel; the packing of z and p before it is not timed), 4 =
+ * the level-0 apply with the Sparse-Input Woodbury update (Eq. 7) of the
+ * scene's current contacts against its C_base (their classification and
+ * top-K run once before, untimed).  If flush != NULL, flush_bytes of that
+ * caller-owned device buffer (16-byte aligned) are read before every launch,
+ * which evicts the stage's data from L2 without leaving dirty lines.  Two
+ * loops run on `stream`: reps x (flush, stage) and reps x (flush); the result
+ * is the difference of their CUDA-event times over reps (an event pair
+ * resolves about 2 us here).  Overwrites the scene's z (stages 2, 4) and its
+ * dot-product scalars; meant for use between timesteps.  IPC_ERR_INVALID for
+ * another stage, reps < 1, or stage 0 before any RebuildMAS. */
 int ipc_profile_replay(ipc_scene* s, int stage, int reps, void* flush, size_t flush_bytes, void* stream,
                        double* ms_mean);
 

@@ -328,7 +328,7 @@ int setup_dev(ipc_scene* s) {
     D.p = A.arr<R>(n3);
     D.zp4 = A.arr<R>(8 * (size_t)m.nv);
     D.hess = A.arr<R>((size_t)D.ntp * kH * kPack);
-    D.blocks = A.arr<R>((size_t)nb * kBlk * kBlk);
+    D.blocks = A.arr<R>((size_t)nb * kW);
     const int nb0 = m.nlev > 1 ? D.blk_off[1] : nb;
     D.asmb = A.arr<double>((size_t)nb0 * kBlk * kBlk);
     D.invflag = A.arr<int>(std::max(nb, 1));
@@ -629,7 +629,8 @@ std::string nonfinite_report(const Dev<R>& D, const Scalars& S, cudaStream_t st)
     if (cudaMalloc(&cnt, 8 * sizeof(unsigned long long)) != cudaSuccess) return "";
     cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), st);
     size_t n3 = 3 * (size_t)D.nv;
-    size_t nb = (size_t)D.blk_off[D.nlev] * kBlk * kBlk;
+    size_t nb = (size_t)D.blk_off[D.nlev] * kW;
+    const size_t nbsq = (size_t)D.blk_off[D.nlev] * kBlk * kBlk;
     KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.g, n3, cnt + 0));
     KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.z, n3, cnt + 1));
     KL(k_count_nonfinite<R><<<256, 256, 0, st>>>(D.p, n3, cnt + 2));
@@ -638,7 +639,7 @@ std::string nonfinite_report(const Dev<R>& D, const Scalars& S, cudaStream_t st)
     KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.x, n3, cnt + 5));
     const size_t nb0 = (size_t)(D.nlev > 1 ? D.blk_off[1] : D.blk_off[D.nlev]) * kBlk * kBlk;
     KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.asmb, nb0, cnt + 6));
-    if (nb > nb0) KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.asmbc, nb - nb0, cnt + 7));
+    if (nbsq > nb0) KL(k_count_nonfinite<double><<<256, 256, 0, st>>>(D.asmbc, nbsq - nb0, cnt + 7));
     unsigned long long h[8] = {0};
     cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
@@ -1205,42 +1206,55 @@ __global__ void k_touch(const uint4* __restrict__ p, size_t n, unsigned* sink) {
     if (acc == 0x9e3779b9u) *sink = acc;
 }
 
+// Replay of one stage's kernels on the scene's current state. The event pair
+// on this system resolves about 2 us, coarse against kernels of 10-200 us,
+// so two loops are timed whole: reps x (flush, preparation, stage) and reps x
+// (flush, preparation); the stage's mean device time is their difference
+// over reps (the flush evicts L2 before every launch in both).
 template <class R>
 int replay_impl(ipc_scene* s, int stage, int reps, void* flush, size_t flush_bytes, cudaStream_t st, double* ms) {
     Dev<R>& D = dev_of<R>(s);
-    cudaEvent_t a = nullptr, b = nullptr;
-    CUDA_TRY(cudaEventCreate(&a));
-    if (cudaEventCreate(&b) != cudaSuccess) {
-        cudaEventDestroy(a);
-        return fail(IPC_ERR_CUDA, "cudaEventCreate failed");
-    }
-    double tot = 0.0;
-    int rc = IPC_OK;
+    if (stage == 0 && !s->mas_built) return fail(IPC_ERR_INVALID, "replay: no blocks have been assembled yet");
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto& f : ev)
+                if (f) cudaEventDestroy(f);
+            return fail(IPC_ERR_CUDA, "cudaEventCreate failed");
+        }
     KL(k_reset_flags<R><<<1, 1, 0, st>>>(D));
-    for (int i = 0; i < reps && rc == IPC_OK; ++i) {
-        if (stage == 3) launch_forms_prep(D, false, st);  // packing and zeroing, untimed
+    if (stage == 4) launch_classify(D, D.C, st);  // the Woodbury lists of the current contacts, untimed
+    auto one = [&](bool with_stage) {
         if (flush && flush_bytes >= 16)
             KL(k_touch<<<1184, 256, 0, st>>>(static_cast<const uint4*>(flush), flush_bytes / 16,
                                              static_cast<unsigned*>(flush)));
-        cudaEventRecord(a, st);
-        if (stage == 2)
-            launch_blocks(D, D.g, D.z, D.C, false, st);
+        if (stage == 3) launch_forms_prep(D, false, st);
+        if (!with_stage) return;
+        if (stage == 0)
+            launch_invert(D, st);
+        else if (stage == 2 || stage == 4)
+            launch_blocks(D, D.g, D.z, D.C, stage == 4, st);
         else
             launch_forms_main(D, D.C, false, st);
-        cudaEventRecord(b, st);
-        float e = 0.f;
-        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&e, a, b) != cudaSuccess)
-            rc = fail(IPC_ERR_CUDA, std::string("replay: ") + cudaGetErrorString(cudaGetLastError()));
-        tot += e;
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    if (rc == IPC_OK) {
-        CUDA_TRY(cudaMemcpy(&s->hv->S.async_timeout, &D.S->async_timeout, sizeof(int), cudaMemcpyDeviceToHost));
-        if (s->hv->S.async_timeout) return fail(IPC_ERR_TIMEOUT, "replay: a bulk copy into shared memory did not complete");
-        *ms = tot / reps;
-    }
-    return rc;
+    };
+    one(true);  // warm the launch path
+    cudaEventRecord(ev[0], st);
+    for (int i = 0; i < reps; ++i) one(true);
+    cudaEventRecord(ev[1], st);
+    cudaEventRecord(ev[2], st);
+    for (int i = 0; i < reps; ++i) one(false);
+    cudaEventRecord(ev[3], st);
+    float t1 = 0.f, t0 = 0.f;
+    int rc = IPC_OK;
+    if (cudaEventSynchronize(ev[3]) != cudaSuccess || cudaEventElapsedTime(&t1, ev[0], ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t0, ev[2], ev[3]) != cudaSuccess)
+        rc = fail(IPC_ERR_CUDA, std::string("replay: ") + cudaGetErrorString(cudaGetLastError()));
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc != IPC_OK) return rc;
+    CUDA_TRY(cudaMemcpy(&s->hv->S.async_timeout, &D.S->async_timeout, sizeof(int), cudaMemcpyDeviceToHost));
+    if (s->hv->S.async_timeout) return fail(IPC_ERR_TIMEOUT, "replay: a bulk copy into shared memory did not complete");
+    *ms = std::max(0.0, (double)(t1 - t0) / reps);
+    return IPC_OK;
 }
 
 // ---- allocation-free preconditioner apply (no counterpart in the paper)
@@ -1613,7 +1627,8 @@ int ipc_eval_forms(ipc_scene* s, const double* x_base, const double* x_curr, con
 int ipc_profile_replay(ipc_scene* s, int stage, int reps, void* flush, size_t flush_bytes, void* stream,
                        double* ms_mean) {
     if (!checked(s) || !ms_mean) return fail(IPC_ERR_INVALID, "null argument");
-    if ((stage != 2 && stage != 3) || reps < 1) return fail(IPC_ERR_INVALID, "replay: stage must be 2 or 3, reps >= 1");
+    if ((stage != 0 && stage != 2 && stage != 3 && stage != 4) || reps < 1)
+        return fail(IPC_ERR_INVALID, "replay: stage must be 0, 2, 3 or 4, reps >= 1");
     cudaStream_t st = (cudaStream_t)stream;
     return s->prec == IPC_PREC_FP64 ? replay_impl<double>(s, stage, reps, flush, flush_bytes, st, ms_mean)
                                     : replay_impl<float>(s, stage, reps, flush, flush_bytes, st, ms_mean);

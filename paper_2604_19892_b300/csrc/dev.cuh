@@ -9,8 +9,9 @@
 //   contacts   structure of arrays, capacity cap, two buffers (current and
 //              trial) swapped on an accepted step, plus the restart snapshot
 //              C_base with an open-addressing key table
-//   MAS        all levels' 96x96 inverse blocks contiguous (level 0 first),
-//              R[nblocks][96][96] row-major (symmetric), assembled in double
+//   MAS        all levels' 96x96 inverses B = W'^T W' as their lower
+//              triangular factors W' packed by columns, R[nblocks][4656]
+//              (level 0 first); blocks assembled in double
 //   CCD        alpha per level-0 subdomain (double) and the straddling
 //              candidate list for the verification passes
 #pragma once
@@ -28,6 +29,16 @@ void count_launch();
 constexpr int kMaxK = 16;          // Woodbury vectors per subdomain
 constexpr int kPack = 32;          // tets per packet
 constexpr int kH = 45;             // packed symmetric 9x9
+// A subdomain block's inverse is kept as its factor W' (B = W'^T W', W'
+// lower triangular), packed by columns with 4-row alignment: column j = 4a + b
+// holds rows 4a..95 (the rows 4a..j-1 above the diagonal are zero) starting
+// at wcol(j), a multiple of 4, so 16-byte vector loads of 4 rows stay
+// aligned. 4,800 values per block (the plain triangle has 4,656).
+constexpr int kW = 4800;
+__host__ __device__ __forceinline__ int wcol(int j) {
+    const int a = j >> 2, b = j & 3;
+    return 4 * (kBlk * a - 2 * a * (a - 1)) + b * (kBlk - 4 * a);
+}
 
 // Per-scene scalars living in device memory; the host reads them once per
 // energy-check trial.
@@ -125,7 +136,7 @@ struct Dev {
     R *g, *gtry, *z, *zprev, *p;
     R* zp4;                                // [nv][2][4]: z and p packed for the forms gathers
     R* hess;                               // [ntp][45][32]
-    R* blocks;                             // nblocks * 96 * 96
+    R* blocks;                             // nblocks * kW: packed factors W' (B = W'^T W')
     double* asmb;                          // level-0 assembly buffer (FP64)
     double* asmbc;                         // coarse-level assembly buffer (FP64)
     const double* mdiag;                   // per block: mass diagonal (96 entries), fixed

@@ -12,15 +12,19 @@
 //     term whose vertices all fall in one level-l node adds nothing to that
 //     level and is skipped; mass and point-ground terms always add;
 //  3. every 96x96 block is inverted through a scaled Cholesky factorisation
-//     in register tiles (B = s W^T W s, W = L^{-1}), padded slots carry an
-//     identity;
+//     in register tiles (B = s W^T W s, W = L^{-1}) and kept as the packed
+//     lower triangular factor W' = W diag(s), B = W'^T W'; padded slots carry
+//     an identity;
 //  4. the contact set is snapshot as C_base with a key table.
 // Woodbury (non-restart iterations): each current contact is classified
 // against C_base (new / rotated: dS = k, u = sqrt(k) n; stiffer: dS = k - k_b,
 // u = sqrt(dS) n; softer: skipped); every subdomain keeps the K updates of
-// largest dS (ties by ascending key) touching it; the block apply reads B_d
-// once for [g_d, U_d], solves the K x K capacitance system in FP64 and
-// corrects z_d = B g_d - W lambda (Eq. 7).  Coarse levels stay frozen (Eq. 8).
+// largest dS (ties by ascending key) touching it; the block apply reads W'_d
+// once, forms V = W' [g_d, U_d], the K x K capacitance C = I + V_U^T V_U (=
+// I + U^T B U) and r = V_U^T V_g (= U^T B g), solves C lambda = r in FP64 and
+// returns z_d = W'^T (V_g - V_U lambda) = B g_d - B U lambda (Eq. 7).  Coarse
+// levels stay frozen (Eq. 8).
+#include <algorithm>
 #include <type_traits>
 
 #include "bulk.cuh"
@@ -580,12 +584,13 @@ __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
 // Inverse of one SPD 96x96 subdomain block, B_d = M_d^{-1} (Sec. 4.2), one
 // CTA per block. The block is scaled to a unit diagonal, S = s A s with
 // s = diag(A)^{-1/2}; S = L L^T by right-looking Cholesky; W = L^{-1}; and
-// B = s W^T W s. Each pivot is floored at eps_piv of the unit diagonal (the
-// pivot relative to the original diagonal entry) and raised where needed to
-// keep every L_rk^2 <= 1: a numerically singular block (stiff rank-1 contact
-// terms) is replaced by A plus a small non-negative diagonal shift. Forming W^T W keeps the stored inverse
-// symmetric positive semi-definite whatever the rounding, so it remains a
-// valid preconditioner when R is FP32.
+// B = s W^T W s, kept as its factor W' = W diag(s). Each pivot is floored at
+// eps_piv of the unit diagonal (the pivot relative to the original diagonal
+// entry) and raised where needed to keep every L_rk^2 <= 1: a numerically
+// singular block (stiff rank-1 contact terms) is replaced by A plus a small
+// non-negative diagonal shift. B = W'^T W' is symmetric positive
+// semi-definite whatever the rounding of W', so it remains a valid
+// preconditioner when R is FP32.
 //
 // Register tiling: the lower triangle is cut into 6x6 tiles (136 of them),
 // one per thread. Each elimination step broadcasts one column of L (or one
@@ -644,6 +649,26 @@ __device__ __forceinline__ void smem_max(float* p, float v) {
 }
 __device__ __forceinline__ void smem_max(double* p, double v) {
     atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+
+// The block's inverse B = s W^T W s is kept as W' = W diag(s) (B = W'^T W'),
+// packed by 4-row-aligned columns (wcol): warp w writes columns w, w +
+// nwarps, ... with its lanes on consecutive rows (coalesced), from W^T in
+// shared memory (wt[c * 96 + r] = W[r][c]); the rows of a column's first
+// quad above the diagonal are written as zeros. Storing the factor instead
+// of B halves the bytes of every later apply, needs no W^T W product here,
+// and keeps B positive semi-definite whatever the rounding of W'.
+template <class R, class T>
+__device__ __forceinline__ void store_factor(const Dev<R>& D, int b, const T* wt, const T* sc) {
+    R* dst = D.blocks + (size_t)b * kW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = warp; j < kBlk; j += nw) {
+        const T s = sc[j];
+        const T* col = wt + j * kBlk;
+        const int r0 = j & ~3;
+        R* out = dst + wcol(j) - r0;
+        for (int r = r0 + lane; r < kBlk; r += 32) out[r] = r >= j ? (R)(col[r] * s) : (R)0;
+    }
 }
 
 // Blocks come from the FP64 assembly (level 0: asmb, coarse levels: asmbc);
@@ -783,7 +808,7 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
             if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
     __syncthreads();
 
-    // W = L^{-1} and W^T W: tiles in row order, t = ti (ti + 1) / 2 + tj
+    // W = L^{-1}: tiles in row order, t = ti (ti + 1) / 2 + tj
     if (act) {
         int rem = t;
         ti = 0;
@@ -831,48 +856,19 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
         }
     }
     __syncthreads();
-    // W -> shared memory, row-major; tiles above the diagonal are zero
-    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
-        int r = i / kBlk, c = i % kBlk;
-        if (r / kTile < c / kTile) buf[i] = (T)0;
-    }
+    // W^T -> shared memory (buf[c * 96 + r] = W[r][c], r >= c): column j of W
+    // is then contiguous for the packed store below
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
         for (int cc = 0; cc < kTile; ++cc)
-            if (act) buf[(r0 + rr) * kBlk + c0 + cc] = a[rr][cc];
-    __syncthreads();
-
-    // ---- B = s W^T W s; tile (ti, tj) needs rows k >= 6 ti of W only
+            if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
     if (pass == 0 && flags && threadIdx.x == 0) flags[b] = s_bad;
     // the final factorisation of this block (FP64 form, or the FP64 redo)
     // modified a pivot: counted for the parity checks
     if ((pass == 1 || !flags) && threadIdx.x == 0 && s_bad && D.pivfix) atomicAdd(D.pivfix, 1);
-    if (!act) return;
-#pragma unroll
-    for (int rr = 0; rr < kTile; ++rr)
-#pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = (T)0;
-    for (int k = r0; k < kBlk; ++k) {
-        const T* Wk = buf + k * kBlk;
-        T wr[kTile], wc[kTile];
-        lds6(Wk + r0, wr);
-        lds6(Wk + c0, wc);
-#pragma unroll
-        for (int rr = 0; rr < kTile; ++rr)
-#pragma unroll
-            for (int cc = 0; cc < kTile; ++cc) a[rr][cc] += wr[rr] * wc[cc];
-    }
-    R* dst = D.blocks + (size_t)b * kBlk * kBlk;
-#pragma unroll
-    for (int rr = 0; rr < kTile; ++rr)
-#pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) {
-            int r = r0 + rr, c = c0 + cc;
-            R v = (R)(a[rr][cc] * sc[r] * sc[c]);
-            dst[r * kBlk + c] = v;
-            dst[c * kBlk + r] = v;
-        }
+    __syncthreads();
+    store_factor<R, T>(D, b, buf, sc);
 }
 
 // FP32 first pass of the block inversion, blocked by the same 6x6 tiles: per
@@ -1074,44 +1070,15 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
         }
     }
     __syncthreads();
-    // W -> shared memory, row-major; tiles above the diagonal are zero
-    for (int i = threadIdx.x; i < kBlk * kBlk; i += blockDim.x) {
-        const int r = i / kBlk, c = i % kBlk;
-        if (r / kTile < c / kTile) buf[i] = 0.f;
-    }
+    // W^T -> shared memory (every thread has finished reading L from buf)
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
         for (int cc = 0; cc < kTile; ++cc)
-            if (act) buf[(r0 + rr) * kBlk + c0 + cc] = a[rr][cc];
-    __syncthreads();
+            if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
     if (threadIdx.x == 0) flags[b] = 0;
-    if (!act) return;
-    // B = s W^T W s; tile (ti, tj) needs rows k >= 6 ti of W only
-#pragma unroll
-    for (int rr = 0; rr < kTile; ++rr)
-#pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = 0.f;
-    for (int k = r0; k < kBlk; ++k) {
-        const float* Wk = buf + k * kBlk;
-        float wr[kTile], wc[kTile];
-        lds6(Wk + r0, wr);
-        lds6(Wk + c0, wc);
-#pragma unroll
-        for (int rr = 0; rr < kTile; ++rr)
-#pragma unroll
-            for (int cc = 0; cc < kTile; ++cc) a[rr][cc] += wr[rr] * wc[cc];
-    }
-    R* dst = D.blocks + (size_t)b * kBlk * kBlk;
-#pragma unroll
-    for (int rr = 0; rr < kTile; ++rr)
-#pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) {
-            const int r = r0 + rr, c = c0 + cc;
-            const R v = (R)(a[rr][cc] * sc[r] * sc[c]);
-            dst[r * kBlk + c] = v;
-            dst[c * kBlk + r] = v;
-        }
+    __syncthreads();
+    store_factor<R, float>(D, b, buf, sc);
 }
 
 // ------------------------------------------------------ C_base snapshot
@@ -1298,90 +1265,243 @@ __global__ void k_restrict_level(Dev<R> D, int l, const R* __restrict__ src) {
     }
 }
 
+// Shared by both block applies: wait (bounded) for the block's factor; a
+// wait that runs out records the timeout in the scene's status, drains the
+// copy still in flight and makes the whole CTA leave (z stays unwritten).
+template <class R>
+__device__ __forceinline__ bool factor_arrived(const Dev<R>& D, uint64_t* bar) {
+    const bool arrived = mbar_wait(bar, 0, D.wait_polls);
+    if (__syncthreads_or(!arrived)) {
+        if (threadIdx.x == 0) {
+            D.S->async_timeout = 1;
+            mbar_wait(bar, 0, kDrainPolls);
+        }
+        return false;
+    }
+    return true;
+}
+
+// four consecutive values from shared memory (16-byte aligned for float,
+// two 16-byte loads for double)
+template <class R>
+__device__ __forceinline__ void ld4(const R* p, R v[4]) {
+    if constexpr (sizeof(R) == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], c = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = c.x;
+        v[3] = c.y;
+    }
+}
+template <class R>
+__device__ __forceinline__ void st4(R* p, const R v[4]) {
+    if constexpr (sizeof(R) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+// Y = W' X for NC columns X[a] (96 values each, shared memory) with the
+// packed factor in shared memory; 96 threads. Warp w, lane 8k + q owns row
+// quad i = 8w + q (rows 4i..4i+3) and the column chunk [24k, 24k + 24): at
+// each step the 8 lanes of a load phase read consecutive quads of one column
+// (no bank conflicts) and the columns above row 4i + 3 are skipped; the four
+// chunks' partial sums meet by shuffles.
+template <class R, int NC>
+__device__ __forceinline__ void lower_apply(const R* __restrict__ Ws, const R (*X)[kBlk], R (*Y)[kBlk], int nc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane & 7, k = lane >> 3;
+    const int i = 8 * warp + q;
+    R acc[NC][4];
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[a][r] = 0;
+    const int j0 = 24 * k, jend = min(j0 + 24, 4 * i + 4);
+    for (int j = j0; j < jend; ++j) {
+        R w[4];
+        ld4(Ws + wcol(j) + 4 * i - (j & ~3), w);
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            if (a >= nc) break;
+            const R xj = X[a][j];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[a][r] += w[r] * xj;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        if (a >= nc) break;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            acc[a][r] += __shfl_xor_sync(0xffffffffu, acc[a][r], 8);
+            acc[a][r] += __shfl_xor_sync(0xffffffffu, acc[a][r], 16);
+        }
+        if (k == 0) st4(&Y[a][4 * i], acc[a]);
+    }
+}
+
+// z = W'^T y (y in shared memory, z into shared memory); 96 threads. Each
+// round a warp takes four columns, 8 lanes per column: lane k of a column
+// handles the row quads k, k + 8, k + 16 (its quads of y stay in registers)
+// and the 8 lanes read consecutive quads of the column; a 3-step shuffle sums
+// them.
+template <class R>
+__device__ __forceinline__ void upper_apply(const R* __restrict__ Ws, const R* __restrict__ y, R* __restrict__ z) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cl = lane >> 3, k = lane & 7;
+    R yq[3][4];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) ld4(y + 4 * (k + 8 * m), yq[m]);
+#pragma unroll 2
+    for (int round = 0; round < 8; ++round) {
+        const int c = 4 * (3 * round + warp) + cl;
+        const int a = c >> 2;
+        const R* col = Ws + wcol(c) - 4 * a;
+        R acc = 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const int Q = k + 8 * m;
+            if (Q >= a) {
+                R w[4];
+                ld4(col + 4 * Q, w);
+                acc += w[0] * yq[m][0] + w[1] * yq[m][1] + w[2] * yq[m][2] + w[3] * yq[m][3];
+            }
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (k == 0) z[c] = acc;
+    }
+}
+
 // Block apply without Woodbury updates (restart iterations, coarse levels):
-// y_b = B_b r_b, one CTA of 96 threads per block. The whole 96 x 96 block
-// (36.9 KB in FP32) streams into shared memory as one bulk copy
-// (cp.async.bulk, completing on an mbarrier) while the CTA gathers r_b;
-// thread c then forms y_c = sum_j B_jc r_j from shared memory (B is
-// symmetric, column reads are conflict-free).
+// z_b = B_b r_b = W'^T (W' r_b), 96 threads per CTA. The CTAs are persistent
+// (a few per SM) and stream their blocks through a 2-stage ring in shared
+// memory: each packed factor (19.2 KB in FP32) arrives as one bulk copy
+// (cp.async.bulk, completing on its slot's mbarrier) issued two blocks ahead,
+// so the copies of later blocks overlap the gathers and products of the
+// current one and no CTA waits out a partial last wave.
+constexpr int kApplyCtasPerSm = 5;
+
 template <class R>
 __global__ void __launch_bounds__(96) k_block_apply_plain(Dev<R> D, const R* __restrict__ g, R* __restrict__ z) {
-    extern __shared__ __align__(128) unsigned char bsm[];
+    extern __shared__ __align__(128) unsigned char bsm[];  // 2 slots of kW values
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(16) R rhs[kBlk];
+    __shared__ __align__(16) R ys[kBlk];
+    constexpr uint32_t kBytes = kW * sizeof(R);
+    const int nb = D.blk_off[D.nlev];
+    const int tid = threadIdx.x;
+    const int first = blockIdx.x, stride = gridDim.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        for (int s = 0; s < 2; ++s) {
+            const int b = first + s * stride;
+            if (b < nb) {
+                mbar_arrive_expect_tx(&bar[s], kBytes);
+                bulk_g2s(bsm + s * kBytes, D.blocks + (size_t)b * kW, kBytes, &bar[s]);
+            }
+        }
+    }
+    int it = 0;
+    for (int b = first; b < nb; b += stride, ++it) {
+        const int slot = it & 1;
+        const uint32_t parity = (uint32_t)(it >> 1) & 1u;
+        const R* Ws = reinterpret_cast<const R*>(bsm + slot * kBytes);
+        int l = 0;
+        while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
+        const int grp = b - D.blk_off[l];
+        const int node = D.members[l][(size_t)grp * kSub + tid / 3];
+        const int comp = tid % 3;
+        if (l == 0)
+            rhs[tid] = node >= 0 ? g[3 * node + comp] : (R)0;
+        else
+            rhs[tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : (R)0;
+        __syncthreads();  // rhs complete; the barriers' initialisation is visible
+        const bool arrived = mbar_wait(&bar[slot], parity, D.wait_polls);
+        if (__syncthreads_or(!arrived)) {
+            // record, drain the copies still in flight (this slot's and the
+            // other slot's, if one was issued), leave z unwritten
+            if (tid == 0) {
+                D.S->async_timeout = 1;
+                mbar_wait(&bar[slot], parity, kDrainPolls);
+                if (b + stride < nb) mbar_wait(&bar[slot ^ 1], (uint32_t)((it + 1) >> 1) & 1u, kDrainPolls);
+            }
+            return;
+        }
+        lower_apply<R, 1>(Ws, &rhs, &ys, 1);
+        __syncthreads();
+        upper_apply(Ws, ys, rhs);  // rhs is free: z into it
+        __syncthreads();           // every read of this slot and of ys is done
+        const R out = rhs[tid];
+        if (tid == 0 && b + 2 * stride < nb) {
+            // reuse the slot: order the generic reads above before the copy
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[slot], kBytes);
+            bulk_g2s(bsm + slot * kBytes, D.blocks + (size_t)(b + 2 * stride) * kW, kBytes, &bar[slot]);
+        }
+        if (node >= 0) {
+            if (l == 0)
+                z[3 * node + comp] = out;
+            else
+                D.coarse_y[D.coarse_off[l] + 3 * node + comp] = out;
+        }
+        const double od = (double)out;
+        if (!(od - od == 0.0)) atomicCAS(&D.S->dbg_block, -1, b);
+        __syncthreads();  // rhs is rewritten by the next block
+    }
+}
+
+// Level-0 apply with the Sparse-Input Woodbury update (Eq. 7) and the plain
+// apply of the coarse blocks. With U_d the subdomain's top-K vectors (ns of
+// them) and V = W' [g_d, U_d]:
+//   C = I + V_U^T V_U = I + U^T B U,  r = V_U^T V_g = U^T B g,
+//   C lambda = r (FP64 Cholesky, one warp, a lane per row),
+//   z_d = W'^T (V_g - V_U lambda) = B g - B U lambda.
+// One pass of the factor over all 1 + ns columns and one transposed pass.
+template <class R>
+__global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z,
+                                                    ContactBuf C, int woodbury) {
+    extern __shared__ __align__(128) unsigned char wsm[];  // the packed factor (bulk copy)
     __shared__ __align__(8) uint64_t bar;
-    __shared__ R rhs[kBlk];
-    const R* Bs = reinterpret_cast<const R*>(bsm);
+    __shared__ __align__(16) R rhs[1 + kMaxK][kBlk];
+    __shared__ __align__(16) R V[1 + kMaxK][kBlk];
+    __shared__ __align__(16) R zs[kBlk];
+    __shared__ double cap[kMaxK][kMaxK + 1];  // C, then its factor; column kMaxK: r
+    __shared__ double rr[kMaxK];
+    __shared__ double lam[kMaxK];
+    __shared__ double qb_sh;
+    __shared__ int keep;
+    __shared__ int sel[kMaxK];
+    __shared__ int nsel;
+    const R* Ws = reinterpret_cast<const R*>(wsm);
     const int b = blockIdx.x;
     const int tid = threadIdx.x;
-    constexpr uint32_t kBytes = kBlk * kBlk * sizeof(R);
+    const int warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
+        constexpr uint32_t kBytes = kW * sizeof(R);
         mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_arrive_expect_tx(&bar, kBytes);
-        bulk_g2s(bsm, D.blocks + (size_t)b * kBlk * kBlk, kBytes, &bar);
+        bulk_g2s(wsm, D.blocks + (size_t)b * kW, kBytes, &bar);
     }
     int l = 0;
     while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
     const int grp = b - D.blk_off[l];
-    const int node = D.members[l][(size_t)grp * kSub + tid / 3];
-    const int comp = tid % 3;
-    if (l == 0)
-        rhs[tid] = node >= 0 ? g[3 * node + comp] : (R)0;
-    else
-        rhs[tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : (R)0;
-    __syncthreads();  // rhs complete; the barrier's initialisation is visible
-    const bool arrived = mbar_wait(&bar, 0, D.wait_polls);
-    if (__syncthreads_or(!arrived)) {
-        // record, wait (bounded) for the copy in flight, leave z unwritten
-        if (tid == 0) {
-            D.S->async_timeout = 1;
-            mbar_wait(&bar, 0, kDrainPolls);
-        }
-        return;
-    }
-    R acc0 = 0, acc1 = 0;
-#pragma unroll 8
-    for (int j = 0; j < kBlk; j += 2) {
-        acc0 += Bs[j * kBlk + tid] * rhs[j];
-        acc1 += Bs[(j + 1) * kBlk + tid] * rhs[j + 1];
-    }
-    const R out = acc0 + acc1;
-    if (node >= 0) {
-        if (l == 0)
-            z[3 * node + comp] = out;
-        else
-            D.coarse_y[D.coarse_off[l] + 3 * node + comp] = out;
-    }
-    double od = (double)out;
-    if (!(od - od == 0.0)) atomicCAS(&D.S->dbg_block, -1, b);
-}
-
-template <class R>
-__global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z,
-                                                    ContactBuf C, int woodbury) {
-    extern __shared__ __align__(128) unsigned char wsm[];  // the 96x96 block (bulk copy)
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ R rhs[1 + kMaxK][kBlk];
-    __shared__ R Y[1 + kMaxK][kBlk];
-    __shared__ double cap[kMaxK][kMaxK + 1];
-    __shared__ double lam[kMaxK];
-    __shared__ int sel[kMaxK];
-    __shared__ int nsel;
-    const R* Bs = reinterpret_cast<const R*>(wsm);
-    int b = blockIdx.x;
-    if (threadIdx.x == 0) {
-        constexpr uint32_t kBytes = kBlk * kBlk * sizeof(R);
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        mbar_arrive_expect_tx(&bar, kBytes);
-        bulk_g2s(wsm, D.blocks + (size_t)b * kBlk * kBlk, kBytes, &bar);
-    }
-    int l = 0;
-    while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
-    int grp = b - D.blk_off[l];
-    int tid = threadIdx.x;
     const int* mem = D.members[l] + (size_t)grp * kSub;
-    int node = mem[tid / 3];
-    int comp = tid % 3;
+    const int node = mem[tid / 3];
+    const int comp = tid % 3;
     if (l == 0)
         rhs[0][tid] = node >= 0 ? g[3 * node + comp] : (R)0;
     else
@@ -1390,81 +1510,48 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
         int n = 0;
         if (l == 0 && woodbury)
             for (int a = 0; a < D.K; ++a) {
-                int u = D.topk[(size_t)grp * D.K + a];
+                const int u = D.topk[(size_t)grp * D.K + a];
                 if (u < 0) break;
                 sel[n++] = u;
             }
         nsel = n;
     }
     __syncthreads();
-    int ns = nsel;
+    const int ns = nsel;
     for (int a = 0; a < ns; ++a) rhs[1 + a][tid] = (R)0;
     __syncthreads();
-    if (tid < ns) {  // build column tid of U_d: u = sqrt(dS) w_j r at slot of vertex j
-        int u = sel[tid];
-        int i = D.upd_c[u];
-        double sc = sqrt(D.upd_dS[u]);
-        int4 q = C.v[i];
-        int vid[4] = {q.x, q.y, q.z, q.w};
-        int nvv = C.type[i] == 2 ? 1 : 4;
+    if (tid < ns) {  // column tid of U_d: u = sqrt(dS) w_j r at the slot of vertex j
+        const int u = sel[tid];
+        const int i = D.upd_c[u];
+        const double sq = sqrt(D.upd_dS[u]);
+        const int4 q = C.v[i];
+        const int vid[4] = {q.x, q.y, q.z, q.w};
+        const int nvv = C.type[i] == 2 ? 1 : 4;
         for (int j = 0; j < nvv; ++j) {
             if (D.grp0[vid[j]] != grp) continue;
-            int s = D.slot0[vid[j]];
-            double wj = sc * C.w[4 * i + j];
+            const int s = D.slot0[vid[j]];
+            const double wj = sq * C.w[4 * i + j];
             for (int r = 0; r < 3; ++r) rhs[1 + tid][3 * s + r] += (R)(wj * C.r[3 * i + r]);
         }
     }
     __syncthreads();
-    // Y = B [rhs] from the staged block; B is symmetric, so thread c reads
-    // column c (consecutive threads, consecutive words) and forms row c of Y
-    const bool arrived = mbar_wait(&bar, 0, D.wait_polls);
-    if (__syncthreads_or(!arrived)) {
-        // record, wait (bounded) for the copy in flight, leave z unwritten
-        if (tid == 0) {
-            D.S->async_timeout = 1;
-            mbar_wait(&bar, 0, kDrainPolls);
-        }
-        return;
-    }
-    {
-        R acc[1 + kMaxK];
-#pragma unroll
-        for (int a = 0; a < 1 + kMaxK; ++a) acc[a] = 0;
-        if (ns == 0) {
-            R a0 = 0, a1 = 0;
-#pragma unroll 8
-            for (int j = 0; j < kBlk; j += 2) {
-                a0 += Bs[j * kBlk + tid] * rhs[0][j];
-                a1 += Bs[(j + 1) * kBlk + tid] * rhs[0][j + 1];
-            }
-            acc[0] = a0 + a1;
-        } else {
-#pragma unroll 2
-            for (int j = 0; j < kBlk; ++j) {
-                const R e = Bs[j * kBlk + tid];
-#pragma unroll
-                for (int a = 0; a < 1 + kMaxK; ++a)
-                    if (a <= ns) acc[a] += e * rhs[a][j];
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < 1 + kMaxK; ++a)
-            if (a <= ns) Y[a][tid] = acc[a];
-    }
+    if (!factor_arrived(D, &bar)) return;
+    // V = W' [rhs]: one read of each factor entry for all 1 + ns columns
+    if (ns == 0)
+        lower_apply<R, 1>(Ws, rhs, V, 1);
+    else
+        lower_apply<R, 1 + kMaxK>(Ws, rhs, V, 1 + ns);
     __syncthreads();
-    R out = Y[0][tid];
     if (ns > 0) {
-        // capacitance I + U^T W (symmetric: the half a <= c) and r = U^T z_base.
-        // U and W = B U hold bulk-precision values, so the products are summed
-        // in R per warp and the warp totals enter the FP64 solve (FP64
-        // products would add no accuracy here, and B300 runs FP64 at a small
-        // fraction of its FP32 rate: these dot products were most of the
-        // kernel's time)
-        int warp = tid >> 5, lane = tid & 31;
+        // C = I + V_U^T V_U (the half a <= c), r = V_U^T V_g and |V_g|^2: dot
+        // products of bulk-precision vectors summed in R per warp, the warp
+        // totals in FP64 (FP64 products would add no accuracy to FP32 values,
+        // and this GPU runs FP64 at a small fraction of its FP32 rate)
         const int nsym = ns * (ns + 1) / 2;
-        for (int e = warp; e < nsym + ns; e += 3) {
-            int a, c;
-            const R* wv;
+        for (int e = warp; e < nsym + ns + 1; e += 3) {
+            const R* va;
+            const R* vb;
+            int a = -1, c = -1;
             if (e < nsym) {
                 a = 0;
                 int rem = e;
@@ -1473,85 +1560,91 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
                     ++a;
                 }
                 c = a + rem;
-                wv = Y[1 + c];
-            } else {
+                va = V[1 + a];
+                vb = V[1 + c];
+            } else if (e < nsym + ns) {
                 a = e - nsym;
-                c = -1;
-                wv = Y[0];
+                va = V[1 + a];
+                vb = V[0];
+            } else {
+                va = V[0];
+                vb = V[0];
             }
-            R s = 0;
-            for (int i = lane; i < kBlk; i += 32) s += rhs[1 + a][i] * wv[i];
-            s = warp_sum(s);
+            R sacc = 0;
+            for (int i = lane; i < kBlk; i += 32) sacc += va[i] * vb[i];
+            sacc = warp_sum(sacc);
             if (lane == 0) {
                 if (c >= 0) {
-                    cap[a][c] = (double)s + (a == c ? 1.0 : 0.0);
+                    cap[a][c] = (double)sacc + (a == c ? 1.0 : 0.0);
                     cap[c][a] = cap[a][c];
+                } else if (a >= 0) {
+                    rr[a] = (double)sacc;
                 } else {
-                    cap[a][kMaxK] = (double)s;
+                    qb_sh = (double)sacc;
                 }
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            // Cholesky solve of the SPD capacitance system, in place in cap
-            // (L below the diagonal, 1 / L_jj on it): one reciprocal square
-            // root per column and no divisions, since the serial FP64 chain
-            // of this thread holds up the whole CTA.
-            // C = I + U^T B U is >= I in exact arithmetic, so every pivot is
-            // >= 1; a pivot below 1/2 means B's rounding swamped a stiff
-            // update direction and the correction is dropped (z_d = B g_d)
+        if (warp == 0) {
+            // Cholesky of the SPD capacitance system by one warp, lane i holding
+            // row i: per column one reciprocal square root and a trailing
+            // update of the rows below. C = I + U^T B U >= I in exact
+            // arithmetic, so every pivot is >= 1; a pivot below 1/2 means B's
+            // rounding swamped a stiff update direction, and the correction is
+            // dropped (z_d = B g_d)
             bool good = true;
             for (int j = 0; j < ns; ++j) {
-                double d = cap[j][j];
-                for (int k = 0; k < j; ++k) d -= cap[j][k] * cap[j][k];
+                const double d = cap[j][j];
                 good = good && (d >= 0.5);
                 const double il = rsqrt(fmax(d, 0.5));
-                cap[j][j] = il;
-                for (int i = j + 1; i < ns; ++i) {
-                    double t = cap[i][j];
-                    for (int k = 0; k < j; ++k) t -= cap[i][k] * cap[j][k];
-                    cap[i][j] = t * il;
+                __syncwarp();
+                if (lane > j && lane < ns) cap[lane][j] *= il;
+                __syncwarp();
+                if (lane > j && lane < ns) {
+                    const double lij = cap[lane][j];
+                    for (int k = j + 1; k <= lane; ++k) cap[lane][k] -= lij * cap[k][j];
                 }
+                if (lane == j) cap[j][j] = il;  // 1 / L_jj
+                __syncwarp();
             }
-            double y[kMaxK];
-            for (int i = 0; i < ns; ++i) {
-                double t = cap[i][kMaxK];
-                for (int k = 0; k < i; ++k) t -= cap[i][k] * y[k];
-                y[i] = t * cap[i][i];
+            // L y = r, then L^T lambda = y: lane i keeps the running value of
+            // row i; each step broadcasts one solved entry
+            double t = lane < ns ? rr[lane] : 0.0;
+            for (int j = 0; j < ns; ++j) {
+                const double yj = __shfl_sync(0xffffffffu, t * cap[j < 32 ? j : 0][j], j);
+                if (lane == j) t = yj;
+                if (lane > j && lane < ns) t -= cap[lane][j] * yj;
             }
-            for (int i = ns - 1; i >= 0; --i) {
-                double t = y[i];
-                for (int k = i + 1; k < ns; ++k) t -= cap[k][i] * lam[k];
-                lam[i] = t * cap[i][i];
+            for (int j = ns - 1; j >= 0; --j) {
+                const double lj = __shfl_sync(0xffffffffu, t * cap[j][j], j);
+                if (lane == j) t = lj;
+                if (lane < j) t -= cap[j][lane] * lj;
             }
-            // a non-finite capacitance solution (overflowing contact
-            // stiffness) drops this subdomain's correction: z_d = B g_d
-            bool ok = good;
-            for (int i = 0; i < ns; ++i) ok = ok && (lam[i] - lam[i] == 0.0);
-            if (!ok)
-                for (int i = 0; i < ns; ++i) lam[i] = 0.0;
+            // g^T B~ g = |V_g|^2 - r^T lambda must lie in [0, g^T B g]
+            // (adding U U^T only lowers the quadratic form); outside that range
+            // (FP32 factors of stiff blocks make the solve unstable), or with a
+            // non-finite lambda, the correction is dropped
+            double rl = lane < ns ? rr[lane] * t : 0.0;
+            bool fin = lane < ns ? (t - t == 0.0) : true;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) rl += __shfl_xor_sync(0xffffffffu, rl, o);
+            fin = __all_sync(0xffffffffu, fin);
+            const double qb = qb_sh, qc = qb - rl;
+            const bool ok = good && fin && qc <= qb * (1.0 + 1e-3) && qc >= -1e-3 * qb;
+            if (lane < ns) lam[lane] = ok ? t : 0.0;
+            if (lane == 0) keep = ok;
         }
         __syncthreads();
-        double o = (double)out;
-        for (int a = 0; a < ns; ++a) o -= lam[a] * (double)Y[1 + a][tid];
-        // Adding U U^T can only lower the quadratic form: 0 <= g_d^T B~ g_d
-        // <= g_d^T B g_d. A corrected z_d outside that range (FP32 inverses
-        // of stiff blocks make the capacitance solve unstable) drops this
-        // subdomain's correction.
-        // (summed in R per warp: the test's tolerance is 1e-3 of qb)
-        const R gi = rhs[0][tid];
-        double qb = (double)warp_sum(gi * Y[0][tid]), qc = (double)warp_sum(gi * (R)o);
-        __shared__ double qsum[2][3];
-        if ((tid & 31) == 0) {
-            qsum[0][tid >> 5] = qb;
-            qsum[1][tid >> 5] = qc;
-        }
+        double o = (double)V[0][tid];
+        if (keep)
+            for (int a = 0; a < ns; ++a) o -= lam[a] * (double)V[1 + a][tid];
         __syncthreads();
-        qb = qsum[0][0] + qsum[0][1] + qsum[0][2];
-        qc = qsum[1][0] + qsum[1][1] + qsum[1][2];
-        const bool in_range = qc <= qb * (1.0 + 1e-3) && qc >= -1e-3 * qb;
-        out = in_range ? (R)o : Y[0][tid];
+        V[0][tid] = (R)o;
     }
+    __syncthreads();
+    upper_apply(Ws, V[0], zs);
+    __syncthreads();
+    const R out = zs[tid];
     if (node >= 0) {
         if (l == 0)
             z[3 * node + comp] = out;
@@ -1559,24 +1652,8 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
             D.coarse_y[D.coarse_off[l] + 3 * node + comp] = out;
     }
     // diagnostics: record the first block whose output is not finite
-    double od = (double)out;
-    if (!(od - od == 0.0) && atomicCAS(&D.S->dbg_block, -1, b) == -1) {
-        double rm = 0, ym = 0, lm = 0, dm = 0;
-        for (int a = 0; a <= ns; ++a)
-            for (int i = 0; i < kBlk; ++i) {
-                rm = fmax(rm, fabs((double)rhs[a][i]));
-                ym = fmax(ym, fabs((double)Y[a][i]));
-            }
-        for (int a = 0; a < ns; ++a) {
-            lm = fmax(lm, fabs(lam[a]));
-            dm = fmax(dm, D.upd_dS[sel[a]]);
-        }
-        D.S->dbg_ns = ns;
-        D.S->dbg_rhs = rm;
-        D.S->dbg_y = ym;
-        D.S->dbg_lam = lm;
-        D.S->dbg_ds = dm;
-    }
+    const double od = (double)out;
+    if (!(od - od == 0.0) && atomicCAS(&D.S->dbg_block, -1, b) == -1) D.S->dbg_ns = ns;
 }
 
 template <class R>
@@ -1616,6 +1693,14 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
         KL(k_asm_sum<R><<<nblk(32LL * D.nitem, 256), 256, 0, st>>>(D));
     }
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
+    launch_invert(D, st);
+    cudaMemsetAsync(D.bkeys, 0xFF, sizeof(unsigned long long) * D.btab, st);
+    KL(k_snapshot<R><<<592, kT, 0, st>>>(D));
+}
+
+template <class R>
+void launch_invert(const Dev<R>& D, cudaStream_t st) {
+    const int nb = D.blk_off[D.nlev];
     // blocks are assembled in FP64 and inverted in the bulk precision R (FP32
     // in the mixed mode: B300's FP64 rate, about two FMAs per clock per SM,
     // would make the inversion the most expensive step) with an FP64 redo of
@@ -1638,8 +1723,6 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
     } else {
         KL(k_invert<R, R><<<nb, kInvThreads, smem_r, st>>>(D, nullptr, 0));
     }
-    cudaMemsetAsync(D.bkeys, 0xFF, sizeof(unsigned long long) * D.btab, st);
-    KL(k_snapshot<R><<<592, kT, 0, st>>>(D));
 }
 
 template <class R>
@@ -1664,18 +1747,24 @@ void launch_restrict(const Dev<R>& D, const R* g, cudaStream_t st) {
 
 template <class R>
 void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool woodbury, cudaStream_t st) {
-    static const bool attr = [] {  // once per process, thread-safe
+    static const int sms = [] {  // once per process, thread-safe
         cudaFuncSetAttribute(k_block_apply_plain<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kBlk * kBlk * sizeof(R)));
-        cudaFuncSetAttribute(k_block_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kBlk * kBlk * sizeof(R)));
-        return true;
+                             (int)(2 * kW * sizeof(R)));
+        cudaFuncSetAttribute(k_block_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kW * sizeof(R)));
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 148;
     }();
-    (void)attr;
-    if (woodbury)
-        KL(k_block_apply<R><<<D.blk_off[D.nlev], 96, kBlk * kBlk * sizeof(R), st>>>(D, g, z, C, 1));
-    else
-        KL(k_block_apply_plain<R><<<D.blk_off[D.nlev], 96, kBlk * kBlk * sizeof(R), st>>>(D, g, z));
+    const int nb = D.blk_off[D.nlev];
+    if (woodbury) {
+        KL(k_block_apply<R><<<nb, 96, kW * sizeof(R), st>>>(D, g, z, C, 1));
+    } else {
+        // persistent CTAs: as many as fit at once (two FP64 rings per SM, five
+        // FP32), never more than the blocks
+        const int per_sm = sizeof(R) == 8 ? 2 : kApplyCtasPerSm;
+        KL(k_block_apply_plain<R><<<std::min(nb, per_sm * sms), 96, 2 * kW * sizeof(R), st>>>(D, g, z));
+    }
 }
 
 template <class R>
@@ -1692,6 +1781,7 @@ void launch_precond(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool
 
 #define INST(R)                                                                                            \
     template void launch_restart<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t);         \
+    template void launch_invert<R>(const Dev<R>&, cudaStream_t);                                          \
     template void launch_classify<R>(const Dev<R>&, const ContactBuf&, cudaStream_t);                     \
     template void launch_precond<R>(const Dev<R>&, const R*, R*, const ContactBuf&, bool, cudaStream_t);   \
     template void launch_restrict<R>(const Dev<R>&, const R*, cudaStream_t);                              \

@@ -22,6 +22,8 @@ template <class R> void launch_detect(const Dev<R>& D, const double* x, const Co
 // RebuildMAS at x with contacts C: projected tet Hessians, level blocks,
 // batched inversion, C_base snapshot
 template <class R> void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st);
+// the batched inversion of the assembled blocks alone (part of launch_restart)
+template <class R> void launch_invert(const Dev<R>& D, cudaStream_t st);
 // classify C against C_base, per-subdomain top-K (Sec. 4.1.1)
 template <class R> void launch_classify(const Dev<R>& D, const ContactBuf& C, cudaStream_t st);
 // z = P g with optional Woodbury update (Eq. 7-8)

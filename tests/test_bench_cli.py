@@ -23,5 +23,7 @@ def test_bench_reference_line():
               "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "impl"):
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] > 0
+    # the same unit as the GPU arm's value, so that the two can be divided
+    assert line["unit"] == "PNCG iters/s" and line["cpu_baseline"]["unit"] == "PNCG iters/s"
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
