@@ -613,6 +613,7 @@ def main():
         "p50_ms": p50,
         "p99_ms": p99,
         "converged_steps": sum(s["converged"] for s in status),
+        "fp64_redo_blocks_last_restart": scene.fp64_blocks() if prec == ipc.IPC_PREC_FP32 else None,
         "plain_fp64_iters_per_s": plain["iters_per_s"] if plain else None,
         "plain_fp64_timesteps_per_s": plain["timesteps_per_s"] if plain else None,
         "fp32_vs_fp64_step_err_max": plain["fp32_step_err_max"] if plain else None,

@@ -28,7 +28,7 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(f) <= t for f in srcs + hdrs):
             return _LIB_PATH
     cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-Wall", "-Wno-unused-function",
-           "-fno-fast-math", "-ffp-contract=off", "-o", _LIB_PATH + ".tmp"] + srcs + ["-lm"]
+           "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-o", _LIB_PATH + ".tmp"] + srcs + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
     return _LIB_PATH
@@ -106,6 +106,7 @@ def _lib_handle():
             "o_chol_inverse": (C.c_int, [C.c_int, _D, _D]),
             "o_chol_floors": (C.c_longlong, [C.c_int]),
             "o_energy_tolerance": (C.c_double, [C.c_void_p, C.c_double]),
+            "o_set_threads": (C.c_int, [C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -422,3 +423,9 @@ def chol_inverse(A):
 def chol_floors(reset=False):
     """Pivots floored by every oracle Cholesky since the last reset."""
     return int(_lib_handle().o_chol_floors(1 if reset else 0))
+
+
+def set_threads(n):
+    """Host threads for the oracle's independent loops (0: query); returns the
+    number now used.  Results do not depend on it."""
+    return int(_lib_handle().o_set_threads(int(n)))

