@@ -899,10 +899,51 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
     const int* mem = D.members[l] + (size_t)grp * kSub;
     const double* src = l == 0 ? D.asmb + (size_t)b * kBlk * kBlk
                                : D.asmbc + (size_t)(b - D.blk_off[1]) * kBlk * kBlk;
+    __shared__ unsigned char pad[kBlk];  // padded slot (no node)
     if (threadIdx.x == 0) s_bad = 0;
     for (int r = threadIdx.x; r < kBlk; r += blockDim.x) {
         const double d = src[r * kBlk + r];
-        sc[r] = (mem[r / 3] < 0 || !(d > 0.0)) ? 1.f : (float)(1.0 / sqrt(d));
+        const bool pr = mem[r / 3] < 0;
+        pad[r] = pr ? 1 : 0;
+        sc[r] = (pr || !(d > 0.0)) ? 1.f : (float)(1.0 / sqrt(d));
+    }
+    __syncthreads();
+    // the scaled block staged in buf (row-major), a warp per row and a lane
+    // per column so the FP64 reads coalesce; 4 rows per pass keep 12
+    // independent loads in flight per lane. Entries above the diagonal inside
+    // the diagonal 6 x 6 tiles are zero; padded slots carry an identity.
+    {
+        constexpr int kRows = 4;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int r0 = warp * kRows; r0 < kBlk; r0 += nw * kRows) {
+            double v[kRows][3];
+#pragma unroll
+            for (int q = 0; q < kRows; ++q)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const int r = r0 + q, c = lane + 32 * m;
+                    v[q][m] = (r < kBlk && c <= r) ? src[r * kBlk + c] : 0.0;
+                }
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int r = r0 + q;
+                if (r >= kBlk) break;
+                const int cend = (r / kTile + 1) * kTile;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const int c = lane + 32 * m;
+                    if (c >= cend) continue;
+                    float f;
+                    if (c > r)
+                        f = 0.f;
+                    else if (pad[r] || pad[c])
+                        f = (r == c) ? 1.f : 0.f;
+                    else
+                        f = scaled_f32(v[q][m], sc[r], sc[c]);
+                    buf[r * kBlk + c] = f;
+                }
+            }
+        }
     }
     // Cholesky: tiles ordered by column from the right, as in k_invert
     const int t = threadIdx.x;
@@ -923,17 +964,8 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) {
-            const int r = r0 + rr, c = c0 + cc;
-            float v = 0.f;
-            if (act) {
-                if (mem[r / 3] < 0 || mem[c / 3] < 0)
-                    v = (r == c) ? 1.f : 0.f;
-                else
-                    v = scaled_f32(src[r * kBlk + c], sc[r], sc[c]);
-            }
-            a[rr][cc] = v;
-        }
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = act ? buf[(r0 + rr) * kBlk + c0 + cc] : 0.f;
+    __syncthreads();  // buf is reused for L^T below
     bool bad = false;
     for (int kt = 0; kt < kNT; ++kt) {
         float* P = pan + (kt & 1) * (kTile * kBlk);  // P[m * 96 + row] = L[row][6 kt + m]
