@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"])
+    ap.add_argument("--bf16-steps", type=int, default=-1,
+                    help="timesteps of the BF16-factor form (IPC_PREC_BF16_MAS) beside the main one (-1 = --steps, 0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=-1,
@@ -278,6 +280,44 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bf16(args, ipc, S, m, flush, stream, peak, warmup):
+    """The same timesteps with the block factors in BF16 (IPC_PREC_BF16_MAS:
+    tensor-core block products, FP32 accumulation), device-timed like the main
+    loop, and its block applies replayed for their roofline."""
+    import torch
+    sc = S.sphere_pile()
+    g = ipc.Scene(sc, precision=ipc.IPC_PREC_BF16_MAS)
+    for _ in range(warmup):
+        g.step(1)
+    g.set_state(sc["x0"], sc["v0"])
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(m)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(m)]
+    its, conv = 0, 0
+    torch.cuda.synchronize()
+    for k in range(m):
+        flush.fill_(float(k))
+        e0[k].record(stream)
+        st = g.step(1)
+        e1[k].record(stream)
+        its += st["iters"]
+        conv += st["converged"]
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1))
+    nv = sc["x0"].shape[0]
+    nblocks = sum(int(q.max()) + 1 for q, _ in g.levels())
+    byts = nblocks * (96 * 97 // 2) * 2 + 2 * 3 * nv * 4
+    roof = {}
+    for stg, sid, kern in (("mas_blocks", 2, "k_block_apply_plain16"), ("mas_woodbury", 4, "k_block_apply<float, true>")):
+        us = 1e3 * g.profile_replay(sid, args.replays, flush=flush, stream=stream)
+        ach = byts / (us * 1e-6) / 1e9
+        roof[stg] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                     "bytes_per_launch": byts, "avg_us": us, "kernel": kern}
+    g.close()
+    return {"precision": "bf16 block factors, fp32 bulk", "timesteps": f"0..{m - 1}", "iters_per_s": its / (ms / 1e3),
+            "timesteps_per_s": m / (ms / 1e3), "mean_iters_per_step": its / m, "converged_steps": conv,
+            "roofline_stages": roof}
+
+
 def run_ablation(args, ipc, S, prec):
     """The paper's ablations on the same kernels: MAS maintenance (Woodbury
     updates, full rebuild every iteration, frozen between restarts) and the
@@ -413,8 +453,8 @@ def main():
     from paper_2604_19892_b300 import scenes as S
     build.build()
     ipc.load()
-    prec = ipc.IPC_PREC_FP32 if args.precision == "fp32" else ipc.IPC_PREC_FP64
-    rsize = 4 if prec == ipc.IPC_PREC_FP32 else 8
+    prec = {"fp32": ipc.IPC_PREC_FP32, "fp64": ipc.IPC_PREC_FP64, "bf16": ipc.IPC_PREC_BF16_MAS}[args.precision]
+    rsize = 8 if prec == ipc.IPC_PREC_FP64 else 4
     sc = S.sphere_pile()
     scene = ipc.Scene(sc, precision=prec)
     nv, nt = sc["x0"].shape[0], sc["tets"].shape[0]
@@ -583,6 +623,11 @@ def main():
                  "fp32_step_err_unit": "max_v |x_fp32 - x_fp64| / bbox diagonal, one timestep from the same state"}
         del s64, s32
 
+    bf16 = None
+    mb = args.steps if args.bf16_steps < 0 else min(args.bf16_steps, args.steps)
+    if mb > 0 and world == 1 and prec == ipc.IPC_PREC_FP32:
+        bf16 = run_bf16(args, ipc, S, mb, flush, stream, peak, args.warmup)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(sc, args.cpu_iters)
@@ -603,7 +648,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if prec == ipc.IPC_PREC_FP32 else "f64",
+        "dtype": "f64" if prec == ipc.IPC_PREC_FP64 else "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "scene": "sphere_pile(n_balls=64, cells=8, seed=1)",
                    "precision": args.precision, "timesteps": f"0..{args.steps - 1}",
@@ -618,6 +663,7 @@ def main():
         "plain_fp64_timesteps_per_s": plain["timesteps_per_s"] if plain else None,
         "fp32_vs_fp64_step_err_max": plain["fp32_step_err_max"] if plain else None,
         "vs_plain_fp64": plain,
+        "bf16_mas": bf16,
         "roofline": dict(roof[dominant], kernel=roof[dominant]["kernel"]),
         "roofline_stages": roof,
         "stage_ms": {k: v["ms"] for k, v in prof.items()},

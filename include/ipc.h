@@ -55,10 +55,15 @@ typedef enum ipc_status {
 
 typedef enum ipc_precision {
     IPC_PREC_FP64 = 0,       /* every quantity in FP64 (the plain method) */
-    IPC_PREC_FP32 = 1        /* FP32 bulk (gradient, H v, MAS blocks and
+    IPC_PREC_FP32 = 1,       /* FP32 bulk (gradient, H v, MAS blocks and
                                 products); FP64 for positions, barrier
                                 distances, CCD, the 2x2 and capacitance
                                 solves and all reductions */
+    IPC_PREC_BF16_MAS = 2    /* as IPC_PREC_FP32, with the MAS block factors
+                                W' (B = W'^T W') stored in BF16 and applied
+                                on the tensor cores (BF16 products, FP32
+                                accumulation; the right-hand sides split into
+                                BF16 high and low parts) */
 } ipc_precision;
 
 /* Scene description (host memory, copied at create). */

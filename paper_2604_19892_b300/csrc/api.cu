@@ -329,6 +329,7 @@ int setup_dev(ipc_scene* s) {
     D.zp4 = A.arr<R>(8 * (size_t)m.nv);
     D.hess = A.arr<R>((size_t)D.ntp * kH * kPack);
     D.blocks = A.arr<R>((size_t)nb * kW);
+    D.blocks16 = p.precision == IPC_PREC_BF16_MAS ? A.get((size_t)nb * kW16 * 2) : nullptr;
     const int nb0 = m.nlev > 1 ? D.blk_off[1] : nb;
     D.asmb = A.arr<double>((size_t)nb0 * kBlk * kBlk);
     D.invflag = A.arr<int>(std::max(nb, 1));
@@ -1384,7 +1385,9 @@ int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params, const
     *out = nullptr;
     if (!(params->h > 0) || !(params->dhat > 0) || !(params->kappa > 0) || params->K < 0 || params->K > kMaxK ||
         params->iter_max <= 0 || params->levels_max < 1 || params->ls_max < 0 ||
-        (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_FP32) || params->broad_phase < 0 ||
+        (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_FP32 &&
+         params->precision != IPC_PREC_BF16_MAS) ||
+        params->broad_phase < 0 ||
         params->broad_phase > 2)
         return fail(IPC_ERR_INVALID, "invalid parameters");
     ipc_scene* s = new ipc_scene();

@@ -35,6 +35,12 @@ constexpr int kH = 45;             // packed symmetric 9x9
 // at wcol(j), a multiple of 4, so 16-byte vector loads of 4 rows stay
 // aligned. 4,800 values per block (the plain triangle has 4,656).
 constexpr int kW = 4800;
+// BF16 factor storage (IPC_PREC_BF16_MAS): W' as its 21 lower 16 x 16 tiles,
+// tile (i, j), i >= j, at index i (i + 1) / 2 + j, each row-major (the
+// upper half of a diagonal tile is zero): 5,376 values, 10,752 bytes
+constexpr int kT16 = 16;
+constexpr int kNT16 = kBlk / kT16;
+constexpr int kW16 = kNT16 * (kNT16 + 1) / 2 * kT16 * kT16;
 __host__ __device__ __forceinline__ int wcol(int j) {
     const int a = j >> 2, b = j & 3;
     return 4 * (kBlk * a - 2 * a * (a - 1)) + b * (kBlk - 4 * a);
@@ -137,6 +143,7 @@ struct Dev {
     R* zp4;                                // [nv][2][4]: z and p packed for the forms gathers
     R* hess;                               // [ntp][45][32]
     R* blocks;                             // nblocks * kW: packed factors W' (B = W'^T W')
+    void* blocks16;                        // BF16 factors (nblocks * kW16 bf16), or null: FP32 / FP64 factors in blocks
     double* asmb;                          // level-0 assembly buffer (FP64)
     double* asmbc;                         // coarse-level assembly buffer (FP64)
     const double* mdiag;                   // per block: mass diagonal (96 entries), fixed

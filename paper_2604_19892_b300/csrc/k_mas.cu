@@ -27,6 +27,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "bulk.cuh"
 #include "kernels.h"
 
@@ -660,6 +662,21 @@ __device__ __forceinline__ void smem_max(double* p, double v) {
 // and keeps B positive semi-definite whatever the rounding of W'.
 template <class R, class T>
 __device__ __forceinline__ void store_factor(const Dev<R>& D, int b, const T* wt, const T* sc) {
+    if (D.blocks16) {
+        // BF16 tiles (IPC_PREC_BF16_MAS): tile (i, j) row-major, written in
+        // order so the global stores coalesce (the column reads of W^T take
+        // bank conflicts: a one-time cost per restart)
+        __nv_bfloat16* d16 = static_cast<__nv_bfloat16*>(D.blocks16) + (size_t)b * kW16;
+        for (int e = threadIdx.x; e < kW16; e += blockDim.x) {
+            const int tix = e >> 8;
+            int ti = 0;
+            while ((ti + 1) * (ti + 2) / 2 <= tix) ++ti;
+            const int tj = tix - ti * (ti + 1) / 2;
+            const int r = kT16 * ti + ((e >> 4) & 15), c = kT16 * tj + (e & 15);
+            d16[e] = __float2bfloat16_rn(r >= c ? (float)(wt[c * kBlk + r] * sc[c]) : 0.f);
+        }
+        return;
+    }
     R* dst = D.blocks + (size_t)b * kW;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = warp; j < kBlk; j += nw) {
@@ -1495,6 +1512,208 @@ __global__ void __launch_bounds__(96) k_block_apply_plain(Dev<R> D, const R* __r
     }
 }
 
+// ---- BF16 factors on the tensor cores (IPC_PREC_BF16_MAS)
+//
+// W' is stored as BF16 16 x 16 tiles. y = W' x and z = W'^T y run as
+// mma.sync m16n8k16 (BF16 operands, FP32 accumulation) with A the factor
+// tiles loaded by ldmatrix (.trans for W'^T) and B the right-hand sides, each
+// split into a BF16 high part and a BF16 low part (x - hi) in two columns of
+// the 8 so that only the factor carries BF16 rounding: y = D[:, 0] + D[:, 1].
+// B = W'^T W' stays symmetric positive semi-definite whatever the rounding.
+
+__device__ __forceinline__ int tile16(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_k, hi_k);  // .x = first (lower k)
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+// high and low BF16 parts of two consecutive values, as two packed registers
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+    const __nv_bfloat162 h2 = __halves2bfloat162(ah, bh);
+    hi = *reinterpret_cast<const uint32_t*>(&h2);
+    lo = pack_bf16(a - __bfloat162float(ah), b - __bfloat162float(bh));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// A fragment of tile T (16 x 16 BF16, row-major, 32-byte rows): lane L points
+// at row (L & 7) + 8 ((L >> 3) & 1), column 8 (L >> 4); for T^T the 8 x 8
+// quarters swap: row (L & 7) + 8 (L >> 4), column 8 ((L >> 3) & 1)
+__device__ __forceinline__ void frag_tile(uint32_t a[4], const __nv_bfloat16* T, bool transposed) {
+    const int L = threadIdx.x & 31;
+    if (!transposed)
+        ldsm_x4(a, T + ((L & 7) + 8 * ((L >> 3) & 1)) * kT16 + 8 * (L >> 4));
+    else
+        ldsm_x4_t(a, T + ((L & 7) + 8 * (L >> 4)) * kT16 + 8 * ((L >> 3) & 1));
+}
+// B fragment of one 16-row segment x of a right-hand side: column 0 its high
+// parts, column 1 its low parts, the other columns zero (lanes with g >= 2)
+__device__ __forceinline__ void frag_rhs(const float* x, uint32_t& b0, uint32_t& b1) {
+    const int L = threadIdx.x & 31, g = L >> 2, t = L & 3;
+    b0 = b1 = 0u;
+    if (g < 2) {
+        uint32_t h0, l0, h1, l1;
+        split_bf16x2(x[2 * t], x[2 * t + 1], h0, l0);
+        split_bf16x2(x[2 * t + 8], x[2 * t + 9], h1, l1);
+        b0 = g == 0 ? h0 : l0;
+        b1 = g == 0 ? h1 : l1;
+    }
+}
+
+// y = W' x (trans = false) or y = W'^T x (trans = true) for one vector, 96
+// threads: warp w takes the output tiles w and 5 - w (equal work)
+__device__ __forceinline__ void tri_apply_bf16(const __nv_bfloat16* Wt, const float* x, float* y, bool trans) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int o = u == 0 ? warp : kNT16 - 1 - warp;  // output tile
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int k0 = trans ? o : 0, k1 = trans ? kNT16 - 1 : o;
+        for (int k = k0; k <= k1; ++k) {
+            uint32_t a[4], b0, b1;
+            // y_o += W'_ok x_k (k <= o), or y_o += W'_ko^T x_k (k >= o)
+            frag_tile(a, Wt + (size_t)(trans ? tile16(k, o) : tile16(o, k)) * (kT16 * kT16), trans);
+            frag_rhs(x + kT16 * k, b0, b1);
+            mma_bf16(acc, a, b0, b1);
+        }
+        if (t == 0) {
+            y[kT16 * o + g] = acc[0] + acc[1];
+            y[kT16 * o + g + 8] = acc[2] + acc[3];
+        }
+    }
+}
+
+// V[a] = W' X[a] for a < nc (nc <= 1 + kMaxK) right-hand sides in shared
+// memory: their high and low parts fill 2 nc columns, 8 per mma; warp w
+// takes the row tiles w and 5 - w. The pair of columns (2a, 2a + 1) lands in
+// lane t = a % 4 of n-tile a / 4.
+__device__ __forceinline__ void lower_apply_bf16(const __nv_bfloat16* Wt, const float (*X)[kBlk], float (*V)[kBlk],
+                                                 int nc) {
+    constexpr int kNq = (2 * (1 + kMaxK) + 7) / 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int nq = (2 * nc + 7) / 8;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int o = u == 0 ? warp : kNT16 - 1 - warp;
+        float acc[kNq][4];
+#pragma unroll
+        for (int q = 0; q < kNq; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+        for (int k = 0; k <= o; ++k) {
+            uint32_t a[4];
+            frag_tile(a, Wt + (size_t)tile16(o, k) * (kT16 * kT16), false);
+#pragma unroll
+            for (int q = 0; q < kNq; ++q) {
+                if (q >= nq) break;
+                const int n = 8 * q + g, col = n >> 1;
+                uint32_t b0 = 0u, b1 = 0u;
+                if (col < nc) {
+                    const float* x = X[col] + kT16 * k;
+                    uint32_t h0, l0, h1, l1;
+                    split_bf16x2(x[2 * t], x[2 * t + 1], h0, l0);
+                    split_bf16x2(x[2 * t + 8], x[2 * t + 9], h1, l1);
+                    b0 = (n & 1) ? l0 : h0;
+                    b1 = (n & 1) ? l1 : h1;
+                }
+                mma_bf16(acc[q], a, b0, b1);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kNq; ++q) {
+            const int col = 4 * q + t;
+            if (q < nq && col < nc) {
+                V[col][kT16 * o + g] = acc[q][0] + acc[q][1];
+                V[col][kT16 * o + g + 8] = acc[q][2] + acc[q][3];
+            }
+        }
+    }
+}
+
+// Plain block apply with BF16 factors: the persistent 2-stage ring of
+// k_block_apply_plain with 10.7 KB tiles and the two products on the tensor
+// cores.
+__global__ void __launch_bounds__(96) k_block_apply_plain16(Dev<float> D, const float* __restrict__ g,
+                                                            float* __restrict__ z) {
+    extern __shared__ __align__(128) unsigned char bsm[];  // 2 slots of kW16 BF16 values
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(16) float rhs[kBlk];
+    __shared__ __align__(16) float ys[kBlk];
+    constexpr uint32_t kBytes = kW16 * 2;
+    const __nv_bfloat16* src16 = static_cast<const __nv_bfloat16*>(D.blocks16);
+    const int nb = D.blk_off[D.nlev];
+    const int tid = threadIdx.x;
+    const int first = blockIdx.x, stride = gridDim.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        for (int s = 0; s < 2; ++s) {
+            const int b = first + s * stride;
+            if (b < nb) {
+                mbar_arrive_expect_tx(&bar[s], kBytes);
+                bulk_g2s(bsm + s * kBytes, src16 + (size_t)b * kW16, kBytes, &bar[s]);
+            }
+        }
+    }
+    int it = 0;
+    for (int b = first; b < nb; b += stride, ++it) {
+        const int slot = it & 1;
+        const uint32_t parity = (uint32_t)(it >> 1) & 1u;
+        const __nv_bfloat16* Wt = reinterpret_cast<const __nv_bfloat16*>(bsm + slot * kBytes);
+        int l = 0;
+        while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
+        const int grp = b - D.blk_off[l];
+        const int node = D.members[l][(size_t)grp * kSub + tid / 3];
+        const int comp = tid % 3;
+        if (l == 0)
+            rhs[tid] = node >= 0 ? g[3 * node + comp] : 0.f;
+        else
+            rhs[tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : 0.f;
+        __syncthreads();
+        const bool arrived = mbar_wait(&bar[slot], parity, D.wait_polls);
+        if (__syncthreads_or(!arrived)) {
+            if (tid == 0) {
+                D.S->async_timeout = 1;
+                mbar_wait(&bar[slot], parity, kDrainPolls);
+                if (b + stride < nb) mbar_wait(&bar[slot ^ 1], (uint32_t)((it + 1) >> 1) & 1u, kDrainPolls);
+            }
+            return;
+        }
+        tri_apply_bf16(Wt, rhs, ys, false);
+        __syncthreads();
+        tri_apply_bf16(Wt, ys, rhs, true);  // z into rhs
+        __syncthreads();
+        const float out = rhs[tid];
+        if (tid == 0 && b + 2 * stride < nb) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar[slot], kBytes);
+            bulk_g2s(bsm + slot * kBytes, src16 + (size_t)(b + 2 * stride) * kW16, kBytes, &bar[slot]);
+        }
+        if (node >= 0) {
+            if (l == 0)
+                z[3 * node + comp] = out;
+            else
+                D.coarse_y[D.coarse_off[l] + 3 * node + comp] = out;
+        }
+        if (!(out - out == 0.f)) atomicCAS(&D.S->dbg_block, -1, b);
+        __syncthreads();
+    }
+}
+
 // Level-0 apply with the Sparse-Input Woodbury update (Eq. 7) and the plain
 // apply of the coarse blocks. With U_d the subdomain's top-K vectors (ns of
 // them) and V = W' [g_d, U_d]:
@@ -1502,9 +1721,10 @@ __global__ void __launch_bounds__(96) k_block_apply_plain(Dev<R> D, const R* __r
 //   C lambda = r (FP64 Cholesky, one warp, a lane per row),
 //   z_d = W'^T (V_g - V_U lambda) = B g - B U lambda.
 // One pass of the factor over all 1 + ns columns and one transposed pass.
-template <class R>
+template <class R, bool kB16 = false>
 __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z,
                                                     ContactBuf C, int woodbury) {
+    static_assert(!kB16 || sizeof(R) == 4, "BF16 factors come with the FP32 bulk");
     extern __shared__ __align__(128) unsigned char wsm[];  // the packed factor (bulk copy)
     __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(16) R rhs[1 + kMaxK][kBlk];
@@ -1518,15 +1738,19 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
     __shared__ int sel[kMaxK];
     __shared__ int nsel;
     const R* Ws = reinterpret_cast<const R*>(wsm);
+    const __nv_bfloat16* Wt = reinterpret_cast<const __nv_bfloat16*>(wsm);
     const int b = blockIdx.x;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        constexpr uint32_t kBytes = kW * sizeof(R);
+        constexpr uint32_t kBytes = kB16 ? kW16 * 2 : kW * sizeof(R);
         mbar_init(&bar, 1);
         fence_mbar_init();
         mbar_arrive_expect_tx(&bar, kBytes);
-        bulk_g2s(wsm, D.blocks + (size_t)b * kW, kBytes, &bar);
+        if constexpr (kB16)
+            bulk_g2s(wsm, static_cast<const __nv_bfloat16*>(D.blocks16) + (size_t)b * kW16, kBytes, &bar);
+        else
+            bulk_g2s(wsm, D.blocks + (size_t)b * kW, kBytes, &bar);
     }
     int l = 0;
     while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
@@ -1569,7 +1793,9 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
     __syncthreads();
     if (!factor_arrived(D, &bar)) return;
     // V = W' [rhs]: one read of each factor entry for all 1 + ns columns
-    if (ns == 0)
+    if constexpr (kB16)
+        lower_apply_bf16(Wt, rhs, V, 1 + ns);
+    else if (ns == 0)
         lower_apply<R, 1>(Ws, rhs, V, 1);
     else
         lower_apply<R, 1 + kMaxK>(Ws, rhs, V, 1 + ns);
@@ -1674,7 +1900,10 @@ __global__ void __launch_bounds__(96) k_block_apply(Dev<R> D, const R* __restric
         V[0][tid] = (R)o;
     }
     __syncthreads();
-    upper_apply(Ws, V[0], zs);
+    if constexpr (kB16)
+        tri_apply_bf16(Wt, V[0], zs, true);
+    else
+        upper_apply(Ws, V[0], zs);
     __syncthreads();
     const R out = zs[tid];
     if (node >= 0) {
@@ -1783,12 +2012,26 @@ void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool 
         cudaFuncSetAttribute(k_block_apply_plain<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(2 * kW * sizeof(R)));
         cudaFuncSetAttribute(k_block_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kW * sizeof(R)));
+        if constexpr (sizeof(R) == 4) {
+            cudaFuncSetAttribute(k_block_apply_plain16, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kW16 * 2);
+            cudaFuncSetAttribute(k_block_apply<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kW16 * 2);
+        }
         int dev = 0, n = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         return n > 0 ? n : 148;
     }();
     const int nb = D.blk_off[D.nlev];
+    if constexpr (sizeof(R) == 4) {
+        if (D.blocks16) {
+            // BF16 factors: tiles of 10.7 KB, more persistent CTAs per SM
+            if (woodbury)
+                KL(k_block_apply<R, true><<<nb, 96, kW16 * 2, st>>>(D, g, z, C, 1));
+            else
+                KL(k_block_apply_plain16<<<std::min(nb, 8 * sms), 96, 2 * kW16 * 2, st>>>(D, g, z));
+            return;
+        }
+    }
     if (woodbury) {
         KL(k_block_apply<R><<<nb, 96, kW * sizeof(R), st>>>(D, g, z, C, 1));
     } else {

@@ -25,6 +25,7 @@ IPC_ERR_TIMEOUT = -5
 IPC_ERR_CAPACITY = -7
 IPC_PREC_FP64 = 0
 IPC_PREC_FP32 = 1
+IPC_PREC_BF16_MAS = 2
 
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
@@ -399,7 +400,7 @@ class Scene:
         precision, through the allocation-free entry point; returns once z is
         complete (the call waits for the stream)."""
         import torch
-        want = torch.float64 if self.precision == IPC_PREC_FP64 else torch.float32
+        want = torch.float64 if self.precision == IPC_PREC_FP64 else torch.float32  # BF16_MAS: FP32 vectors
         for t in (g_dev, z_dev):
             if not (t.is_cuda and t.dtype == want and t.is_contiguous() and t.numel() == 3 * self.nv):
                 raise ValueError(f"expected a contiguous CUDA {want} tensor of {3 * self.nv} values")

@@ -173,6 +173,27 @@ def test_preconditioner_fp32(lib, name):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
+def test_preconditioner_bf16(lib, name):
+    """BF16 factors (IPC_PREC_BF16_MAS): W' rounded to BF16 (8 significant
+    bits) and applied on the tensor cores. B~ = W~'^T W~' stays positive
+    definite (g.z > 0), and z follows the FP64 oracle to the BF16 rounding of
+    the factor times its conditioning: within 2e-2 here, the restart and the
+    Woodbury-patched forms alike."""
+    sc = SCENES[name]
+    g, o = _pair(lib, sc, precision=2)
+    xb = contact_state(sc, 0.9)
+    xc = contact_state(sc, 0.4) + 1e-6 * RNG.normal(size=xb.shape)
+    for trial in range(3):
+        grad = RNG.normal(size=xb.shape)
+        for cur in (None, xc):
+            zg = g.precond_apply(xb, grad, cur)
+            zo = o.precond_apply(xb, grad, cur)
+            rel = np.linalg.norm(zg - zo) / np.linalg.norm(zo)
+            assert rel <= 2e-2, (cur is None, rel)
+            assert float(np.sum(zg * grad)) > 0
+
+
+@pytest.mark.parametrize("name", list(SCENES))
 def test_fp32_inversion_hands_blocks_to_fp64(lib, name):
     """The FP32 first pass of the block inversion hands a block to the FP64
     pass (Sec. 4.2 inverse with the pivot rules) when a pivot of its scaled

@@ -70,6 +70,27 @@ def test_fp32_bulk_steps_follow_the_fp64_oracle(lib):
     assert max(errs) <= 1e-5, errs
 
 
+def test_bf16_factor_steps_follow_the_fp64_oracle(lib):
+    """With BF16 block factors the preconditioner changes, not the minimiser:
+    fed the oracle's state each timestep, the BF16 form converges (tol 1e-5)
+    to the oracle's positions within 1e-5 of the bounding-box diagonal."""
+    import oracle as O
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.ground_drop(n=3, gap=0.003, drop_speed=0.5)
+    o = O.Scene(sc, params={"tol": 1e-8})
+    g = lib.Scene(sc, precision=lib.IPC_PREC_BF16_MAS, params={"tol": 1e-5})
+    x, v = sc["x0"].copy(), sc["v0"].copy()
+    errs = []
+    for step in range(4):
+        g.set_state(x, v)
+        st = g.step(1)
+        assert st["converged"] == 1, (step, st)
+        xo, vo, so = o.step(x, v)
+        errs.append(float(np.abs(g.positions() - xo).max() / o.bbox_diag()))
+        x, v = xo, vo
+    assert max(errs) <= 1e-5, errs
+
+
 def test_exhausted_copy_wait_reports_timeout_and_leaves_the_context_usable(lib):
     """wait_polls = 0: every bounded wait of the block-apply CTAs reports a
     timeout without polling; ipc_step stops with IPC_ERR_TIMEOUT before z is
