@@ -58,6 +58,8 @@ def parse():
                     help="scenes in the serving measurement (ipc_server, 0 = skip)")
     ap.add_argument("--ablation", type=int, default=0,
                     help="timesteps of the ablation runs (MAS maintenance, CCD step; 0 = skip)")
+    ap.add_argument("--stiffness-sweep", type=int, default=0,
+                    help="timesteps per case of the stiffness sweep, MAS vs 3x3 block-Jacobi (0 = skip)")
     ap.add_argument("--scale", type=int, default=5,
                     help="timesteps of the large-scene run (512 spheres in a 2.5 x 2 x 2.5 m box; 0 = skip)")
     ap.add_argument("--profile-from-step", type=int, default=-1,
@@ -318,6 +320,40 @@ def run_bf16(args, ipc, S, m, flush, stream, peak, warmup):
             "roofline_stages": roof}
 
 
+def run_stiffness_sweep(args, ipc, S, prec):
+    """The paper's preconditioner comparison over material stiffness (Sec.
+    5.1): two 8^3-cell cubes stacked 5 mm apart above the ground with seeded
+    random vertex velocities (0.2 m/s per component, exciting the elastic
+    modes), Young's modulus E in {1e4 .. 1e7} Pa (kappa follows E); from the
+    same initial state, `args.stiffness_sweep` timesteps with MAS (Woodbury
+    maintenance) and with 3x3 block-Jacobi preconditioning on the same PNCG
+    iteration. The convergence test max |z| <= tol h bbox depends on P: a
+    weak preconditioner can meet it early, so the energy each reaches is
+    reported beside the iteration counts."""
+    import torch
+    out = []
+    for E in (1e4, 1e5, 1e6, 1e7):
+        sc = S.two_cubes(n=8, gap=0.005)
+        sc["v0"] = 0.2 * np.random.default_rng(5).normal(size=sc["x0"].shape)
+        sc["E"] = np.full_like(sc["E"], E)
+        sc["params"] = S.default_params(S.bbox_diag(sc["x0"]), sc["params"]["h"], E)
+        row = {"E": E}
+        for name, prm in (("mas", {}), ("block_jacobi", {"mas_mode": 3})):
+            g = ipc.Scene(sc, params=prm, precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = g.step(args.stiffness_sweep)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            row[name] = {"iters_per_step": st["iters"] / args.stiffness_sweep,
+                         "ms_per_step": 1e3 * dt / args.stiffness_sweep, "converged": st["converged"],
+                         "final_energy": st["energy"]}
+            g.close()
+        out.append(row)
+    return {"scene": "two_cubes(n=8, gap=0.005), random v0, E scaled", "timesteps": args.stiffness_sweep,
+            "rows": out}
+
+
 def run_ablation(args, ipc, S, prec):
     """The paper's ablations on the same kernels: MAS maintenance (Woodbury
     updates, full rebuild every iteration, frozen between restarts) and the
@@ -327,7 +363,7 @@ def run_ablation(args, ipc, S, prec):
     sc = S.sphere_pile()
     out = {}
     for name, prm in (("woodbury_per_subdomain", {}), ("full_rebuild", {"mas_mode": 1}), ("freeze", {"mas_mode": 2}),
-                      ("global_alpha", {"ccd_mode": 1})):
+                      ("block_jacobi", {"mas_mode": 3}), ("global_alpha", {"ccd_mode": 1})):
         g = ipc.Scene(sc, params=prm, precision=prec)
         g.step(1)  # one-time setup and graph captures
         g.set_state(sc["x0"], sc["v0"])
@@ -560,6 +596,7 @@ def main():
 
     serving = run_serving(args, ipc, S) if args.serve > 0 and world == 1 else None
     ablation = run_ablation(args, ipc, S, prec) if args.ablation > 0 and world == 1 else None
+    sweep = run_stiffness_sweep(args, ipc, S, prec) if args.stiffness_sweep > 0 and world == 1 else None
     scale = run_scale(args, ipc, S, prec, rsize, flush, stream, peak) if args.scale > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
@@ -670,6 +707,7 @@ def main():
         "stage_ms_timesteps": f"0..{n_prof - 1}, a separate profiled pass (kernels launched one by one)",
         "serving": serving,
         "ablation": ablation,
+        "stiffness_sweep": sweep,
         "scale": scale,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -113,7 +113,11 @@ typedef struct ipc_params {
                                 current positions and contacts (the PNCG
                                 recurrence goes on: not a restart); 2 freeze,
                                 the preconditioner and H_base of the last
-                                restart serve unchanged */
+                                restart serve unchanged; 3 3x3 block-Jacobi
+                                preconditioning instead of MAS (the inverse
+                                3x3 diagonal blocks of H_base, rebuilt at
+                                restarts, frozen between them: the paper's
+                                MAS-vs-Jacobi comparison, Sec. 5.1) */
     int ccd_mode;            /* 0 per-subdomain step bounds alpha_d (Sec. 4.4,
                                 default); 1 one global step min_d alpha_d */
     int graphs;              /* 1 (default): the per-iteration launch sequences

@@ -330,6 +330,7 @@ int setup_dev(ipc_scene* s) {
     D.hess = A.arr<R>((size_t)D.ntp * kH * kPack);
     D.blocks = A.arr<R>((size_t)nb * kW);
     D.blocks16 = p.precision == IPC_PREC_BF16_MAS ? A.get((size_t)nb * kW16 * 2) : nullptr;
+    D.jac = p.mas_mode == 3 ? A.arr<R>(9 * (size_t)m.nv) : nullptr;
     const int nb0 = m.nlev > 1 ? D.blk_off[1] : nb;
     D.asmb = A.arr<double>((size_t)nb0 * kBlk * kBlk);
     D.invflag = A.arr<int>(std::max(nb, 1));
@@ -792,6 +793,8 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         // MAS maintenance between restarts: Woodbury updates, a full rebuild
         // (the blocks and H_base at the current state; not a PNCG restart) or
         // nothing (frozen)
+        // (mas_mode 3, block-Jacobi, is rebuilt at restarts like MAS and frozen
+        // between them)
         const bool rebuild = restart || P.mas_mode == 1;
         const bool woodbury = !restart && P.mas_mode == 0;
         if (rebuild) {
@@ -1384,7 +1387,8 @@ int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params, const
     if (!out || !desc || !params) return fail(IPC_ERR_INVALID, "null argument");
     *out = nullptr;
     if (!(params->h > 0) || !(params->dhat > 0) || !(params->kappa > 0) || params->K < 0 || params->K > kMaxK ||
-        params->iter_max <= 0 || params->levels_max < 1 || params->ls_max < 0 ||
+        params->iter_max <= 0 || params->levels_max < 1 || params->ls_max < 0 || params->mas_mode < 0 ||
+        params->mas_mode > 3 || params->ccd_mode < 0 || params->ccd_mode > 1 ||
         (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_FP32 &&
          params->precision != IPC_PREC_BF16_MAS) ||
         params->broad_phase < 0 ||

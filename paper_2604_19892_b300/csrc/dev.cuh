@@ -144,6 +144,7 @@ struct Dev {
     R* hess;                               // [ntp][45][32]
     R* blocks;                             // nblocks * kW: packed factors W' (B = W'^T W')
     void* blocks16;                        // BF16 factors (nblocks * kW16 bf16), or null: FP32 / FP64 factors in blocks
+    R* jac;                                // 3x3 block-Jacobi preconditioner (mas_mode 3): nv x 9, else null
     double* asmb;                          // level-0 assembly buffer (FP64)
     double* asmbc;                         // coarse-level assembly buffer (FP64)
     const double* mdiag;                   // per block: mass diagonal (96 entries), fixed

@@ -1938,6 +1938,37 @@ __global__ void k_clear_upd(Dev<R> D) {
     D.S->n_upd = 0;
 }
 
+// ---- 3x3 block-Jacobi preconditioner (the paper's MAS-vs-Jacobi ablation,
+// Sec. 5.1): P = blockdiag(H_vv)^-1 over the vertices, H_vv the 3x3 diagonal
+// blocks of H_base at the restart, read from the level-0 assembly (lower
+// triangle) and inverted in FP64 by cofactors.
+template <class R>
+__global__ void k_jacobi_build(Dev<R> D) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= D.nv) return;
+    const double* A = D.asmb + (size_t)D.grp0[v] * (kBlk * kBlk) + (size_t)(3 * D.slot0[v]) * kBlk + 3 * D.slot0[v];
+    const double a = A[0], b = A[kBlk], c = A[2 * kBlk], d = A[kBlk + 1], e = A[2 * kBlk + 1], f = A[2 * kBlk + 2];
+    // symmetric [[a b c] [b d e] [c e f]]
+    const double c00 = d * f - e * e, c01 = c * e - b * f, c02 = b * e - c * d;
+    const double c11 = a * f - c * c, c12 = b * c - a * e, c22 = a * d - b * b;
+    const double det = a * c00 + b * c01 + c * c02;
+    const double id = det > 0.0 ? 1.0 / det : 0.0;
+    R* J = D.jac + 9 * (size_t)v;
+    const double m[9] = {c00, c01, c02, c01, c11, c12, c02, c12, c22};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) J[k] = (R)(m[k] * id);
+}
+
+template <class R>
+__global__ void k_jacobi_apply(Dev<R> D, const R* __restrict__ g, R* __restrict__ z) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= D.nv) return;
+    const R* J = D.jac + 9 * (size_t)v;
+    const R g0 = g[3 * v], g1 = g[3 * v + 1], g2 = g[3 * v + 2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) z[3 * v + r] = J[3 * r] * g0 + J[3 * r + 1] * g1 + J[3 * r + 2] * g2;
+}
+
 }  // namespace
 
 template <class R>
@@ -1954,7 +1985,10 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
         KL(k_asm_sum<R><<<nblk(32LL * D.nitem, 256), 256, 0, st>>>(D));
     }
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
-    launch_invert(D, st);
+    if (D.jac)
+        KL(k_jacobi_build<R><<<nblk(D.nv), kT, 0, st>>>(D));
+    else
+        launch_invert(D, st);
     cudaMemsetAsync(D.bkeys, 0xFF, sizeof(unsigned long long) * D.btab, st);
     KL(k_snapshot<R><<<592, kT, 0, st>>>(D));
 }
@@ -2000,6 +2034,7 @@ void launch_classify(const Dev<R>& D, const ContactBuf& C, cudaStream_t st) {
 
 template <class R>
 void launch_restrict(const Dev<R>& D, const R* g, cudaStream_t st) {
+    if (D.jac) return;  // block-Jacobi: no coarse levels
     for (int l = 0; l + 1 < D.nlev; ++l) {
         const R* src = l == 0 ? g : D.coarse_r + D.coarse_off[l];
         KL(k_restrict_level<R><<<nblk(32LL * D.ngroups[l]), kT, 0, st>>>(D, l, src));
@@ -2022,6 +2057,10 @@ void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool 
         return n > 0 ? n : 148;
     }();
     const int nb = D.blk_off[D.nlev];
+    if (D.jac) {
+        KL(k_jacobi_apply<R><<<nblk(D.nv), kT, 0, st>>>(D, g, z));
+        return;
+    }
     if constexpr (sizeof(R) == 4) {
         if (D.blocks16) {
             // BF16 factors: tiles of 10.7 KB, more persistent CTAs per SM
@@ -2044,7 +2083,7 @@ void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool 
 
 template <class R>
 void launch_prolong(const Dev<R>& D, R* z, cudaStream_t st) {
-    if (D.nlev > 1) KL(k_prolong<R><<<nblk(D.nv), kT, 0, st>>>(D, z));
+    if (D.nlev > 1 && !D.jac) KL(k_prolong<R><<<nblk(D.nv), kT, 0, st>>>(D, z));
 }
 
 template <class R>

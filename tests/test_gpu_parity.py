@@ -456,12 +456,12 @@ def test_graphs_match_direct_launches():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", [{"mas_mode": 1}, {"mas_mode": 2}, {"ccd_mode": 1}])
+@pytest.mark.parametrize("mode", [{"mas_mode": 1}, {"mas_mode": 2}, {"mas_mode": 3}, {"ccd_mode": 1}])
 def test_ablation_modes_reach_the_same_minimiser(mode):
-    """Full MAS rebuild, frozen MAS and the global CCD step change how the
-    iteration gets there, not where: on a scene whose incremental potential
-    has one minimiser each converges at tol 1e-7 to the default mode's
-    positions."""
+    """Full MAS rebuild, frozen MAS, 3x3 block-Jacobi preconditioning and the
+    global CCD step change how the iteration gets there, not where: on a
+    scene whose incremental potential has one minimiser each converges at tol
+    1e-7 to the default mode's positions."""
     import torch
     from paper_2604_19892_b300 import ipc
     from paper_2604_19892_b300 import scenes as S
