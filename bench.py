@@ -60,6 +60,8 @@ def parse():
                     help="timesteps of the ablation runs (MAS maintenance, CCD step; 0 = skip)")
     ap.add_argument("--stiffness-sweep", type=int, default=0,
                     help="timesteps per case of the stiffness sweep, MAS vs 3x3 block-Jacobi (0 = skip)")
+    ap.add_argument("--large", type=int, default=0,
+                    help="timesteps of the large spiky-ball scene (8 balls, 1.13M vertices, 2.84M tets; 0 = skip)")
     ap.add_argument("--scale", type=int, default=5,
                     help="timesteps of the large-scene run (512 spheres in a 2.5 x 2 x 2.5 m box; 0 = skip)")
     ap.add_argument("--profile-from-step", type=int, default=-1,
@@ -354,6 +356,45 @@ def run_stiffness_sweep(args, ipc, S, prec):
             "rows": out}
 
 
+def run_large(args, ipc, S, prec):
+    """The large scene shaped like the paper's teaser: eight spiky balls
+    (1,132,296 vertices, 2,840,064 tets), `args.large` timesteps of their drop
+    and collisions, FP32 bulk; per timestep its iterations, contacts and
+    device time."""
+    import torch
+    t0 = time.perf_counter()
+    sc = S.spiky_balls()
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g = ipc.Scene(sc, precision=prec)
+    setup_s = time.perf_counter() - t0
+    free, total = torch.cuda.mem_get_info()
+    print(f"large scene: generated in {gen_s:.1f} s, set up in {setup_s:.1f} s, {(total - free) / 1e9:.1f} GB in use",
+          file=sys.stderr, flush=True)
+    rows = []
+    g.profile(True)  # per-stage device times (events around each stage)
+    for k in range(args.large):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = g.step(1)
+        torch.cuda.synchronize()
+        rows.append({"t": k, "ms": 1e3 * (time.perf_counter() - t0), "iters": st["iters"],
+                     "restarts": st["restarts"], "contacts": st["n_contacts"], "converged": st["converged"],
+                     "min_dist": st["min_dist"]})
+        rows[-1]["stage_ms"] = {kk: round(v["ms"], 1) for kk, v in g.profile_read().items()}
+        print(f"large scene timestep {k}: {rows[-1]}", file=sys.stderr, flush=True)
+        g.profile(True)  # reset the counters
+    g.profile(False)
+    g.close()
+    its = sum(r["iters"] for r in rows)
+    secs = sum(r["ms"] for r in rows) / 1e3
+    return {"scene": "spiky_balls(n_balls=8): 32^3-cell balls with 200 spikes each", "vertices": int(sc["x0"].shape[0]),
+            "tets": int(sc["tets"].shape[0]), "generation_s": gen_s, "setup_s": setup_s,
+            "device_bytes_in_use_after_setup": int(total - free), "timesteps": args.large,
+            "iters_per_s": its / secs if secs else None, "timesteps_per_s": args.large / secs if secs else None,
+            "peak_contacts": max((r["contacts"] for r in rows), default=0), "per_step": rows}
+
+
 def run_ablation(args, ipc, S, prec):
     """The paper's ablations on the same kernels: MAS maintenance (Woodbury
     updates, full rebuild every iteration, frozen between restarts) and the
@@ -597,6 +638,7 @@ def main():
     serving = run_serving(args, ipc, S) if args.serve > 0 and world == 1 else None
     ablation = run_ablation(args, ipc, S, prec) if args.ablation > 0 and world == 1 else None
     sweep = run_stiffness_sweep(args, ipc, S, prec) if args.stiffness_sweep > 0 and world == 1 else None
+    large = run_large(args, ipc, S, prec) if args.large > 0 and world == 1 else None
     scale = run_scale(args, ipc, S, prec, rsize, flush, stream, peak) if args.scale > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
@@ -708,6 +750,7 @@ def main():
         "serving": serving,
         "ablation": ablation,
         "stiffness_sweep": sweep,
+        "large": large,
         "scale": scale,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -284,7 +284,11 @@ int setup_dev(ipc_scene* s) {
     }
     D.has_ground = m.has_ground;
     D.goff = m.goff;
-    D.cell = std::max(m.mean_surface_edge, 1e-12);
+    // broad-phase cell: the mean surface edge, but no smaller than a third of
+    // the longest one, so that on meshes mixing fine and coarse features
+    // (thin spikes on a coarse ball) the coarse primitives still cover a few
+    // cells each instead of falling into the list every query scans
+    D.cell = std::max(std::max(m.mean_surface_edge, m.max_surface_edge / 3.0), 1e-12);
 
     const size_t n3 = 3 * (size_t)m.nv;
     // mesh

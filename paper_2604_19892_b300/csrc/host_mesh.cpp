@@ -165,7 +165,7 @@ int build_host_mesh(const ipc_scene_desc* d, int levels_max, HostMesh* m, std::s
     std::sort(edges.begin(), edges.end());
     edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
     m->se.clear();
-    double elen = 0.0;
+    double elen = 0.0, emax = 0.0;
     for (auto& e : edges) {
         m->se.push_back(e.first);
         m->se.push_back(e.second);
@@ -175,8 +175,10 @@ int build_host_mesh(const ipc_scene_desc* d, int levels_max, HostMesh* m, std::s
             s += dd * dd;
         }
         elen += std::sqrt(s);
+        emax = std::max(emax, std::sqrt(s));
     }
     m->mean_surface_edge = edges.empty() ? 0.0 : elen / edges.size();
+    m->max_surface_edge = emax;
     m->sv.clear();
     for (int v = 0; v < nv; ++v)
         if (on_surf[v]) m->sv.push_back(v);

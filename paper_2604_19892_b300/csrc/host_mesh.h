@@ -29,6 +29,7 @@ struct HostMesh {
     std::vector<std::vector<int>> group_of, slot_of, members, node_of_vert;
     double bbox_diag = 0.0;
     double mean_surface_edge = 0.0;
+    double max_surface_edge = 0.0;
     double gravity[3] = {0, 0, 0};
     int has_ground = 0;
     double gn[3] = {0, 1, 0}, goff = 0.0;

@@ -343,3 +343,124 @@ def small_cubes(n=2, gap=0.01, jitter=1e-4, seed=0, h=1.0 / 30, edge_len=0.1, dr
     sc["v0"][:, 1] = -drop_speed
     sc["name"] = f"small_cubes_{n}"
     return sc
+
+
+def _prism_tets(p):
+    """Three positively ordered tets of the prism with bottom (p0, p1, p2) and
+    top (p3, p4, p5) (p3 above p0, ...), each quad face split along the
+    diagonal from its smallest vertex id, so neighbouring prisms that share a
+    quad face split it the same way (the usual id-based rule for conforming
+    prism meshes)."""
+    p = list(p)
+    # rotate / flip so that the smallest id is p0
+    k = int(np.argmin(p))
+    rot = [[0, 1, 2, 3, 4, 5], [1, 2, 0, 4, 5, 3], [2, 0, 1, 5, 3, 4],
+           [3, 5, 4, 0, 2, 1], [4, 3, 5, 1, 0, 2], [5, 4, 3, 2, 1, 0]][k]
+    q = [p[i] for i in rot]
+    if min(q[1], q[5]) < min(q[2], q[4]):
+        return [(q[0], q[1], q[2], q[5]), (q[0], q[1], q[5], q[4]), (q[0], q[4], q[5], q[3])]
+    return [(q[0], q[1], q[2], q[4]), (q[0], q[4], q[2], q[5]), (q[0], q[4], q[5], q[3])]
+
+
+def spiky_ball_mesh(cells, radius, center, n_spikes=200, layers=132, spike_len=0.5, tip=0.15, seed=0):
+    """A cube-to-ball mapped grid (cells^3, 6 tets per cell) with n_spikes
+    conical spikes grown from surface quads: each spike extrudes the two
+    boundary triangles of one surface quad outward in `layers` layers of
+    prisms (3 tets each), tapering linearly to `tip` of its base size, to a
+    length of spike_len * radius. The base triangles are the ball's own, so
+    the mesh is conforming. Quads are picked at random without repetition,
+    avoiding quads that share a vertex with an earlier pick."""
+    x, t = ball_mesh(cells, radius, center)
+    rng = np.random.default_rng(seed)
+    # boundary triangles of the ball (faces used once)
+    faces = np.concatenate([t[:, [0, 1, 2]], t[:, [0, 1, 3]], t[:, [0, 2, 3]], t[:, [1, 2, 3]]])
+    key = np.sort(faces, axis=1)
+    uniq, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    bnd = uniq[cnt == 1]
+    # pair boundary triangles into quads: two triangles sharing an edge whose
+    # four vertices lie on one cell face (the face diagonal)
+    from collections import defaultdict
+    edge_tris = defaultdict(list)
+    for i, tr in enumerate(bnd):
+        for a, b in ((tr[0], tr[1]), (tr[0], tr[2]), (tr[1], tr[2])):
+            edge_tris[(min(a, b), max(a, b))].append(i)
+    # the lattice index of each ball vertex tells which edges are face diagonals
+    n1 = cells + 1
+    ijk = np.stack(np.unravel_index(np.arange(n1 ** 3), (n1, n1, n1)), axis=1)
+    quads = []
+    for (a, b), tris in edge_tris.items():
+        if len(tris) != 2:
+            continue
+        if np.count_nonzero(ijk[a] != ijk[b]) != 2:  # not a face diagonal
+            continue
+        tr0, tr1 = bnd[tris[0]], bnd[tris[1]]
+        quads.append((tr0, tr1))
+    order = rng.permutation(len(quads))
+    used = set()
+    picked = []
+    for qi in order:
+        tr0, tr1 = quads[qi]
+        vs = set(tr0.tolist()) | set(tr1.tolist())
+        if vs & used:
+            continue
+        picked.append((tr0, tr1))
+        used |= vs
+        if len(picked) == n_spikes:
+            break
+    pts = [x]
+    tets = [t]
+    nxt = x.shape[0]
+    c = np.asarray(center, dtype=np.float64)
+    for tr0, tr1 in picked:
+        base = np.array(sorted(set(tr0.tolist()) | set(tr1.tolist())))
+        bp = x[base]
+        mid = bp.mean(axis=0)
+        axis = mid - c
+        axis /= np.linalg.norm(axis)
+        ids = {int(v): int(v) for v in base}
+        prev = ids
+        for lay in range(1, layers + 1):
+            f = lay / layers
+            shrink = 1.0 - (1.0 - tip) * f
+            layer_pts = mid + shrink * (bp - mid) + axis * (spike_len * radius * f)
+            cur = {}
+            for j, v in enumerate(base):
+                cur[int(v)] = nxt
+                nxt += 1
+            pts.append(layer_pts)
+            for tri in (tr0, tr1):
+                pr = [prev[int(v)] for v in tri] + [cur[int(v)] for v in tri]
+                tets.append(np.array(_prism_tets(pr), dtype=np.int64))
+            prev = cur
+    X = np.concatenate(pts)
+    T = np.concatenate([np.asarray(q, dtype=np.int64).reshape(-1, 4) for q in tets])
+    return X, _orient(X, T).astype(np.int32)
+
+
+def spiky_balls(n_balls=8, cells=32, radius=0.1, n_spikes=200, layers=132, seed=5, h=1.0 / 30, E=5e4, nu=0.45,
+                rho=1000.0):
+    """Large-scene stand-in shaped like the paper's teaser (puffer balls):
+    spiky balls (a 32^3-cell ball with 200 conical spikes of half its radius,
+    about 141k vertices and 355k tets each) in two layers of four, spaced
+    5 mm beyond their spike reach, the lower layer 5 mm above the ground;
+    E = 5e4 Pa, nu = 0.45, dt = 1/30 s, dhat = 1e-4 of the bounding-box
+    diagonal (the paper's value for this scene; the spike layers are 0.4 mm
+    thick, so the default 1e-3 would put a spike's own faces within dhat)."""
+    rng = np.random.default_rng(seed)
+    reach = radius * 1.5
+    sp = 2 * reach + 0.005
+    bodies = []
+    for b in range(n_balls):
+        layer, k = divmod(b, 4)
+        cx = (k % 2) * sp + rng.uniform(-0.01, 0.01)
+        cz = (k // 2) * sp + rng.uniform(-0.01, 0.01)
+        cy = 0.005 + reach + layer * (sp + 0.02)
+        x, t = spiky_ball_mesh(cells, radius, (cx, cy, cz), n_spikes=n_spikes, layers=layers, seed=seed + b)
+        bodies.append((x, t, E, nu, rho))
+    sc = _assemble(bodies)
+    bb = bbox_diag(sc["x0"])
+    sc["params"] = default_params(bb, h, E)
+    sc["params"]["dhat"] = 1e-4 * bb
+    sc["params"]["kappa"] = 10.0 * h * h * E * sc["params"]["dhat"]
+    sc["name"] = f"spiky_balls_{n_balls}"
+    return sc
