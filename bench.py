@@ -60,6 +60,10 @@ def parse():
                     help="timesteps of the ablation runs (MAS maintenance, CCD step; 0 = skip)")
     ap.add_argument("--stiffness-sweep", type=int, default=0,
                     help="timesteps per case of the stiffness sweep, MAS vs 3x3 block-Jacobi (0 = skip)")
+    ap.add_argument("--serve-stream", type=int, default=0,
+                    help="requests of the serving stream (Poisson arrivals at 200 timesteps/s over a pool of "
+                         "scenes; 0 = skip)")
+    ap.add_argument("--pool", type=int, default=200, help="config-3-sized scenes in the serving pool")
     ap.add_argument("--large", type=int, default=0,
                     help="timesteps of the large spiky-ball scene (8 balls, 1.13M vertices, 2.84M tets; 0 = skip)")
     ap.add_argument("--scale", type=int, default=5,
@@ -356,6 +360,111 @@ def run_stiffness_sweep(args, ipc, S, prec):
             "rows": out}
 
 
+def run_serve_stream(args, ipc, S, rate=200.0, torus_frac=0.1, n_torus=10, slots=8, margin_gb=40.0, wall_cap_s=240.0):
+    """Serving stream: timestep requests arrive as a Poisson process (`rate`
+    per second, seed 3), each for a scene drawn from a pool of `args.pool`
+    config-3-sized scenes (500-20k vertices, cubes, balls and rods) and, with
+    probability `torus_frac`, from `n_torus` stacks of interlocked torus rings
+    of 100k-300k vertices (10 of them: a hundred would need about 400 GB of
+    device memory, more than the GPU holds, and each first request would pay
+    a ~2 s scene creation). The small scenes are made resident before the
+    stream starts; a torus scene is created on its first request (admission:
+    while free device memory is below `margin_gb`, idle torus scenes are
+    destroyed, least recently used first) and stays resident after. Requests
+    run through ipc_server (continuous batching, `slots` at once); latency is
+    completion minus arrival, scene creation included. After `wall_cap_s`
+    no new request is submitted (the line then reports how many arrived and
+    ran)."""
+    import torch
+    rng = np.random.default_rng(3)
+    t0 = time.perf_counter()
+    pool = []
+    for k, sc in enumerate(S.batched_scenes(n_scenes=args.pool, seed=2)):
+        pool.append(ipc.Scene(sc, precision=ipc.IPC_PREC_FP32, use_torch_allocator=False))
+        if k % 50 == 49:
+            print(f"serving pool: {k + 1} scenes resident after {time.perf_counter() - t0:.1f} s", file=sys.stderr,
+                  flush=True)
+    pool_s = time.perf_counter() - t0
+    sizes = np.exp(rng.uniform(np.log(1e5), np.log(3e5), size=n_torus))
+    torus = {}            # id -> Scene (resident)
+    last_use = {}
+    busy = {}             # scene key -> live tickets
+    created = evicted = 0
+    free0, total = torch.cuda.mem_get_info()
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_stream))
+    picks = [("t", int(rng.integers(n_torus))) if rng.uniform() < torus_frac else ("s", int(rng.integers(args.pool)))
+             for _ in range(args.serve_stream)]
+    srv = ipc.Server(slots=slots)
+    live = {}
+    lat, steps_done, torus_steps, create_s = [], 0, 0, 0.0
+    nxt = 0
+    start = time.perf_counter()
+    capped = False
+    while nxt < len(picks) or live:
+        now = time.perf_counter() - start
+        if now > wall_cap_s and nxt < len(picks):
+            capped = True
+            picks = picks[:nxt]
+        while nxt < len(picks) and arrivals[nxt] <= now:
+            kind, i = picks[nxt]
+            if kind == "s":
+                scene = pool[i]
+            else:
+                if i not in torus:
+                    tc = time.perf_counter()
+                    while torch.cuda.mem_get_info()[0] < margin_gb * 1e9:
+                        idle = [j for j in torus if busy.get(("t", j), 0) == 0]
+                        if not idle:
+                            break
+                        j = min(idle, key=lambda q: last_use.get(q, 0.0))
+                        torus.pop(j).close()
+                        evicted += 1
+                    torus[i] = ipc.Scene(S.torus_stack(int(sizes[i]), seed=1000 + i), precision=ipc.IPC_PREC_FP32,
+                                         use_torch_allocator=False)
+                    created += 1
+                    create_s += time.perf_counter() - tc
+                    print(f"serving stream: torus scene {i} ({torus[i].nv} vertices) created in "
+                          f"{time.perf_counter() - tc:.1f} s at {now:.1f} s", file=sys.stderr, flush=True)
+                scene = torus[i]
+                last_use[i] = now
+                torus_steps += 1
+            busy[(kind, i)] = busy.get((kind, i), 0) + 1
+            live[srv.submit(scene, 1)] = (arrivals[nxt], (kind, i))
+            nxt += 1
+        done = []
+        for tk, (arr, key) in live.items():
+            r = srv.poll(tk)
+            if r is not None:
+                lat.append(1e3 * (time.perf_counter() - start - arr))
+                if key[0] == "t":
+                    print(f"serving stream: torus {key[1]} step done, {r['iters']} iterations, latency "
+                          f"{lat[-1]:.0f} ms", file=sys.stderr, flush=True)
+                busy[key] -= 1
+                steps_done += 1
+                done.append(tk)
+                if steps_done % 200 == 0:
+                    print(f"serving stream: {steps_done} done at {time.perf_counter() - start:.1f} s, torus created "
+                          f"{created}", file=sys.stderr, flush=True)
+        for tk in done:
+            del live[tk]
+        if not done:
+            time.sleep(2e-4)
+    wall = time.perf_counter() - start
+    srv.close()
+    for g in pool:
+        g.close()
+    for g in torus.values():
+        g.close()
+    lat.sort()
+    return {"requests": len(picks), "capped_at_s": wall_cap_s if capped else None, "rate_per_s": rate, "pool_scenes": args.pool, "torus_scenes": n_torus,
+            "torus_frac": torus_frac, "slots": slots, "pool_setup_s": pool_s,
+            "device_gb_after_pool": (total - free0) / 1e9, "torus_created": created, "torus_evicted": evicted,
+            "torus_create_s": create_s, "torus_requests": torus_steps, "timesteps_per_s": steps_done / wall,
+            "arrival_span_s": float(arrivals[-1]), "wall_s": wall,
+            "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "latency": "completion minus arrival, queueing and torus scene creation included"}
+
+
 def run_large(args, ipc, S, prec):
     """The large scene shaped like the paper's teaser: eight spiky balls
     (1,132,296 vertices, 2,840,064 tets), `args.large` timesteps of their drop
@@ -639,6 +748,7 @@ def main():
     ablation = run_ablation(args, ipc, S, prec) if args.ablation > 0 and world == 1 else None
     sweep = run_stiffness_sweep(args, ipc, S, prec) if args.stiffness_sweep > 0 and world == 1 else None
     large = run_large(args, ipc, S, prec) if args.large > 0 and world == 1 else None
+    stream = run_serve_stream(args, ipc, S) if args.serve_stream > 0 and world == 1 else None
     scale = run_scale(args, ipc, S, prec, rsize, flush, stream, peak) if args.scale > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
@@ -737,6 +847,7 @@ def main():
         "p50_ms": p50,
         "p99_ms": p99,
         "converged_steps": sum(s["converged"] for s in status),
+        "ccd_fallbacks": sum(s["ccd_fallbacks"] for s in status),
         "fp64_redo_blocks_last_restart": scene.fp64_blocks() if prec == ipc.IPC_PREC_FP32 else None,
         "plain_fp64_iters_per_s": plain["iters_per_s"] if plain else None,
         "plain_fp64_timesteps_per_s": plain["timesteps_per_s"] if plain else None,
@@ -751,6 +862,7 @@ def main():
         "ablation": ablation,
         "stiffness_sweep": sweep,
         "large": large,
+        "serve_stream": stream,
         "scale": scale,
         "cpu_baseline": cpu,
         "e2e": e2e,

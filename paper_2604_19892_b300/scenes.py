@@ -277,6 +277,8 @@ def mixed_scene(target_nv, seed, h=1.0 / 60):
         bodies.append((x, t, E, 0.4, 1000.0))
     sc = _assemble(bodies)
     sc["x_rest"] += rng.uniform(-1e-5, 1e-5, size=sc["x_rest"].shape)
+    # the jitter can flip a sliver tet of the mapped balls: orient again
+    sc["tets"] = _orient(sc["x_rest"], sc["tets"].astype(np.int64)).astype(np.int32)
     sc["x0"] = sc["x_rest"].copy()
     sc["params"] = default_params(bbox_diag(sc["x0"]), h, Emax)
     sc["name"] = f"mixed_{target_nv}_{seed}"
@@ -290,25 +292,32 @@ def batched_scenes(n_scenes=256, nv_lo=500, nv_hi=20000, seed=2):
     return [mixed_scene(int(s), seed * 100003 + i) for i, s in enumerate(sizes)]
 
 
-def torus_stack(target_nv, seed, h=1.0 / 60):
-    """Interlocked chain of torus rings (square tube cross-section)."""
+def torus_stack(target_nv, seed, h=1.0 / 60, R=0.1, r=0.015, n_around=96, n_tube=7):
+    """Interlocked chain of torus rings (square tube cross-section of side
+    2r, ring radius R) along x: rings alternate between flat (in the xz
+    plane) and upright (in the xy plane), centres R apart at one height, so
+    that every ring passes through the holes of its two neighbours; enough
+    rings for about target_nv vertices (6,144 per ring). The chain hangs
+    2 cm above the ground; dhat is 1e-3 of one ring's diagonal."""
     rng = np.random.default_rng(seed)
-    R, r = 0.1, 0.02
-    n_tube = 3
-    n_around = 24
     per_ring = n_around * (n_tube + 1) ** 2
     n_rings = max(2, int(round(target_nv / per_ring)))
+    yc = R + r + 0.02
     bodies = []
     for q in range(n_rings):
-        axis = 2 if q % 2 == 0 else 0
-        centre = (0.0 if q % 2 == 0 else R, 0.15 + q * (R + r * 0.2), 0.0)
-        # interlocked chain: alternate ring planes, offset by the radius
-        x, t = torus_mesh(n_around, n_tube, R, r, (0.0, 0.0, 0.0), axis=axis)
-        x = x[:, [0, 2, 1]] if axis == 2 else x
-        x = x + np.asarray(centre) + rng.uniform(-1e-4, 1e-4, size=3)
+        x, t = torus_mesh(n_around, n_tube, R, r, (0.0, 0.0, 0.0), axis=2)  # ring in the xy plane
+        if q % 2 == 0:
+            x = x[:, [0, 2, 1]]  # flat: into the xz plane
+        x = x + np.array([q * R, yc, 0.0]) + rng.uniform(-1e-4, 1e-4, size=3)
+        # swapping two axes (and the bend) can reverse the tets' orientation
+        t = _orient(x, t.astype(np.int64)).astype(np.int32)
         bodies.append((x, t, 1e5, 0.4, 1000.0))
     sc = _assemble(bodies)
-    sc["params"] = default_params(bbox_diag(sc["x0"]), h, 1e5)
+    # dhat from one ring's size: 1e-3 of the whole chain's diagonal (metres
+    # long) would exceed the rings' own cells and put every ring in contact
+    # with itself
+    ring = bodies[0][0]
+    sc["params"] = default_params(bbox_diag(ring), h, 1e5)
     sc["name"] = f"torus_stack_{n_rings}"
     return sc
 
