@@ -145,6 +145,9 @@ typedef struct ipc_params {
                                 exits. 0 makes every such wait report a
                                 timeout without polling (a test of the error
                                 path that needs no fault). */
+    int apply_ctas;          /* CTAs per SM of the persistent MAS block apply;
+                                0 (default): picked at ipc_scene_create by
+                                timing the candidates (IPC_Q_APPLY_CTAS) */
 } ipc_params;
 
 /* Device allocator used for all scene memory; NULL functions = cudaMalloc. */
@@ -179,7 +182,8 @@ void ipc_default_params(ipc_params* p);
  * extracts the boundary surface, computes lumped mass rho V / 4 and rest
  * shapes, builds the MAS hierarchy (32-vertex subdomains by greedy BFS over
  * mesh adjacency, supplement Sec. 1.2), allocates device state and copies
- * it up.  Fails with IPC_ERR_INTERSECTING if a contact of the initial state
+ * it up, and picks the block apply's launch configuration by timing (see
+ * IPC_Q_APPLY_CTAS).  Fails with IPC_ERR_INTERSECTING if a contact of the initial state
  * has distance <= 0.  `alloc` may be NULL. */
 int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params,
                      const ipc_alloc_fns* alloc, ipc_scene** out);
@@ -216,10 +220,15 @@ typedef enum ipc_query_kind {
                                 (Sec. 4.2 inverse with the row-norm bound), 0
                                 before the first restart; FP64 bulk: every
                                 block. */
-    IPC_Q_PIVOT_FIXES = 13   /* int: blocks of the last restart whose final
+    IPC_Q_PIVOT_FIXES = 13,  /* int: blocks of the last restart whose final
                                 (FP64) factorisation floored or raised a
                                 pivot: 0 means every stored inverse is that of
                                 a plain Cholesky factorisation */
+    IPC_Q_APPLY_CTAS = 14    /* int: CTAs per SM of the persistent MAS block
+                                apply, picked at ipc_scene_create by timing
+                                the candidates the kernel's shared memory
+                                allows on this scene's blocks (the project's
+                                autotuner; results do not depend on it) */
 } ipc_query_kind;
 
 /* Copy a piece of state into host memory dst (dst_bytes long). */

@@ -559,6 +559,15 @@ int setup_dev(ipc_scene* s) {
     CUDA_TRY(cudaMemset(D.C.count, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(D.Ct.count, 0, sizeof(int)));
     CUDA_TRY(cudaDeviceSynchronize());
+    // launch configuration of the per-iteration block apply, timed on this
+    // scene's block count (the autotuner; its values are overwritten by the
+    // first RebuildMAS)
+    if (p.apply_ctas > 0)
+        D.apply_ctas = p.apply_ctas;
+    else
+        autotune_apply(D, (cudaStream_t)0);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemset(D.S, 0, sizeof(Scalars)));
     return 0;
 }
 
@@ -1383,6 +1392,7 @@ void ipc_default_params(ipc_params* p) {
     p->fp32_pivot_floor = 1e-6;
     p->grid_pair_capacity = 0;
     p->wait_polls = 1 << 22;
+    p->apply_ctas = 0;
 }
 
 const char* ipc_last_error(void) { return g_err.c_str(); }
@@ -1392,7 +1402,8 @@ int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params, const
     *out = nullptr;
     if (!(params->h > 0) || !(params->dhat > 0) || !(params->kappa > 0) || params->K < 0 || params->K > kMaxK ||
         params->iter_max <= 0 || params->levels_max < 1 || params->ls_max < 0 || params->mas_mode < 0 ||
-        params->mas_mode > 3 || params->ccd_mode < 0 || params->ccd_mode > 1 ||
+        params->mas_mode > 3 || params->ccd_mode < 0 || params->ccd_mode > 1 || params->apply_ctas < 0 ||
+        params->apply_ctas > 16 ||
         (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_FP32 &&
          params->precision != IPC_PREC_BF16_MAS) ||
         params->broad_phase < 0 ||
@@ -1551,6 +1562,10 @@ int ipc_query(ipc_scene* s, int what, void* dst, size_t bytes, void* stream) {
             CUDA_TRY(cudaStreamSynchronize(st));
             return IPC_OK;
         }
+        case IPC_Q_APPLY_CTAS:
+            if (!need(sizeof(int))) return fail(IPC_ERR_INVALID, "destination too small");
+            *(int*)dst = f64 ? s->dd.apply_ctas : s->df.apply_ctas;
+            return IPC_OK;
         case IPC_Q_BBOX_DIAG:
             if (!need(sizeof(double))) return fail(IPC_ERR_INVALID, "destination too small");
             *(double*)dst = s->hm.bbox_diag;

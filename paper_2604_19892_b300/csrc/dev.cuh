@@ -113,6 +113,7 @@ struct Dev {
     // allowance of the two computed energies)
     double tau_rel, tau_abs;
     int wait_polls;                        // polls of a bounded wait on a bulk copy
+    int apply_ctas;                        // persistent plain block apply: CTAs per SM (autotuned; 0 = default)
     double gravity[3];
     int has_ground;
     double gn[3], goff;

@@ -25,6 +25,7 @@
 // returns z_d = W'^T (V_g - V_U lambda) = B g_d - B U lambda (Eq. 7).  Coarse
 // levels stay frozen (Eq. 8).
 #include <algorithm>
+#include <vector>
 #include <type_traits>
 
 #include <cuda_bf16.h>
@@ -2067,7 +2068,8 @@ void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool 
             if (woodbury)
                 KL(k_block_apply<R, true><<<nb, 96, kW16 * 2, st>>>(D, g, z, C, 1));
             else
-                KL(k_block_apply_plain16<<<std::min(nb, 8 * sms), 96, 2 * kW16 * 2, st>>>(D, g, z));
+                KL(k_block_apply_plain16<<<std::min(nb, (D.apply_ctas > 0 ? D.apply_ctas : 8) * sms), 96,
+                                           2 * kW16 * 2, st>>>(D, g, z));
             return;
         }
     }
@@ -2076,9 +2078,60 @@ void launch_blocks(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool 
     } else {
         // persistent CTAs: as many as fit at once (two FP64 rings per SM, five
         // FP32), never more than the blocks
-        const int per_sm = sizeof(R) == 8 ? 2 : kApplyCtasPerSm;
+        const int per_sm = D.apply_ctas > 0 ? D.apply_ctas : (sizeof(R) == 8 ? 2 : kApplyCtasPerSm);
         KL(k_block_apply_plain<R><<<std::min(nb, per_sm * sms), 96, 2 * kW * sizeof(R), st>>>(D, g, z));
     }
+}
+
+template <class R>
+int autotune_apply(Dev<R>& D, cudaStream_t st) {
+    // candidate CTAs per SM of the persistent plain apply, bounded by its
+    // 2-slot ring in shared memory: FP64 factors 38.4 KB a slot, FP32 19.2
+    // KB, BF16 10.7 KB
+    std::vector<int> cand;
+    if (sizeof(R) == 8)
+        cand = {1, 2};
+    else if (D.blocks16)
+        cand = {4, 6, 8, 10};
+    else
+        cand = {2, 3, 4, 5};
+    if (D.jac || D.blk_off[D.nlev] < 2 * 148) return D.apply_ctas = cand.back();  // small scenes: one block a CTA
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return D.apply_ctas = 0;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return D.apply_ctas = 0;
+    }
+    // zero factors and gradient: the timing does not depend on the values
+    const int nb = D.blk_off[D.nlev];
+    if (D.blocks16)
+        cudaMemsetAsync(D.blocks16, 0, (size_t)nb * kW16 * 2, st);
+    else
+        cudaMemsetAsync(D.blocks, 0, (size_t)nb * kW * sizeof(R), st);
+    cudaMemsetAsync(D.g, 0, sizeof(R) * 3 * (size_t)D.nv, st);
+    if (D.nlev > 1) cudaMemsetAsync(D.coarse_r, 0, sizeof(R) * (size_t)D.coarse_off[D.nlev], st);
+    int best = 0;
+    float best_ms = 0.f;
+    constexpr int kReps = 8;
+    for (int c : cand) {
+        D.apply_ctas = c;
+        launch_blocks(D, D.g, D.z, D.C, false, st);  // warm
+        cudaEventRecord(a, st);
+        for (int r = 0; r < kReps; ++r) launch_blocks(D, D.g, D.z, D.C, false, st);
+        cudaEventRecord(b, st);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            best = 0;
+            break;
+        }
+        if (best == 0 || ms < best_ms) {
+            best = c;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return D.apply_ctas = best;
 }
 
 template <class R>
@@ -2096,6 +2149,7 @@ void launch_precond(const Dev<R>& D, const R* g, R* z, const ContactBuf& C, bool
 #define INST(R)                                                                                            \
     template void launch_restart<R>(const Dev<R>&, const double*, const ContactBuf&, cudaStream_t);         \
     template void launch_invert<R>(const Dev<R>&, cudaStream_t);                                          \
+    template int autotune_apply<R>(Dev<R>&, cudaStream_t);                                                \
     template void launch_classify<R>(const Dev<R>&, const ContactBuf&, cudaStream_t);                     \
     template void launch_precond<R>(const Dev<R>&, const R*, R*, const ContactBuf&, bool, cudaStream_t);   \
     template void launch_restrict<R>(const Dev<R>&, const R*, cudaStream_t);                              \

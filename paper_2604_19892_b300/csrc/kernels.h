@@ -24,6 +24,10 @@ template <class R> void launch_detect(const Dev<R>& D, const double* x, const Co
 template <class R> void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st);
 // the batched inversion of the assembled blocks alone (part of launch_restart)
 template <class R> void launch_invert(const Dev<R>& D, cudaStream_t st);
+// picks the CTAs per SM of the persistent plain block apply by timing the
+// candidates on this scene's blocks (zeroed first), sets D.apply_ctas and
+// returns it (0 if timing failed: the default is used)
+template <class R> int autotune_apply(Dev<R>& D, cudaStream_t st);
 // classify C against C_base, per-subdomain top-K (Sec. 4.1.1)
 template <class R> void launch_classify(const Dev<R>& D, const ContactBuf& C, cudaStream_t st);
 // z = P g with optional Woodbury update (Eq. 7-8)

@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("levels_max", C.c_int), ("ls_max", C.c_int), ("precision", C.c_int),
                 ("contact_capacity", C.c_int), ("broad_phase", C.c_int), ("mas_mode", C.c_int),
                 ("ccd_mode", C.c_int), ("graphs", C.c_int), ("fp32_pivot_floor", C.c_double),
-                ("grid_pair_capacity", C.c_int), ("wait_polls", C.c_int)]
+                ("grid_pair_capacity", C.c_int), ("wait_polls", C.c_int), ("apply_ctas", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -82,7 +82,7 @@ class Profile(C.Structure):
 STAGES = ["restart", "classify", "mas_blocks", "forms", "direction", "ccd", "trial_eval", "other"]
 
 Q_POSITIONS, Q_VELOCITIES, Q_N_VERTS, Q_N_CONTACTS, Q_SUBDOMAIN_ALPHA, Q_N_SUBDOMAINS, Q_TRACE_LEN, Q_TRACE, \
-    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG, Q_N_BODIES, Q_FP64_BLOCKS, Q_PIVOT_FIXES = range(14)
+    Q_SURFACE_COUNTS, Q_LEVEL_MAP, Q_BBOX_DIAG, Q_N_BODIES, Q_FP64_BLOCKS, Q_PIVOT_FIXES, Q_APPLY_CTAS = range(15)
 
 _lib = None
 
@@ -193,7 +193,7 @@ def default_params(sc_params: dict, precision: int = IPC_PREC_FP64) -> Params:
     lib.ipc_default_params(C.byref(p))
     for k in ("h", "dhat", "kappa", "tol", "delta", "eps_rot_deg", "ccd_shrink", "eps_sing", "eps_abs", "K",
               "iter_max", "levels_max", "ls_max", "broad_phase", "mas_mode", "ccd_mode", "graphs",
-              "fp32_pivot_floor", "grid_pair_capacity", "wait_polls"):
+              "fp32_pivot_floor", "grid_pair_capacity", "wait_polls", "apply_ctas"):
         if k in sc_params:
             setattr(p, k, type(getattr(p, k))(sc_params[k]))
     p.precision = precision
@@ -307,6 +307,11 @@ class Scene:
         """Subdomain blocks the last restart inverted in FP64 (FP32 bulk: the
         blocks whose FP32 factorisation would floor or raise a pivot)."""
         return int(self._query_array(Q_FP64_BLOCKS, 1, np.int32)[0])
+
+    def apply_ctas(self):
+        """CTAs per SM of the persistent block apply chosen by the library's
+        autotuner at scene creation."""
+        return int(self._query_array(Q_APPLY_CTAS, 1, np.int32)[0])
 
     def pivot_fixes(self):
         """Blocks of the last restart whose final (FP64) factorisation

@@ -77,3 +77,4 @@ def test_params_mirror_matches_the_header():
     assert p.fp32_pivot_floor == 1e-6
     assert p.grid_pair_capacity == 0
     assert p.wait_polls == 1 << 22
+    assert p.apply_ctas == 0

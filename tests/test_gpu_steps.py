@@ -91,6 +91,30 @@ def test_bf16_factor_steps_follow_the_fp64_oracle(lib):
     assert max(errs) <= 1e-5, errs
 
 
+def test_autotuned_apply_configuration_does_not_change_results(lib):
+    """The autotuner picks the persistent apply's CTAs per SM among the
+    candidates its shared memory allows; the preconditioner is the same
+    whatever the choice (each block's arithmetic does not depend on the
+    grid), here on a scene large enough to be tuned (46,656 vertices): every
+    forced candidate gives the tuned result to the rounding of the restart's
+    atomically summed assembly."""
+    from paper_2604_19892_b300 import scenes as S
+    sc = S.sphere_pile()
+    rng = np.random.default_rng(4)
+    grad = rng.normal(size=sc["x0"].shape)
+    for prec, cands in ((lib.IPC_PREC_FP32, (2, 3, 4, 5)), (lib.IPC_PREC_BF16_MAS, (4, 6, 8, 10))):
+        g = lib.Scene(sc, precision=prec)
+        assert g.apply_ctas() in cands
+        z0 = g.precond_apply(sc["x0"], grad)
+        g.close()
+        for c in cands:
+            h = lib.Scene(sc, precision=prec, params={"apply_ctas": c})
+            assert h.apply_ctas() == c
+            z = h.precond_apply(sc["x0"], grad)
+            assert np.linalg.norm(z - z0) <= 1e-5 * np.linalg.norm(z0), (prec, c)
+            h.close()
+
+
 def test_exhausted_copy_wait_reports_timeout_and_leaves_the_context_usable(lib):
     """wait_polls = 0: every bounded wait of the block-apply CTAs reports a
     timeout without polling; ipc_step stops with IPC_ERR_TIMEOUT before z is
