@@ -194,7 +194,11 @@ def stage_bytes(nv, nt, nblocks, rsize):
 # DRAM bytes per launch (read + write) from one ncu capture of each kernel in
 # its current form on the same workload (profiles/ holds the summaries and
 # commands); None where the kernel changed since its last capture
-TRAFFIC = {}
+TRAFFIC = {
+    # k_invert_tiled (FP32 first pass of the block inversion) on the 64-sphere
+    # pile, 1,507 blocks: 65,064,448 B read + 3,064,832 B written
+    ("invert", "fp32"): 65064448 + 3064832,
+}
 
 
 def host_cpu():
@@ -707,10 +711,12 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     fl = invert_flops(nblocks)
+    tr_inv = TRAFFIC.get(("invert", args.precision))
     roof = {
         "invert": {"bound": "alu", "achieved": fl / (stage_us["invert"] * 1e-6) / 1e12, "peak": alu_peak,
                    "unit": "TFLOP/s", "frac": fl / (stage_us["invert"] * 1e-6) / 1e12 / alu_peak,
-                   "traffic": None, "flops_per_launch": fl, "avg_us": stage_us["invert"],
+                   "traffic": tr_inv if nblocks == 1507 else None, "flops_per_launch": fl,
+                   "avg_us": stage_us["invert"],
                    "kernel": "k_invert_tiled" if prec == ipc.IPC_PREC_FP32 else "k_invert",
                    "peak_source": (f"FP32 FMA peak from unit counts: {sm_count} SMs x 128 lanes x 2 flops x "
                                    f"{sm_mhz:.0f} MHz (median SM clock of the timed region)")},

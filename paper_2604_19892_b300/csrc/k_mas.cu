@@ -1433,6 +1433,24 @@ __device__ __forceinline__ void upper_apply(const R* __restrict__ Ws, const R* _
     }
 }
 
+// The right-hand side entry of thread tid for block b: its node (< 0 for a
+// padded slot) and value; level 0 reads g, coarse levels their restricted
+// residuals. Two dependent global loads, issued one block ahead by the
+// persistent applies so their latency overlaps the current block's products.
+template <class R>
+__device__ __forceinline__ void gather_rhs(const Dev<R>& D, const R* __restrict__ g, int b, int tid, int& l, int& node,
+                                           R& val) {
+    l = 0;
+    while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
+    const int grp = b - D.blk_off[l];
+    node = D.members[l][(size_t)grp * kSub + tid / 3];
+    const int comp = tid % 3;
+    if (node < 0)
+        val = (R)0;
+    else
+        val = l == 0 ? g[3 * node + comp] : D.coarse_r[D.coarse_off[l] + 3 * node + comp];
+}
+
 // Block apply without Woodbury updates (restart iterations, coarse levels):
 // z_b = B_b r_b = W'^T (W' r_b), 96 threads per CTA. The CTAs are persistent
 // (a few per SM) and stream their blocks through a 2-stage ring in shared
@@ -1465,19 +1483,16 @@ __global__ void __launch_bounds__(96) k_block_apply_plain(Dev<R> D, const R* __r
         }
     }
     int it = 0;
+    int l_n = 0, node_n = -1;
+    R val_n = (R)0;
+    if (first < nb) gather_rhs(D, g, first, tid, l_n, node_n, val_n);
     for (int b = first; b < nb; b += stride, ++it) {
         const int slot = it & 1;
         const uint32_t parity = (uint32_t)(it >> 1) & 1u;
         const R* Ws = reinterpret_cast<const R*>(bsm + slot * kBytes);
-        int l = 0;
-        while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
-        const int grp = b - D.blk_off[l];
-        const int node = D.members[l][(size_t)grp * kSub + tid / 3];
-        const int comp = tid % 3;
-        if (l == 0)
-            rhs[tid] = node >= 0 ? g[3 * node + comp] : (R)0;
-        else
-            rhs[tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : (R)0;
+        const int l = l_n, node = node_n, comp = tid % 3;
+        rhs[tid] = val_n;
+        if (b + stride < nb) gather_rhs(D, g, b + stride, tid, l_n, node_n, val_n);  // next block's, in flight
         __syncthreads();  // rhs complete; the barriers' initialisation is visible
         const bool arrived = mbar_wait(&bar[slot], parity, D.wait_polls);
         if (__syncthreads_or(!arrived)) {
@@ -1671,19 +1686,16 @@ __global__ void __launch_bounds__(96) k_block_apply_plain16(Dev<float> D, const 
         }
     }
     int it = 0;
+    int l_n = 0, node_n = -1;
+    float val_n = 0.f;
+    if (first < nb) gather_rhs(D, g, first, tid, l_n, node_n, val_n);
     for (int b = first; b < nb; b += stride, ++it) {
         const int slot = it & 1;
         const uint32_t parity = (uint32_t)(it >> 1) & 1u;
         const __nv_bfloat16* Wt = reinterpret_cast<const __nv_bfloat16*>(bsm + slot * kBytes);
-        int l = 0;
-        while (l + 1 < D.nlev && b >= D.blk_off[l + 1]) ++l;
-        const int grp = b - D.blk_off[l];
-        const int node = D.members[l][(size_t)grp * kSub + tid / 3];
-        const int comp = tid % 3;
-        if (l == 0)
-            rhs[tid] = node >= 0 ? g[3 * node + comp] : 0.f;
-        else
-            rhs[tid] = node >= 0 ? D.coarse_r[D.coarse_off[l] + 3 * node + comp] : 0.f;
+        const int l = l_n, node = node_n, comp = tid % 3;
+        rhs[tid] = val_n;
+        if (b + stride < nb) gather_rhs(D, g, b + stride, tid, l_n, node_n, val_n);  // next block's, in flight
         __syncthreads();
         const bool arrived = mbar_wait(&bar[slot], parity, D.wait_polls);
         if (__syncthreads_or(!arrived)) {
