@@ -281,6 +281,17 @@ int ipc_profile_read(ipc_scene* s, ipc_profile* out);
 int ipc_profile_replay(ipc_scene* s, int stage, int reps, void* flush, size_t flush_bytes, void* stream,
                        double* ms_mean);
 
+/* Measured FMA throughput of the SM's SIMT pipes on the current device, in
+ * TFLOP/s (2 flops per FMA): every thread of a grid that fills each SM runs 8
+ * independent FMA chains; one launch of about target_ms is timed with CUDA
+ * events after a calibration and a warm-up launch.  precision:
+ * IPC_PREC_FP32 or IPC_PREC_FP64.  The denominator of an ALU-bound kernel's
+ * roofline (the FP32 block inversion) beside lanes x 2 x clock.  Allocates
+ * and frees one device buffer; synchronises the device.  IPC_ERR_INVALID for
+ * another precision or target_ms outside (0, 1000]; IPC_ERR_CUDA on a CUDA
+ * error. */
+int ipc_profile_fma_peak(int precision, double target_ms, double* tflops);
+
 /* Number of CUDA kernels this library has launched in the process so far
  * (all scenes, all calls). */
 long long ipc_kernel_launches(void);

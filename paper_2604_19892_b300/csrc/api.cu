@@ -52,6 +52,7 @@ struct Arena {
     bool ok = true;
     size_t bytes = 0;
     void* get(size_t n) {
+        if (!ok) return nullptr;  // no further requests once one has failed
         if (n == 0) n = 16;
         n = (n + 255) & ~(size_t)255;
         void* p = nullptr;
@@ -100,6 +101,7 @@ struct HostView {
     Scalars S;
     int nC, nCt;
     int cand_n[2];
+    unsigned long long nonfinite;
 };
 
 }  // namespace
@@ -149,6 +151,7 @@ struct ipc_scene {
     Dev<float> df;
     int prec = IPC_PREC_FP64;
     HostView* hv = nullptr;  // pinned
+    unsigned long long* nonfinite = nullptr;  // device counter of ipc_set_state's check
     std::vector<ipc_iter_record> trace;
     StageProf prof;
     // cached candidate pairs: built with margin cand_delta; cand_bound bounds
@@ -492,6 +495,7 @@ int setup_dev(ipc_scene* s) {
     D.gpair = A.arr<int2>(D.gpair_cap);
     D.gpair_n = A.arr<int>(2);
     D.S = A.arr<Scalars>(1);
+    s->nonfinite = A.arr<unsigned long long>(1);
     if (!A.ok) return fail(IPC_ERR_OOM, "scene: device allocation failed");
 
     D.tets = d_tets;
@@ -792,6 +796,11 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
     if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");
     if (s->hv->S.nonpos)
         return fail(IPC_ERR_INTERSECTING, "a contact has non-positive distance");
+    // an energy that overflowed (e.g. velocities so large that |x - x~|^2
+    // exceeds the FP64 range) stops the timestep before any kernel uses it;
+    // x is left as it was
+    if (!std::isfinite(s->hv->S.E_k))
+        return fail(IPC_ERR_NUMERIC, "non-finite energy at the start of the timestep");
     s->trace.clear();
     double Ek = s->hv->S.E_k;
     double min_dist = s->hv->S.min_dist;
@@ -1470,6 +1479,21 @@ int ipc_set_state(ipc_scene* s, const double* x, const double* v, int on_device,
     double* dx = s->prec == IPC_PREC_FP64 ? s->dd.x : s->df.x;
     double* dv = s->prec == IPC_PREC_FP64 ? s->dd.v : s->df.v;
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // a non-finite coordinate is refused before it reaches the scene: no
+    // kernel ever sees one from the caller
+    unsigned long long bad = 0;
+    if (on_device) {
+        CUDA_TRY(cudaMemsetAsync(s->nonfinite, 0, sizeof(unsigned long long), st));
+        KL(k_count_nonfinite<double><<<64, 256, 0, st>>>(x, n3, s->nonfinite));
+        if (v) KL(k_count_nonfinite<double><<<64, 256, 0, st>>>(v, n3, s->nonfinite));
+        CUDA_TRY(cudaMemcpyAsync(&s->hv->nonfinite, s->nonfinite, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        bad = s->hv->nonfinite;
+    } else {
+        for (size_t i = 0; i < n3; ++i) bad += !std::isfinite(x[i]) + (v ? !std::isfinite(v[i]) : 0);
+    }
+    if (bad) return fail(IPC_ERR_INVALID, "non-finite position or velocity (state unchanged)");
     CUDA_TRY(cudaMemcpyAsync(dx, x, sizeof(double) * n3, kind, st));
     s->cand_ok = false;
     if (v)
@@ -1658,6 +1682,15 @@ int ipc_profile_replay(ipc_scene* s, int stage, int reps, void* flush, size_t fl
     cudaStream_t st = (cudaStream_t)stream;
     return s->prec == IPC_PREC_FP64 ? replay_impl<double>(s, stage, reps, flush, flush_bytes, st, ms_mean)
                                     : replay_impl<float>(s, stage, reps, flush, flush_bytes, st, ms_mean);
+}
+
+int ipc_profile_fma_peak(int precision, double target_ms, double* tflops) {
+    if (!tflops || !(target_ms > 0.0) || target_ms > 1000.0 ||
+        (precision != IPC_PREC_FP64 && precision != IPC_PREC_FP32))
+        return fail(IPC_ERR_INVALID, "fma peak: precision FP64 or FP32, 0 < target_ms <= 1000");
+    const int r = precision == IPC_PREC_FP64 ? measure_fma_peak<double>(target_ms, tflops)
+                                             : measure_fma_peak<float>(target_ms, tflops);
+    return r == 0 ? IPC_OK : fail(IPC_ERR_CUDA, "fma peak: CUDA error");
 }
 
 int ipc_precond_apply_noalloc(ipc_scene* s, const void* g_dev, void* z_dev, void* stream) {

@@ -119,6 +119,9 @@ __device__ __forceinline__ float fdot(f3 a, f3 b) { return a.x * b.x + a.y * b.y
 __device__ __forceinline__ f3 fmad3(f3 a, float t, f3 b) { return {a.x + t * b.x, a.y + t * b.y, a.z + t * b.z}; }
 __device__ __forceinline__ float fclamp01(float t) { return fminf(fmaxf(t, 0.f), 1.f); }
 
+// Squared point-triangle distance by the Voronoi regions of the triangle
+// (vertices, edges, face), the published closest-point method of C. Ericson,
+// Real-Time Collision Detection (2005), Sec. 5.1.5.
 __device__ inline float pt_dist2_f(f3 p, f3 a, f3 b, f3 c) {
     f3 ab = fsub(b, a), ac = fsub(c, a), ap = fsub(p, a);
     float d1 = fdot(ab, ap), d2 = fdot(ac, ap);
@@ -150,6 +153,9 @@ __device__ inline float pt_dist2_f(f3 p, f3 a, f3 b, f3 c) {
     return fdot(r, r);
 }
 
+// Squared segment-segment distance: the unconstrained line parameters clamped
+// to [0, 1], the other parameter recomputed and clamped in turn (Ericson,
+// Real-Time Collision Detection (2005), Sec. 5.1.9).
 __device__ inline float ee_dist2_f(f3 p1, f3 q1, f3 p2, f3 q2) {
     f3 d1 = fsub(q1, p1), d2 = fsub(q2, p2), r = fsub(p1, p2);
     float a = fdot(d1, d1), e = fdot(d2, d2), f = fdot(d2, r);

@@ -59,6 +59,9 @@ template <class R> void launch_ccd_list(const Dev<R>& D, cudaStream_t st, int pa
 template <class R> void launch_global_alpha(const Dev<R>& D, cudaStream_t st);
 // S->accepted = E_try <= E_k + tau (the rounding allowance of the energies)
 template <class R> void launch_accept(const Dev<R>& D, cudaStream_t st);
+// FMA throughput of the SIMT pipe for T (float or double) in TFLOP/s, from one
+// launch of about target_ms on the current device; 0 on success
+template <class T> int measure_fma_peak(double target_ms, double* tflops);
 // H_base-only forms for evaluation entry points
 template <class R> void launch_zero_scalars(const Dev<R>& D, cudaStream_t st);
 

@@ -21,7 +21,11 @@ IPC_OK = 0
 IPC_NOT_CONVERGED = 1
 IPC_PENDING = 2
 IPC_ERR_INVALID = -1
+IPC_ERR_INTERSECTING = -2
+IPC_ERR_OOM = -3
+IPC_ERR_NUMERIC = -4
 IPC_ERR_TIMEOUT = -5
+IPC_ERR_CUDA = -6
 IPC_ERR_CAPACITY = -7
 IPC_PREC_FP64 = 0
 IPC_PREC_FP32 = 1
@@ -113,7 +117,15 @@ EXPORTS = {
     "ipc_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "ipc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
     "ipc_kernel_launches": (C.c_longlong, []),
+    "ipc_profile_fma_peak": (C.c_int, [C.c_int, C.c_double, C.POINTER(C.c_double)]),
 }
+
+
+def fma_peak_tflops(precision: int = IPC_PREC_FP32, target_ms: float = 20.0) -> float:
+    """Measured FMA throughput of the SIMT pipes (ipc_profile_fma_peak)."""
+    out = C.c_double()
+    _check(load().ipc_profile_fma_peak(int(precision), float(target_ms), C.byref(out)))
+    return out.value
 
 
 def kernel_launches() -> int:
@@ -206,7 +218,7 @@ class Scene:
     """One resident scene on the current CUDA device."""
 
     def __init__(self, sc: dict, params: dict | None = None, precision: int = IPC_PREC_FP64,
-                 use_torch_allocator: bool = True, stream=None):
+                 use_torch_allocator: bool = True, stream=None, alloc_fns: "AllocFns | None" = None):
         lib = load()
         self.lib = lib
         p = dict(sc["params"])
@@ -242,7 +254,10 @@ class Scene:
         self._prm = default_params(p, precision)
         self._alloc = None
         fns = None
-        if use_torch_allocator:
+        if alloc_fns is not None:  # the caller's device allocator (kept alive with the scene)
+            self._alloc = alloc_fns
+            fns = C.byref(alloc_fns)
+        elif use_torch_allocator:
             import torch
             self._alloc = _TorchAllocator(torch.cuda.current_device())
             fns = C.byref(self._alloc.fns)

@@ -117,3 +117,39 @@ def test_fullsize_ccd(pile):
     assert ao.min() < 1.0
     np.testing.assert_allclose(ag, ao, rtol=0, atol=1e-6)
     np.testing.assert_allclose(abg, abo, rtol=0, atol=1e-6)
+
+
+def test_fullsize_woodbury_preconditioner(pile):
+    """The Woodbury-patched preconditioner (Eq. 7) of the benchmarked form:
+    P_base at the state eps = 0.9 dhat, the contacts of the state eps = 0.4
+    dhat (the same pairs, stiffer: dS = k - k_base) patched in per
+    subdomain. The oracle rebuilds the level-0 inverses of H_base + U U^T
+    instead."""
+    sc, x, pairs, g, o, rng = pile
+    xb, _ = pile_contact_state(sc, eps_frac=0.9)
+    xc, _ = pile_contact_state(sc, eps_frac=0.4)
+    kb, kc = o.contacts(xb)["k"], o.contacts(xc)["k"]
+    assert len(kb) > 0 and len(kc) >= len(kb) and kc.max() > kb.max()
+    grad = rng.normal(size=x.shape)
+    zg = g.precond_apply(xb, grad, xc)
+    zo = o.precond_apply(xb, grad, xc)
+    assert np.linalg.norm(zg - zo) <= 1e-3 * np.linalg.norm(zo)
+    assert float(np.sum(zg * grad)) > 0
+
+
+def test_fullsize_forms(pile):
+    """The three quadratic forms of H~ (Eq. 6) at full size in the FP32 bulk.
+    zHz and pHp are sums of non-negative per-element terms: relative 2e-5.
+    For zHp, sum_t |z_t H_t p_t| <= sqrt(zHz pHp) (Cauchy-Schwarz per element
+    and over elements) bounds the summed magnitudes, so the FP32 rounding of
+    the sum is within 2e-5 of that product."""
+    sc, x, pairs, g, o, rng = pile
+    xb, _ = pile_contact_state(sc, eps_frac=0.9)
+    xc, _ = pile_contact_state(sc, eps_frac=0.4)
+    z, p = rng.normal(size=(2,) + x.shape)
+    for cur in (None, xc):
+        fg = g.hess_forms(xb, z, p, cur)
+        fo = o.hess_forms(xb, z, p, cur)
+        assert fg[0] == pytest.approx(fo[0], rel=2e-5)
+        assert fg[2] == pytest.approx(fo[2], rel=2e-5)
+        assert abs(fg[1] - fo[1]) <= 2e-5 * np.sqrt(fo[0] * fo[2])

@@ -78,3 +78,40 @@ def test_server_orders_requests_of_one_scene():
         assert srv.wait(t)["converged"]
     srv.close()
     assert float(np.abs(g.positions() - x3).max()) / _bbox(sc["x0"]) <= 1e-6
+
+
+def test_numeric_failure_of_one_scene_leaves_the_others_as_alone():
+    # one served scene gets velocities so large that its inertia energy
+    # overflows: its request fails with IPC_ERR_NUMERIC, the requests of the
+    # other scenes running beside it give their solo results, and the failed
+    # scene steps normally again once its state is reset
+    import torch
+    from paper_2604_19892_b300 import ipc
+
+    torch.cuda.set_device(0)
+    scs = [S.mixed_scene(nv, seed) for nv, seed in ((1200, 41), (2500, 42), (1800, 43))]
+    scenes = [ipc.Scene(sc, precision=ipc.IPC_PREC_FP32, use_torch_allocator=False) for sc in scs]
+    alone = []
+    for g, sc in zip(scenes, scs):
+        g.set_state(sc["x0"], sc["v0"])
+        assert g.step(2)["converged"]
+        alone.append(g.positions())
+        g.set_state(sc["x0"], sc["v0"])
+    bad = 1
+    scenes[bad].set_state(scs[bad]["x0"], np.full_like(scs[bad]["x0"], 1e200))
+    srv = ipc.Server(slots=3)
+    tickets = [srv.submit(g, 2) for g in scenes]
+    for i, (t, g, sc, xa) in enumerate(zip(tickets, scenes, scs, alone)):
+        if i == bad:
+            with pytest.raises(ipc.IPCError) as e:
+                srv.wait(t)
+            assert e.value.code == ipc.IPC_ERR_NUMERIC
+            assert np.array_equal(g.positions(), sc["x0"])  # x untouched
+            continue
+        assert srv.wait(t)["converged"]
+        assert float(np.abs(g.positions() - xa).max()) / _bbox(sc["x0"]) <= 1e-6
+    g, sc = scenes[bad], scs[bad]
+    g.set_state(sc["x0"], sc["v0"])
+    assert srv.wait(srv.submit(g, 2))["converged"]
+    srv.close()
+    assert float(np.abs(g.positions() - alone[bad]).max()) / _bbox(sc["x0"]) <= 1e-6

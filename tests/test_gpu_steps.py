@@ -129,3 +129,62 @@ def test_exhausted_copy_wait_reports_timeout_and_leaves_the_context_usable(lib):
     good = lib.Scene(sc)
     st = good.step(2)
     assert st["converged"] == 1
+
+
+def test_allocation_failure_is_reported_and_everything_released(lib):
+    # a caller allocator that refuses its 30th request: scene creation fails
+    # with IPC_ERR_OOM, every block it was given is handed back, and a scene
+    # created afterwards steps normally
+    import torch
+    from paper_2604_19892_b300 import scenes as S
+
+    ipc = lib
+    sc = S.mixed_scene(1500, 51)
+    live, calls = {}, [0]
+
+    def _alloc(n, ctx):
+        calls[0] += 1
+        if calls[0] >= 30:
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(n), device=0)
+        live[p] = int(n)
+        return p
+
+    def _free(p, ctx):
+        assert live.pop(p, None) is not None
+        torch.cuda.caching_allocator_delete(p)
+
+    fns = ipc.AllocFns(ipc.ALLOC_FN(_alloc), ipc.FREE_FN(_free), None)
+    with pytest.raises(ipc.IPCError) as e:
+        ipc.Scene(sc, precision=ipc.IPC_PREC_FP32, alloc_fns=fns)
+    assert e.value.code == ipc.IPC_ERR_OOM
+    assert calls[0] == 30 and not live
+    g = ipc.Scene(sc, precision=ipc.IPC_PREC_FP32)
+    assert g.step(1)["converged"]
+    g.close()
+
+
+def test_non_finite_state_is_refused_and_the_state_kept(lib):
+    # NaN or Inf in positions or velocities, from host or device buffers, is
+    # refused before any kernel uses it; the scene keeps its state
+    import torch
+    from paper_2604_19892_b300 import scenes as S
+
+    ipc = lib
+    sc = S.mixed_scene(1200, 52)
+    g = ipc.Scene(sc, precision=ipc.IPC_PREC_FP32)
+    g.set_state(sc["x0"], sc["v0"])
+    assert g.step(1)["converged"]
+    x1, v1 = g.positions(), g.velocities()
+    for on_device in (False, True):
+        for which, bad in (("x", np.nan), ("v", np.inf)):
+            x, v = x1.copy(), v1.copy()
+            (x if which == "x" else v)[7, 1] = bad
+            if on_device:
+                x, v = torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda()
+            with pytest.raises(ipc.IPCError) as e:
+                g.set_state(x, v)
+            assert e.value.code == ipc.IPC_ERR_INVALID
+            assert np.array_equal(g.positions(), x1) and np.array_equal(g.velocities(), v1)
+    assert g.step(1)["converged"]
+    g.close()
