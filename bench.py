@@ -195,9 +195,14 @@ def stage_bytes(nv, nt, nblocks, rsize):
 # its current form on the same workload (profiles/ holds the summaries and
 # commands); None where the kernel changed since its last capture
 TRAFFIC = {
-    # k_invert_tiled (FP32 first pass of the block inversion) on the 64-sphere
-    # pile, 1,507 blocks: 65,064,448 B read + 3,064,832 B written
-    ("invert", "fp32"): 65064448 + 3064832,
+    # DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+    # on the 64-sphere pile, replayed after an L2-evicting read.
+    # k_invert_tiled (FP32 first pass of the block inversion), 1,507 blocks:
+    ("invert", "fp32"): 65064704 + 2966016,
+    # k_block_apply_plain (FP32 factors, all 1,507 blocks, no Woodbury patch):
+    ("mas_blocks", "fp32"): 29716480 + 0,
+    # k_forms_all (FP32 bulk):
+    ("forms", "fp32"): 49571584 + 99584,
 }
 
 

@@ -458,12 +458,14 @@ int setup_dev(ipc_scene* s) {
     D.alpha = A.arr<double>(m.ngroups[0]);
     D.shrink = A.arr<double>(m.ngroups[0]);
     D.shrink3 = A.arr<double>(m.ngroups[0]);
+    D.shrink4 = A.arr<double>(m.ngroups[0]);
     D.nbody = m.nbody;
     int* d_body = A.arr<int>(m.nv);
     D.body = d_body;
     D.alpha_b = A.arr<double>(m.nbody);
     D.shrink_b = A.arr<double>(m.nbody);
     D.shrink3_b = A.arr<double>(m.nbody);
+    D.shrink4_b = A.arr<double>(m.nbody);
     D.vflags = A.arr<int>(32);
     D.str_v = A.arr<int4>(D.straddle_cap);
     D.str_t = A.arr<int>(D.straddle_cap);
@@ -497,6 +499,9 @@ int setup_dev(ipc_scene* s) {
     D.S = A.arr<Scalars>(1);
     s->nonfinite = A.arr<unsigned long long>(1);
     if (!A.ok) return fail(IPC_ERR_OOM, "scene: device allocation failed");
+    // level-0 assembly blocks are written at and below the diagonal only:
+    // the entries above it are zeroed here, once
+    CUDA_TRY(cudaMemset(D.asmb, 0, sizeof(double) * (size_t)nb0 * kBlk * kBlk));
 
     D.tets = d_tets;
     D.tetB = d_tb;

@@ -176,11 +176,13 @@ struct Dev {
     double* alpha;                         // per level-0 group
     double* shrink;
     double* shrink3;                       // second verification scratch per level-0 subdomain
+    double* shrink4;                       // third verification scratch per level-0 subdomain
     int nbody;
     const int* body;                       // connected body of each vertex
     double* alpha_b;                       // per body
     double* shrink_b;
     double* shrink3_b;
+    double* shrink4_b;
     int* vflags;                           // verification: violation flag per grouping and pass
     int4* str_v;                           // straddling candidates: vertices
     int* str_t;                            // 0 PT (p, t0, t1, t2), 1 EE (a0, a1, b0, b1)

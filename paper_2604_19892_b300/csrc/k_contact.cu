@@ -43,6 +43,9 @@ constexpr int kMaxCells = 64;
 constexpr int kSplitProx = 8;
 constexpr int kSplitSwept = 32;
 constexpr int kCcdPasses = 8;   // verification passes before the uniform fallback
+// vflags: a violation flag per grouping and pass, then the compact-list
+// length of each pass
+static_assert(3 * kCcdPasses <= 32, "vflags holds 32 ints");
 
 inline int nblk(long long n, int t = kT) { return (int)((n + t - 1) / t); }
 
@@ -495,13 +498,16 @@ __device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const do
         double s = scale ? scale[grp[v[j]]] : 1.0;
         Q[j] = mk(s * (double)p[3 * v[j]], s * (double)p[3 * v[j] + 1], s * (double)p[3 * v[j] + 2]);
     }
-    double d0, l = 0.0, c[4];
+    // l: the largest relative displacement, one square root of the largest
+    // square (the same value as the largest root: sqrt is monotone and
+    // correctly rounded; FP64 square roots are costly here)
+    double d0, l2 = 0.0, c[4];
     if (kind == 0) {  // (p, t0, t1, t2)
         double w[3];
         d0 = sqrt(pt_closest(X[0], X[1], X[2], X[3], w));
         for (int j = 1; j < 4; ++j) {
             d3 dd = Q[0] - Q[j];
-            l = fmax(l, sqrt(dot(dd, dd)));
+            l2 = fmax(l2, dot(dd, dd));
         }
         cubic_of(X[2] - X[1], Q[2] - Q[1], X[3] - X[1], Q[3] - Q[1], X[0] - X[1], Q[0] - Q[1], c);
     } else {  // (a0, a1, b0, b1)
@@ -510,10 +516,11 @@ __device__ double pair_alpha(const Dev<R>& D, int kind, const int v[4], const do
         for (int i = 0; i < 2; ++i)
             for (int j = 2; j < 4; ++j) {
                 d3 dd = Q[i] - Q[j];
-                l = fmax(l, sqrt(dot(dd, dd)));
+                l2 = fmax(l2, dot(dd, dd));
             }
         cubic_of(X[2] - X[0], Q[2] - Q[0], X[1] - X[0], Q[1] - Q[0], X[3] - X[0], Q[3] - Q[0], c);
     }
+    const double l = sqrt(l2);
     double al = l > 0.0 ? (1.0 - D.ccd_shrink) * d0 / l : __longlong_as_double(0x7ff0000000000000ULL);
     double a = cubic_safe(c, al);
     // the coplanarity walk only rules out crossing; a step ending closer than
@@ -594,13 +601,19 @@ __device__ __forceinline__ bool ccd_needed(const Dev<R>& D, int kind, const int 
     return ccd_screen(D, kind, v, one_scale_of(D, v)) != 0;
 }
 
+// defer = (a, b) != nullptr: the screening pass of a cached list. A pair
+// that needs the FP64 walk is appended to the scratch list gpair as (a, b)
+// instead, for a second pass in which every lane of a warp runs the walk;
+// when the list is full it is handled here. Every other pair is finished
+// here either way.
 template <class R>
-__device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4]) {
+__device__ void ccd_pair(const Dev<R>& D, int kind, const int v[4], const int2* defer = nullptr) {
     const int g0 = D.grp0[v[0]], g1 = D.grp0[v[1]], g2 = D.grp0[v[2]], g3 = D.grp0[v[3]];
     const int b0 = D.body[v[0]], b1 = D.body[v[1]], b2 = D.body[v[2]], b3 = D.body[v[3]];
     const bool one_scale = g1 == g0 && g2 == g0 && g3 == g0 && b1 == b0 && b2 == b0 && b3 == b0;
     const int scr = ccd_screen(D, kind, v, one_scale);
     if (scr == 0) return;
+    if (scr == 2 && defer && append_ok(D.gpair, D.gpair_n, D.gpair_cap, defer->x, defer->y)) return;
     const bool whole_step = scr == 1;
     const double a = whole_step ? 1.0 : pair_alpha(D, kind, v, D.x, D.p, nullptr);
     if (a < 1.0) {
@@ -775,6 +788,56 @@ __global__ void k_prox_ee_list(Dev<R> D, const double* __restrict__ x, ContactBu
     }
 }
 
+// Screening passes over a cached candidate list: the proximity pairs that
+// need the FP64 distance (FP32 lower bound below dhat) and the CCD pairs that
+// need the FP64 walk are appended to the scratch list gpair, which the list
+// kernels below then finish one thread per pair with all lanes of a warp on
+// the FP64 path (FP64 runs at a small fraction of the FP32 rate here, and a
+// warp that mixes screened-out pairs with one FP64 pair issues the FP64 code
+// for that one lane). A pair that does not fit the scratch list is finished
+// in the screening pass itself, so each pair is handled exactly once.
+template <class R, int kKind>
+__global__ void __launch_bounds__(kT, 8) k_prox_screen(Dev<R> D, const double* __restrict__ x, ContactBuf C, const int2* list,
+                              const int* cnt, int cap) {
+    const int n = min(*cnt, cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int2 q = list[k];
+        const bool need = kKind == 0 ? pt_needed(D, q.x, q.y) : ee_needed(D, q.x, q.y);
+        if (need && !append_ok(D.gpair, D.gpair_n, D.gpair_cap, q.x, q.y)) {
+            if (kKind == 0)
+                pt_try(D, x, C, q.x, q.y);
+            else
+                ee_try(D, x, C, q.x, q.y);
+        }
+    }
+}
+
+template <class R, int kKind>
+__global__ void __launch_bounds__(kT, 6) k_ccd_screen(Dev<R> D, const int2* list, const int* cnt, int cap) {
+    const int n = min(*cnt, cap);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int2 q = list[k];
+        int v[4];
+        float lo[3], hi[3], blo[3], bhi[3];
+        if (kKind == 0) {
+            v[0] = q.x;
+            v[1] = D.sf[3 * q.y];
+            v[2] = D.sf[3 * q.y + 1];
+            v[3] = D.sf[3 * q.y + 2];
+            prim_box(D, v, 1, 0.f, lo, hi);
+            prim_box(D, v + 1, 3, 0.f, blo, bhi);
+        } else {
+            v[0] = D.se[2 * q.x];
+            v[1] = D.se[2 * q.x + 1];
+            v[2] = D.se[2 * q.y];
+            v[3] = D.se[2 * q.y + 1];
+            prim_box(D, v, 2, 0.f, lo, hi);
+            prim_box(D, v + 2, 2, 0.f, blo, bhi);
+        }
+        if (overlap(lo, hi, blo, bhi)) ccd_pair(D, kKind, v, &q);
+    }
+}
+
 template <class R>
 __global__ void k_ccd_pt_list(Dev<R> D, const int2* list, const int* cnt, int cap,
                               const int* skip) {
@@ -831,7 +894,7 @@ __global__ void k_ccd_begin(Dev<R> D) {
     Scalars* S = D.S;
     S->n_straddle = 0;
     S->overflow &= ~2;
-    for (int i = 0; i < 2 * kCcdPasses; ++i) D.vflags[i] = 0;
+    for (int i = 0; i < 3 * kCcdPasses; ++i) D.vflags[i] = 0;
     S->ccd_viol = S->ccd_viol_b = 0;
     S->ccd_uniform = S->ccd_uniform_b = 0;
     S->ccd_passes = S->ccd_passes_b = 0;
@@ -844,6 +907,7 @@ struct Grouping {
     double* alpha;
     double* shrink;       // scratch, n
     double* third;        // scratch, n
+    double* fourth;       // scratch, n
     int n;
     int* viol;
     int* state;           // 0 running, 1 uniform fallback, 2 verified
@@ -854,12 +918,16 @@ struct Grouping {
     double* fmax;
 };
 
-// is straddling pair k violated under grouping G's steps a? (the FP64 walk
-// with the actual motion a_g(v) p_v, skipped where FP32 bounds prove rho = 1);
-// if so, m = the smallest step of the groups it touches
+// does straddling pair k need the FP64 walk under grouping G's steps a?
+// False where it cannot be violated: all four vertices in one group, one
+// common step, or FP32 bounds that prove rho = 1. prev: the steps of the
+// previous pass (nullptr in the first): a pair none of whose groups changed
+// since moves exactly as it did when it was last checked, and then it was
+// not violated (a violation lowers at least one of its groups), so it is not
+// checked again
 template <class R>
-__device__ __forceinline__ bool pair_violated(const Dev<R>& D, const Grouping& G, const double* a, int k, int v[4],
-                                              double& m) {
+__device__ __forceinline__ bool pair_needs_walk(const Dev<R>& D, const Grouping& G, const double* a,
+                                                const double* prev, int k, int v[4]) {
     const int4 q = D.str_v[k];
     v[0] = q.x;
     v[1] = q.y;
@@ -867,6 +935,15 @@ __device__ __forceinline__ bool pair_violated(const Dev<R>& D, const Grouping& G
     v[3] = q.w;
     const int g0 = G.of[v[0]];
     if (G.of[v[1]] == g0 && G.of[v[2]] == g0 && G.of[v[3]] == g0) return false;
+    if (prev) {
+        bool same = true;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gj = G.of[v[j]];
+            same = same && a[gj] == prev[gj];
+        }
+        if (same) return false;
+    }
     // groups with one common step a move the pair uniformly by a p, and each
     // group's a is at most this pair's own safe fraction (the minimum over
     // the pairs touching it, this one included): safe
@@ -897,9 +974,18 @@ __device__ __forceinline__ bool pair_violated(const Dev<R>& D, const Grouping& G
         const float lim = pair_dist_lb(D, kind, v) * (1.f - (float)D.ccd_shrink);
         if (lim > 1.001f * lr + 2e-3f * pm) return false;
     }
-    const double rho = pair_alpha(D, kind, v, D.x, D.p, a, G.of);
+    return true;
+}
+
+// the FP64 walk of straddling pair k (vertices v) with the actual motion:
+// violated when it cannot take the whole step; then m = the smallest step of
+// the groups it touches
+template <class R>
+__device__ __forceinline__ bool pair_walk_violated(const Dev<R>& D, const Grouping& G, const double* a, int k,
+                                                   const int v[4], double& m) {
+    const double rho = pair_alpha(D, D.str_t[k], v, D.x, D.p, a, G.of);
     if (!(rho < 1.0)) return false;
-    m = a[g0];
+    m = a[G.of[v[0]]];
     for (int j = 1; j < 4; ++j) m = fmin(m, a[G.of[v[j]]]);
     return true;
 }
@@ -911,14 +997,20 @@ __device__ __forceinline__ bool pair_violated(const Dev<R>& D, const Grouping& G
 // (the pair then moves uniformly on a segment already checked). A grouping
 // stops at its first clean pass; after kCcdPasses passes with a violation, or
 // when the candidate list overflowed, it takes the uniform step
-// min_g alpha_g. A pass needs one grid barrier: it reads the steps from
-// buffer k mod 3 and takes minima into buffer k + 1 mod 3 (each group's own
-// step and the violations' minima, both commutative), while buffer
-// k + 2 mod 3, which nothing touches in this pass, is reset for the next.
+// min_g alpha_g. A pass reads the steps from buffer k mod 4 and takes minima
+// into buffer k + 1 mod 4 (each group's own step and the violations' minima,
+// both commutative), reads the previous pass's steps from buffer k + 3 mod 4
+// (pairs whose groups all kept their step are not checked again), while
+// buffer k + 2 mod 4, which nothing touches in this pass, is reset for the
+// next. It has two grid barriers: the first after the FP32 screen of every
+// pair, which collects the pairs that need the FP64 walk into a compact list
+// (the scratch pair list, free at this point), the second after the walks of
+// that list, so that the lanes of a warp walk together instead of one lane
+// at a time.
 // Grid-wide barriers are cooperative-groups syncs of a co-resident grid
 // (cudaLaunchCooperativeKernel); every thread executes the same sequence.
 template <class R>
-__global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Grouping G1) {
+__global__ void __launch_bounds__(256, 2) k_verify_all(Dev<R> D, Grouping G0, Grouping G1) {
     cg::grid_group grid = cg::this_grid();
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int nth = gridDim.x * blockDim.x;
@@ -926,6 +1018,7 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
     const int nstr = min(D.S->n_straddle, D.straddle_cap);
     const bool overflow = (D.S->overflow & 2) != 0;
     const Grouping* Gs[2] = {&G0, &G1};
+    int* vcnt = D.vflags + 2 * kCcdPasses;  // compact-list length of each pass (zeroed by k_ccd_begin)
     if (tid == 0) {
         *G0.amin = *G1.amin = 1.0;
         *G0.fmin = *G1.fmin = 1.0;
@@ -952,10 +1045,11 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
         for (int gi = 0; gi < 2; ++gi) {
             if (state[gi] != 0) continue;
             const Grouping& G = *Gs[gi];
-            double* bufs[3] = {G.alpha, G.shrink, G.third};
-            const double* A = bufs[pass % 3];
-            double* B = bufs[(pass + 1) % 3];
-            double* Z = bufs[(pass + 2) % 3];
+            double* bufs[4] = {G.alpha, G.shrink, G.third, G.fourth};
+            const double* A = bufs[pass % 4];
+            double* B = bufs[(pass + 1) % 4];
+            double* Z = bufs[(pass + 2) % 4];
+            const double* Pv = pass > 0 ? bufs[(pass + 3) % 4] : nullptr;
             int* vf = D.vflags + gi * kCcdPasses;
             for (int g = tid; g < G.n; g += nth) {
                 atomicMinPos(&B[g], A[g]);
@@ -964,8 +1058,31 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
             for (int k = tid; k < nstr; k += nth) {
                 int v[4];
                 double m;
-                if (pair_violated(D, G, A, k, v, m)) {
+                // pairs that need the FP64 walk go to the compact list of this
+                // pass; one that does not fit is walked here
+                if (pair_needs_walk(D, G, A, Pv, k, v) &&
+                    !append_ok(D.gpair, vcnt + pass, D.gpair_cap, k, gi) && pair_walk_violated(D, G, A, k, v, m)) {
                     vf[pass] = 1;
+                    for (int j = 0; j < 4; ++j) atomicMinPos(&B[G.of[v[j]]], m);
+                }
+            }
+        }
+        grid.sync();
+        // the walks of the compact list, every lane of a warp on one
+        {
+            const int nw = min(__ldcg(vcnt + pass), D.gpair_cap);
+            for (int e = tid; e < nw; e += nth) {
+                const int2 q = __ldcg(&D.gpair[e]);
+                const int k = q.x, gi = q.y;
+                const Grouping& G = *Gs[gi];
+                double* bufs[4] = {G.alpha, G.shrink, G.third, G.fourth};
+                const double* A = bufs[pass % 4];
+                double* B = bufs[(pass + 1) % 4];
+                const int4 qv = D.str_v[k];
+                const int v[4] = {qv.x, qv.y, qv.z, qv.w};
+                double m;
+                if (pair_walk_violated(D, G, A, k, v, m)) {
+                    D.vflags[gi * kCcdPasses + pass] = 1;
                     for (int j = 0; j < 4; ++j) atomicMinPos(&B[G.of[v[j]]], m);
                 }
             }
@@ -976,7 +1093,7 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
             if (__ldcg(&D.vflags[gi * kCcdPasses + pass]) == 0) {
                 state[gi] = 2;
                 passes[gi] = pass + 1;
-                fin[gi] = pass % 3;
+                fin[gi] = pass % 4;
             }
         }
     }
@@ -988,7 +1105,7 @@ __global__ void __launch_bounds__(256) k_verify_all(Dev<R> D, Grouping G0, Group
             state[gi] = 1;
             passes[gi] = -1;
         }
-        const double* src = fin[gi] == 0 ? G.alpha : fin[gi] == 1 ? G.shrink : G.third;
+        const double* src = fin[gi] == 0 ? G.alpha : fin[gi] == 1 ? G.shrink : fin[gi] == 2 ? G.third : G.fourth;
         const double a_uni = __ldcg(G.amin);
         double lo = 1.0, hi = 0.0;
         for (int g = tid; g < G.n; g += nth) {
@@ -1099,9 +1216,9 @@ void launch_ccd(const Dev<R>& D, cudaStream_t st) {
     }
     if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     Scalars* S = D.S;
-    Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
+    Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, D.shrink4, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
                  &S->alpha_min, &S->alpha_max, &S->vstat[0], &S->vstat[1]};
-    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
+    Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.shrink4_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
                  &S->ccd_passes_b, &S->alpha_bmin, &S->alpha_bmax, &S->vstat[2], &S->vstat[3]};
     verify_groupings(D, sub, bod, st);
 }
@@ -1133,8 +1250,14 @@ template <class R>
 void launch_detect_list(const Dev<R>& D, const double* x, const ContactBuf& C, cudaStream_t st) {
     KL(k_reset_detect<R><<<1, 1, 0, st>>>(D, C));
     if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, (const R*)nullptr));
-    KL(k_prox_pt_list<R><<<1184, kT, 0, st>>>(D, x, C, D.cand_pt, &D.cand_n[0], D.cand_cap, nullptr));
-    KL(k_prox_ee_list<R><<<1184, kT, 0, st>>>(D, x, C, D.cand_ee, &D.cand_n[1], D.cand_cap, nullptr));
+    // FP32 screen of each cached list into the scratch list, then the FP64
+    // tests of the screened pairs
+    cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+    KL(k_prox_screen<R, 0><<<1184, kT, 0, st>>>(D, x, C, D.cand_pt, &D.cand_n[0], D.cand_cap));
+    KL(k_prox_pt_list<R><<<1184, kT, 0, st>>>(D, x, C, D.gpair, D.gpair_n, D.gpair_cap, nullptr));
+    cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+    KL(k_prox_screen<R, 1><<<1184, kT, 0, st>>>(D, x, C, D.cand_ee, &D.cand_n[1], D.cand_cap));
+    KL(k_prox_ee_list<R><<<1184, kT, 0, st>>>(D, x, C, D.gpair, D.gpair_n, D.gpair_cap, nullptr));
     if (D.nsv) KL(k_prox_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D, x, C));
 }
 
@@ -1146,15 +1269,21 @@ void launch_ccd_list(const Dev<R>& D, cudaStream_t st, int part) {
         KL(k_fill<R><<<nblk(ng), kT, 0, st>>>(D, D.alpha, ng, 1.0));
         KL(k_fill<R><<<nblk(D.nbody), kT, 0, st>>>(D, D.alpha_b, D.nbody, 1.0));
         if (D.nsv) KL(k_vert_f32<R><<<nblk(D.nsv), kT, 0, st>>>(D, D.x, (const R*)D.p));
-        KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D, D.cand_pt, &D.cand_n[0], D.cand_cap, nullptr));
-        KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D, D.cand_ee, &D.cand_n[1], D.cand_cap, nullptr));
+        // FP32 screen of each cached list (pairs that need the FP64 walk into
+        // the scratch list), then the walks of the screened pairs
+        cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+        KL(k_ccd_screen<R, 0><<<1184, kT, 0, st>>>(D, D.cand_pt, &D.cand_n[0], D.cand_cap));
+        KL(k_ccd_pt_list<R><<<1184, kT, 0, st>>>(D, D.gpair, D.gpair_n, D.gpair_cap, nullptr));
+        cudaMemsetAsync(D.gpair_n, 0, 2 * sizeof(int), st);
+        KL(k_ccd_screen<R, 1><<<1184, kT, 0, st>>>(D, D.cand_ee, &D.cand_n[1], D.cand_cap));
+        KL(k_ccd_ee_list<R><<<1184, kT, 0, st>>>(D, D.gpair, D.gpair_n, D.gpair_cap, nullptr));
         if (D.nsv) KL(k_ccd_pg<R><<<nblk(D.nsv), kT, 0, st>>>(D));
     }
     if (part != 1) {  // verification: one cooperative launch, ordered across scenes
         Scalars* S = D.S;
-        Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
+        Grouping sub{D.grp0, D.alpha, D.shrink, D.shrink3, D.shrink4, ng, &S->ccd_viol, &S->ccd_uniform, &S->ccd_passes,
                      &S->alpha_min, &S->alpha_max, &S->vstat[0], &S->vstat[1]};
-        Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
+        Grouping bod{D.body, D.alpha_b, D.shrink_b, D.shrink3_b, D.shrink4_b, D.nbody, &S->ccd_viol_b, &S->ccd_uniform_b,
                      &S->ccd_passes_b, &S->alpha_bmin, &S->alpha_bmax, &S->vstat[2], &S->vstat[3]};
         verify_groupings(D, sub, bod, st);
     }

@@ -311,9 +311,10 @@ __global__ void __launch_bounds__(64) k_tet_hessian(Dev<R> D, const double* __re
 // ------------------------------------------------------ block assembly
 
 // Every assembly block set to its mass term: zero except the lumped node
-// masses on the diagonal (a table fixed by the mesh), level 0 into asmb, the
-// coarse levels into asmbc. Four FP64 entries (two 16-byte stores) per thread
-// and step; only diagonal rows read the table.
+// masses on the diagonal (a table fixed by the mesh), level 0 into asmb (at
+// and below the diagonal), the coarse levels into asmbc. Four FP64 entries
+// (two 16-byte stores) per thread and step; only diagonal rows read the
+// table.
 template <class R>
 __global__ void __launch_bounds__(256) k_init_blocks(Dev<R> D, int nb0, int nb) {
     constexpr int kQ = kBlk * kBlk / 4;  // 4-entry groups per block
@@ -323,6 +324,9 @@ __global__ void __launch_bounds__(256) k_init_blocks(Dev<R> D, int nb0, int nb) 
         const int rem = 4 * (e - b * kQ);
         const int row = rem / kBlk, col = rem - row * kBlk;
         const int dc = row - col;  // the diagonal sits at entry dc of this group if 0 <= dc < 4
+        // level 0 is assembled and read at or below the diagonal only: its
+        // groups strictly above it were zeroed once at scene set-up and stay 0
+        if (b < nb0 && dc < 0) continue;
         const double dg = (dc >= 0 && dc < 4) ? D.mdiag[(size_t)b * kBlk + row] : 0.0;
         double* dst = (b < nb0 ? D.asmb + (size_t)b * (kBlk * kBlk) : D.asmbc + (size_t)(b - nb0) * (kBlk * kBlk)) + rem;
         reinterpret_cast<double2*>(dst)[0] = make_double2(dc == 0 ? dg : 0.0, dc == 1 ? dg : 0.0);
@@ -508,11 +512,13 @@ __global__ void __launch_bounds__(256) k_asm_sum(Dev<R> D) {
 // one subdomain; a coarse level sums the weights of the vertices sharing a
 // node, W_P = sum_{a in P} w_a, and adds k W_P W_Q r r^T per node pair (none
 // for a pair or edge contact inside one node: its weights sum to zero).
-__device__ __forceinline__ void add_rr(double* A, int si, int sj, const double kr[3][3], double c) {
+__device__ __forceinline__ void add_rr(double* A, int si, int sj, const double kr[3][3], double c,
+                                       bool lower = false) {
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int s2 = 0; s2 < 3; ++s2) {
+            if (lower && si == sj && s2 > r) continue;  // above the diagonal of a diagonal 3x3 block
             const double v = c * kr[r][s2];
             if (v != 0.0) atomicAdd(&A[(3 * si + r) * kBlk + 3 * sj + s2], v);
         }
@@ -543,7 +549,10 @@ __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b)
-                if (a < nvv && b < nvv && g[a] == g[b]) add_rr(D.asmb + (size_t)g[a] * (kBlk * kBlk), sl[a], sl[b], kr, w[a] * w[b]);
+                // level 0 at and below the diagonal only (row slot >= column
+                // slot): the blocks of (a, b) and (b, a) are transposes
+                if (a < nvv && b < nvv && g[a] == g[b] && sl[a] >= sl[b])
+                    add_rr(D.asmb + (size_t)g[a] * (kBlk * kBlk), sl[a], sl[b], kr, w[a] * w[b], true);
         for (int l = 1; l < D.nlev; ++l) {
             int nd[4];
             double W[4] = {0.0, 0.0, 0.0, 0.0};
@@ -606,6 +615,19 @@ constexpr int kInvThreads = 160;
 static_assert(kNT * kTile == kBlk, "tile size must divide the block size");
 static_assert(kInvThreads >= kNTiles && kInvThreads % 32 == 0, "one thread per lower tile");
 
+// Packed lower column panels: panel kt holds columns 6 kt .. 6 kt + 5 of a
+// lower-triangular 96 x 96 matrix over rows 6 kt .. 95, column-major (each
+// column is 96 - 6 kt consecutive entries): 4,896 entries, about half the
+// square. A 6-row slice of a column starts at an even index.
+__host__ __device__ constexpr int panel_off(int kt) { return kTile * (kBlk * kt - kTile * kt * (kt - 1) / 2); }
+constexpr int kPanelsSize = panel_off(kNT);
+static_assert(kPanelsSize == kNTiles * kTile * kTile, "the panels hold the lower tiles exactly");
+// entry (r, c) of the panels; r >= 6 floor(c / 6)
+__device__ __forceinline__ int pix(int r, int c) {
+    const int kt = c / kTile;
+    return panel_off(kt) + (c - kTile * kt) * (kBlk - kTile * kt) + (r - kTile * kt);
+}
+
 template <class T>
 struct Vec2;
 template <>
@@ -656,12 +678,20 @@ __device__ __forceinline__ void smem_max(double* p, double v) {
 
 // The block's inverse B = s W^T W s is kept as W' = W diag(s) (B = W'^T W'),
 // packed by 4-row-aligned columns (wcol): warp w writes columns w, w +
-// nwarps, ... with its lanes on consecutive rows (coalesced), from W^T in
-// shared memory (wt[c * 96 + r] = W[r][c]); the rows of a column's first
-// quad above the diagonal are written as zeros. Storing the factor instead
-// of B halves the bytes of every later apply, needs no W^T W product here,
-// and keeps B positive semi-definite whatever the rounding of W'.
-template <class R, class T>
+// nwarps, ... with its lanes on consecutive rows (coalesced), from W in
+// shared memory (kPanels: the packed column panels, pix; otherwise W^T,
+// wt[c * 96 + r] = W[r][c]); the rows of a column's first quad above the
+// diagonal are written as zeros. Storing the factor instead of B halves the
+// bytes of every later apply, needs no W^T W product here, and keeps B
+// positive semi-definite whatever the rounding of W'.
+template <bool kPanels>
+__device__ __forceinline__ int wix(int r, int c) {
+    if constexpr (kPanels)
+        return pix(r, c);
+    else
+        return c * kBlk + r;
+}
+template <class R, class T, bool kPanels = false>
 __device__ __forceinline__ void store_factor(const Dev<R>& D, int b, const T* wt, const T* sc) {
     if (D.blocks16) {
         // BF16 tiles (IPC_PREC_BF16_MAS): tile (i, j) row-major, written in
@@ -674,7 +704,7 @@ __device__ __forceinline__ void store_factor(const Dev<R>& D, int b, const T* wt
             while ((ti + 1) * (ti + 2) / 2 <= tix) ++ti;
             const int tj = tix - ti * (ti + 1) / 2;
             const int r = kT16 * ti + ((e >> 4) & 15), c = kT16 * tj + (e & 15);
-            d16[e] = __float2bfloat16_rn(r >= c ? (float)(wt[c * kBlk + r] * sc[c]) : 0.f);
+            d16[e] = __float2bfloat16_rn(r >= c ? (float)(wt[wix<kPanels>(r, c)] * sc[c]) : 0.f);
         }
         return;
     }
@@ -682,10 +712,9 @@ __device__ __forceinline__ void store_factor(const Dev<R>& D, int b, const T* wt
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int j = warp; j < kBlk; j += nw) {
         const T s = sc[j];
-        const T* col = wt + j * kBlk;
         const int r0 = j & ~3;
         R* out = dst + wcol(j) - r0;
-        for (int r = r0 + lane; r < kBlk; r += 32) out[r] = r >= j ? (R)(col[r] * s) : (R)0;
+        for (int r = r0 + lane; r < kBlk; r += 32) out[r] = r >= j ? (R)(wt[wix<kPanels>(r, j)] * s) : (R)0;
     }
 }
 
@@ -901,11 +930,11 @@ __global__ void __launch_bounds__(kInvThreads) k_invert(Dev<R> D, int* flags, in
 // pass inverts it with those rules; every other block is an unmodified
 // Cholesky factorisation, which is what k_invert computes for it too.
 template <class R>
-__global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* flags) {
+__global__ void __launch_bounds__(kInvThreads, 6) k_invert_tiled(Dev<R> D, int* flags) {
     static_assert(sizeof(R) == 4, "FP32 first pass");
     extern __shared__ unsigned char smem_raw[];
-    float* buf = reinterpret_cast<float*>(smem_raw);  // 96 x 96: L^T, then W
-    float* pan = buf + kBlk * kBlk;                    // 2 x 6 x 96: panel columns of L, then row blocks of W
+    float* buf = reinterpret_cast<float*>(smem_raw);  // packed column panels (pix): A, then L, then W
+    float* pan = buf + kPanelsSize;                    // 2 x 6 x 96: panel columns of L, then row blocks of W
     float* sc = pan + 2 * kTile * kBlk;                // diagonal scaling s
     float* idg = sc + kBlk;                            // 1 / L_kk
     __shared__ int s_bad;
@@ -958,7 +987,7 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
                         f = (r == c) ? 1.f : 0.f;
                     else
                         f = scaled_f32(v[q][m], sc[r], sc[c]);
-                    buf[r * kBlk + c] = f;
+                    buf[pix(r, c)] = f;
                 }
             }
         }
@@ -977,12 +1006,14 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
         ti = c + rem;
     }
     int r0 = kTile * ti, c0 = kTile * tj;
+    // the thread's tile in the panels: column cc at tb + cc * ld, 6 rows each
+    int tb = panel_off(tj) + (r0 - c0), ld = kBlk - c0;
     __syncthreads();
     float a[kTile][kTile];
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = act ? buf[(r0 + rr) * kBlk + c0 + cc] : 0.f;
+        for (int cc = 0; cc < kTile; ++cc) a[rr][cc] = act ? buf[tb + cc * ld + rr] : 0.f;
     __syncthreads();  // buf is reused for L^T below
     bool bad = false;
     for (int kt = 0; kt < kNT; ++kt) {
@@ -1053,12 +1084,12 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
         }
     }
     if (bad) s_bad = 1;
-    // L^T -> shared memory (lower entries only)
+    // L -> the panels, in place of A (lower entries only)
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
         for (int cc = 0; cc < kTile; ++cc)
-            if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
+            if (act && (ti > tj || rr >= cc)) buf[tb + cc * ld + rr] = a[rr][cc];
     __syncthreads();
     if (s_bad) {  // uniform over the CTA: the FP64 pass inverts this block
         if (threadIdx.x == 0) flags[b] = 1;
@@ -1078,6 +1109,8 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
     }
     r0 = kTile * ti;
     c0 = kTile * tj;
+    tb = panel_off(tj) + (r0 - c0);
+    ld = kBlk - c0;
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
@@ -1090,7 +1123,7 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
             for (int r = 0; r < kTile; ++r) {
                 float Lr[kTile];
 #pragma unroll
-                for (int m = 0; m < r; ++m) Lr[m] = buf[(k0 + m) * kBlk + k0 + r];
+                for (int m = 0; m < r; ++m) Lr[m] = buf[panel_off(kt) + m * (kBlk - k0) + r];
                 const float ir = idg[k0 + r];
 #pragma unroll
                 for (int cc = 0; cc < kTile; ++cc) {
@@ -1110,7 +1143,7 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
 #pragma unroll
             for (int m = 0; m < kTile; ++m) {
                 float lr[kTile], wc[kTile];
-                lds6(buf + (kTile * kt + m) * kBlk + r0, lr);
+                lds6(buf + panel_off(kt) + m * (kBlk - kTile * kt) + (r0 - kTile * kt), lr);
                 lds6(Q + m * kBlk + c0, wc);
 #pragma unroll
                 for (int rr = 0; rr < kTile; ++rr)
@@ -1120,15 +1153,15 @@ __global__ void __launch_bounds__(kInvThreads, 5) k_invert_tiled(Dev<R> D, int* 
         }
     }
     __syncthreads();
-    // W^T -> shared memory (every thread has finished reading L from buf)
+    // W -> the panels, in place of L (every thread has finished reading L)
 #pragma unroll
     for (int rr = 0; rr < kTile; ++rr)
 #pragma unroll
         for (int cc = 0; cc < kTile; ++cc)
-            if (act && (ti > tj || rr >= cc)) buf[(c0 + cc) * kBlk + r0 + rr] = a[rr][cc];
+            if (act && (ti > tj || rr >= cc)) buf[tb + cc * ld + rr] = a[rr][cc];
     if (threadIdx.x == 0) flags[b] = 0;
     __syncthreads();
-    store_factor<R, float>(D, b, buf, sc);
+    store_factor<R, float, true>(D, b, buf, sc);
 }
 
 // ------------------------------------------------------ C_base snapshot
@@ -2015,7 +2048,7 @@ void launch_invert(const Dev<R>& D, cudaStream_t st) {
     // the blocks FP32 cannot carry
     const size_t smem_r = sizeof(R) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
     const size_t smem_d = sizeof(double) * ((size_t)kBlk * kBlk + 4 * kBlk + 4);
-    const size_t smem_t = sizeof(float) * ((size_t)kBlk * kBlk + 2 * kTile * kBlk + 2 * kBlk);
+    const size_t smem_t = sizeof(float) * ((size_t)kPanelsSize + 2 * kTile * kBlk + 2 * kBlk);
     static const bool attr_set = [&] {  // once per process, thread-safe
         cudaFuncSetAttribute(k_invert<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r);
         cudaFuncSetAttribute(k_invert<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);

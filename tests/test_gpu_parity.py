@@ -81,8 +81,13 @@ def test_energy_gradient_parity(lib, name, precision, gtol, etol):
 # hashed grid (its screened pairs finished by the list kernels); the grid
 # with a one-pair scratch list, so every pass overflows to the fused query;
 # cached candidate lists
-BROAD_PHASES = [dict(broad_phase=1), dict(broad_phase=1, grid_pair_capacity=1), dict(broad_phase=2)]
-BP_IDS = ["grid", "grid-overflow", "lists"]
+# grid_pair_capacity=1: the scratch pair list overflows at once, so the grid
+# queries take their fused path, and with cached lists the screening passes
+# and the verification finish almost every pair themselves instead of through
+# their compact lists
+BROAD_PHASES = [dict(broad_phase=1), dict(broad_phase=1, grid_pair_capacity=1), dict(broad_phase=2),
+                dict(broad_phase=2, grid_pair_capacity=1)]
+BP_IDS = ["grid", "grid-overflow", "lists", "lists-overflow"]
 
 
 @pytest.mark.parametrize("bp", BROAD_PHASES, ids=BP_IDS)
