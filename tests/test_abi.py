@@ -78,3 +78,16 @@ def test_params_mirror_matches_the_header():
     assert p.grid_pair_capacity == 0
     assert p.wait_polls == 1 << 22
     assert p.apply_ctas == 0
+
+
+def test_fma_peak_refuses_bad_arguments_before_any_cuda_call():
+    # the argument checks come first, so this runs without a GPU
+    import ctypes as C
+    from paper_2604_19892_b300 import build, ipc
+    lib = ipc.load(build.build())
+    out = C.c_double(-1.0)
+    for prec, ms in ((7, 10.0), (ipc.IPC_PREC_BF16_MAS, 10.0), (ipc.IPC_PREC_FP32, 0.0),
+                     (ipc.IPC_PREC_FP32, 5000.0)):
+        assert lib.ipc_profile_fma_peak(prec, ms, C.byref(out)) == ipc.IPC_ERR_INVALID
+    assert lib.ipc_profile_fma_peak(ipc.IPC_PREC_FP32, 10.0, None) == ipc.IPC_ERR_INVALID
+    assert out.value == -1.0

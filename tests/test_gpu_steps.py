@@ -188,3 +188,17 @@ def test_non_finite_state_is_refused_and_the_state_kept(lib):
             assert np.array_equal(g.positions(), x1) and np.array_equal(g.velocities(), v1)
     assert g.step(1)["converged"]
     g.close()
+
+
+def test_fma_peak_measurement_is_plausible(lib):
+    # the SIMT FMA throughput the inversion's roofline is read against: both
+    # pipes measured, FP32 far above FP64 on this part and below the unit
+    # count bound (lanes x 2 flops x the maximum clock)
+    import torch
+    ipc = lib
+    f32 = ipc.fma_peak_tflops(ipc.IPC_PREC_FP32, 5.0)
+    f64 = ipc.fma_peak_tflops(ipc.IPC_PREC_FP64, 5.0)
+    props = torch.cuda.get_device_properties(0)
+    bound = props.multi_processor_count * 128 * 2 * 2.2e9 / 1e12
+    assert 0.25 * bound < f32 <= 1.05 * bound, (f32, bound)
+    assert 0.0 < f64 < f32 / 10, (f64, f32)
