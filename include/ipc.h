@@ -308,8 +308,12 @@ typedef struct ipc_iter_record {
     double alpha_min, alpha_max;
     double r;
     double pmax;             /* max_v |p_v| of the direction */
-    int ccd_passes;          /* verification passes, -1 = uniform fallback */
+    int ccd_passes;          /* per-subdomain verification passes, -1 = uniform fallback */
     int cached_pairs;        /* 1 if the broad phase used the cached candidate lists */
+    int ccd_passes_body;     /* per-body verification passes, -1 = uniform fallback; when
+                                the per-subdomain one fell back and this one did not,
+                                the first energy-check trial was the per-body step */
+    int pad_;
 } ipc_iter_record;
 
 /* ---- evaluation entry points (host arrays in and out) -------------------

@@ -52,7 +52,8 @@ class OIterRecord(C.Structure):
     _fields_ = [("restart", C.c_int), ("n_contacts", C.c_int), ("n_update", C.c_int),
                 ("ls_halvings", C.c_int), ("mu", C.c_double), ("nu", C.c_double), ("gz", C.c_double),
                 ("znorm", C.c_double), ("energy_before", C.c_double), ("energy_after", C.c_double),
-                ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("r", C.c_double)]
+                ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("r", C.c_double),
+                ("ccd_passes", C.c_int), ("ccd_passes_body", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)

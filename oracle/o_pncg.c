@@ -30,7 +30,12 @@
  *    connected body moves uniformly by its own verified alpha_b) scaled by
  *    1, 1/2, 1/4, 1/8 -- skipped when no body exceeds the uniform step --
  *    then to the uniform step beta = min_d alpha_d (safe by construction)
- *    halved until one is accepted, ls_max + 1 trials in all.
+ *    halved until one is accepted, ls_max + 1 trials in all. When the
+ *    per-subdomain verification of straddling pairs fell back to the
+ *    uniform step and the per-body verification did not, the per-subdomain
+ *    trial would be that uniform step: the per-body step (verified, and no
+ *    smaller anywhere) is tried first instead, and the per-body tier goes on
+ *    at 1/2, 1/4, 1/8.
  *    If none is accepted, x does not move and the next iteration restarts.
  *  - Algorithm 1 tests convergence (restart and |z| <= eps) after the update
  *    whatever the update was, so a restart iteration with |z| <= eps ends the
@@ -211,7 +216,10 @@ int o_step(OScene* s, double* x, double* v, OStepStats* st) {
         rec.znorm = zn;
         S.znorm = zn;
         /* step sizes per level-0 subdomain and per body */
-        o_ccd(s, xk, p, alpha, alpha_b, NULL);
+        int passes_b = 0;
+        const int passes = o_ccd(s, xk, p, alpha, alpha_b, &passes_b);
+        rec.ccd_passes = passes;
+        rec.ccd_passes_body = passes_b;
         rec.alpha_min = 1.0;
         rec.alpha_max = 0.0;
         for (int gi = 0; gi < s->ngroups[0]; ++gi) {
@@ -222,23 +230,29 @@ int o_step(OScene* s, double* x, double* v, OStepStats* st) {
         for (int b = 0; b < s->nbody; ++b)
             if (alpha_b[b] > bmax) bmax = alpha_b[b];
         /* energy check over the trial list: per-subdomain step; per-body
-         * steps scaled by 1, 1/2, 1/4, 1/8; uniform steps alpha_min / 2^j */
+         * steps scaled by 1, 1/2, 1/4, 1/8; uniform steps alpha_min / 2^j.
+         * When the per-subdomain verification fell back to the uniform step
+         * and the per-body one did not, the first trial is the per-body step
+         * (also verified, and at least the uniform step everywhere), and the
+         * per-body tier continues at 1/2. */
         rec.energy_before = Ek;
         int accepted = 0, halv = 0;
         int body_tier = bmax > rec.alpha_min;
+        int body_first = body_tier && passes < 0 && passes_b >= 0;
+        int nbody_trials = body_tier ? (body_first ? 3 : 4) : 0;
         int j0 = (rec.alpha_max > rec.alpha_min || body_tier) ? 0 : 1;
         for (int ls = 0; ls <= s->prm.ls_max; ++ls) {
-            if (ls == 0) {
+            if (ls == 0 && !body_first) {
                 for (int i = 0; i < nv; ++i)
                     for (int r = 0; r < 3; ++r)
                         xtry[3 * i + r] = xk[3 * i + r] + alpha[s->group_of[0][i]] * p[3 * i + r];
-            } else if (body_tier && ls <= 4) {
-                double c = ldexp(1.0, -(ls - 1));
+            } else if (ls == 0 || ls <= nbody_trials) {
+                double c = ldexp(1.0, -(ls + (body_first ? 0 : -1)));
                 for (int i = 0; i < nv; ++i)
                     for (int r = 0; r < 3; ++r)
                         xtry[3 * i + r] = xk[3 * i + r] + c * alpha_b[s->body[i]] * p[3 * i + r];
             } else {
-                int j = j0 + (ls - 1 - (body_tier ? 4 : 0));
+                int j = j0 + (ls - 1 - nbody_trials);
                 double beta = ldexp(rec.alpha_min, -j);
                 for (int i = 0; i < n3; ++i) xtry[i] = xk[i] + beta * p[i];
             }

@@ -78,6 +78,8 @@ typedef struct OIterRecord {
     double energy_before, energy_after;
     double alpha_min, alpha_max;
     double r;
+    int ccd_passes;      /* per-subdomain verification passes, -1 = fell back */
+    int ccd_passes_body; /* per-body verification passes, -1 = fell back */
 } OIterRecord;
 
 /* ---- scene ---------------------------------------------------------- */

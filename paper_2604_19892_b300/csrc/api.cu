@@ -924,6 +924,7 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         rec.alpha_max = S.alpha_max;
         rec.pmax = S.pmax;
         rec.ccd_passes = S.ccd_passes;
+        rec.ccd_passes_body = S.ccd_passes_b;
         rec.cached_pairs = use_list ? 1 : 0;
         rec.energy_before = Ek;
         int accepted = S.accepted;
@@ -931,18 +932,22 @@ int run_timestep(ipc_scene* s, cudaStream_t st, ipc_step_stats* acc) {
         if (!accepted) {
             // trial list after the per-subdomain step: per-body steps scaled
             // by 1, 1/2, 1/4, 1/8 (when some body exceeds the uniform step),
-            // then the uniform step alpha_min / 2^j
+            // then the uniform step alpha_min / 2^j. When the first trial
+            // already was the per-body step (the per-subdomain verification
+            // fell back, the per-body one did not: k_trial), the per-body
+            // tier goes on at 1/2
             halv = 1;
-            bool body_tier = S.alpha_bmax > S.alpha_min;
-            int j0 = (S.alpha_max > S.alpha_min || body_tier) ? 0 : 1;
+            const bool body_tier = S.alpha_bmax > S.alpha_min;
+            const bool body_first = body_tier && S.ccd_passes < 0 && S.ccd_passes_b >= 0;
+            const int nbt = body_tier ? (body_first ? 3 : 4) : 0;
+            const int j0 = (S.alpha_max > S.alpha_min || body_tier) ? 0 : 1;
             for (int ls = 1; ls <= P.ls_max; ++ls) {
                 {
                     Stage t(s, 6, st);
-                    if (body_tier && ls <= 4)
-                        eval_trial(D, 1, std::ldexp(1.0, -(ls - 1)), st, use_list);
+                    if (ls <= nbt)
+                        eval_trial(D, 1, std::ldexp(1.0, -(ls - (body_first ? 0 : 1))), st, use_list);
                     else
-                        eval_trial(D, 2, std::ldexp(S.alpha_min, -(j0 + ls - 1 - (body_tier ? 4 : 0))), st,
-                                   use_list);
+                        eval_trial(D, 2, std::ldexp(S.alpha_min, -(j0 + ls - 1 - nbt)), st, use_list);
                 }
                 if (int e = read_view(s, D, st)) return e;
                 if (s->hv->S.overflow & 1) return fail(IPC_ERR_CAPACITY, "contact buffer overflow");

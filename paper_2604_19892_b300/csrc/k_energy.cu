@@ -32,6 +32,16 @@ template <class R>
 __global__ void k_trial(Dev<R> D, int mode, double c) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * D.nv) return;
+    if (mode == 0) {
+        // when the per-subdomain verification fell back to the uniform step
+        // and the per-body one did not, the first trial is the per-body step
+        // (verified, and no smaller anywhere than the uniform one)
+        const Scalars* S = D.S;
+        if (S->ccd_passes < 0 && S->ccd_passes_b >= 0 && S->alpha_bmax > S->alpha_min) {
+            mode = 1;
+            c = 1.0;
+        }
+    }
     double a = mode == 0 ? D.alpha[D.grp0[i / 3]] : (mode == 1 ? c * D.alpha_b[D.body[i / 3]] : c);
     D.xtry[i] = D.x[i] + a * (double)D.p[i];
 }

@@ -76,7 +76,7 @@ class IterRecord(C.Structure):
                 ("mu", C.c_double), ("nu", C.c_double), ("gz", C.c_double), ("znorm", C.c_double),
                 ("energy_before", C.c_double), ("energy_after", C.c_double), ("alpha_min", C.c_double),
                 ("alpha_max", C.c_double), ("r", C.c_double), ("pmax", C.c_double), ("ccd_passes", C.c_int),
-                ("cached_pairs", C.c_int)]
+                ("cached_pairs", C.c_int), ("ccd_passes_body", C.c_int), ("pad_", C.c_int)]
 
 
 class Profile(C.Structure):

@@ -202,3 +202,35 @@ def test_fma_peak_measurement_is_plausible(lib):
     bound = props.multi_processor_count * 128 * 2 * 2.2e9 / 1e12
     assert 0.25 * bound < f32 <= 1.05 * bound, (f32, bound)
     assert 0.0 < f64 < f32 / 10, (f64, f32)
+
+
+def test_first_trial_takes_the_body_steps_after_a_subdomain_fallback(lib):
+    """Per-subdomain steps on thin features (Sec. 4.4): two small spiky balls
+    whose 64-layer spikes run through several 32-vertex subdomains. In
+    timestep 1 the per-subdomain verification of the straddling pairs falls
+    back to the uniform step on some iterations while the per-body one
+    verifies; the first energy-check trial is then the per-body step, on both
+    sides. From the oracle's state after timestep 0, the GPU's FP64 form
+    follows the oracle iteration by iteration up to and including the first
+    such iteration."""
+    import oracle as O
+    from paper_2604_19892_b300 import scenes as S
+
+    ipc = lib
+    sc = S.spiky_balls(n_balls=2, cells=4, n_spikes=8, layers=64)
+    g = ipc.Scene(sc, precision=ipc.IPC_PREC_FP64)
+    o = O.Scene(sc)
+    x, v, _ = o.step(sc["x0"].copy(), sc["v0"].copy())
+    g.set_state(x, v)
+    g.step(1)
+    o.step(x, v)
+    tg, to = g.trace(), o.trace()
+    k = next(i for i, r in enumerate(to) if r["ccd_passes"] < 0 and r["ccd_passes_body"] >= 0)
+    assert len(tg) > k
+    for i in range(k + 1):
+        rg, ro = tg[i], to[i]
+        assert rg["restart"] == ro["restart"], i
+        assert rg["ccd_passes"] == ro["ccd_passes"] and rg["ccd_passes_body"] == ro["ccd_passes_body"], i
+        assert rg["ls_halvings"] == ro["ls_halvings"], i
+        assert rg["energy_after"] == pytest.approx(ro["energy_after"], rel=1e-8), i
+    g.close()

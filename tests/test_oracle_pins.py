@@ -355,3 +355,23 @@ def test_oracle_results_do_not_depend_on_the_thread_count():
     O.set_threads(0)
     np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
+
+
+def test_subdomain_fallback_takes_the_verified_body_steps_safely():
+    """Thin spikes crossing several 32-vertex subdomains (two small spiky
+    balls): in timestep 1 the per-subdomain verification of straddling pairs
+    falls back on some iterations while the per-body one verifies, and the
+    energy check then starts from the per-body steps. Every accepted step
+    keeps the state separated (all active contacts at d > 0, which the
+    oracle's own contact search checks), the energy never rises beyond the
+    rounding allowance, and the timestep converges."""
+    sc = S.spiky_balls(n_balls=2, cells=4, n_spikes=8, layers=64)
+    o = O.Scene(sc)
+    x, v, _ = o.step(sc["x0"].copy(), sc["v0"].copy())
+    x, v, st = o.step(x, v)
+    tr = o.trace()
+    fb = [r for r in tr if r["ccd_passes"] < 0 and r["ccd_passes_body"] >= 0]
+    assert fb, "the scene no longer exercises the fallback"
+    assert st["converged"] and st["min_dist"] > 0.0
+    for r in tr:
+        assert r["energy_after"] <= r["energy_before"] + o.energy_tolerance(r["energy_before"])
