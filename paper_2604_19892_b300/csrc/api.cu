@@ -343,6 +343,7 @@ int setup_dev(ipc_scene* s) {
     D.invflag = A.arr<int>(std::max(nb, 1));
     D.pivfix = A.arr<int>(1);
     D.asmbc = A.arr<double>((size_t)std::max(nb - nb0, 1) * kBlk * kBlk);
+    D.pg_k = A.arr<double>((size_t)std::max(D.coarse_off[m.nlev] / 3, 1));
     // diagonal of each block's mass term: the lumped mass of the block's
     // nodes (sums of vertex masses at the coarse levels), fixed by the mesh
     std::vector<double> mdiag((size_t)nb * kBlk, 0.0);

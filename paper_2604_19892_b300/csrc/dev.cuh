@@ -177,6 +177,8 @@ struct Dev {
     double* shrink;
     double* shrink3;                       // second verification scratch per level-0 subdomain
     double* shrink4;                       // third verification scratch per level-0 subdomain
+    double* pg_k;                          // per coarse node (offset coarse_off[l] / 3): the summed
+                                           // stiffness of its point-ground contacts (RebuildMAS scratch)
     int nbody;
     const int* body;                       // connected body of each vertex
     double* alpha_b;                       // per body

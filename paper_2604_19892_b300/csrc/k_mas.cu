@@ -554,6 +554,16 @@ __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
                 if (a < nvv && b < nvv && g[a] == g[b] && sl[a] >= sl[b])
                     add_rr(D.asmb + (size_t)g[a] * (kBlk * kBlk), sl[a], sl[b], kr, w[a] * w[b], true);
         for (int l = 1; l < D.nlev; ++l) {
+            if (nvv == 1) {
+                // a point-ground contact adds k n n^T (weight 1, the plane
+                // normal n) to its node's diagonal block: its stiffness is
+                // summed per node here and the block updated once per node
+                // (k_assemble_pg_coarse), instead of nine atomics per contact
+                // on the few entries that every ground contact of a coarse
+                // node shares
+                atomicAdd(&D.pg_k[D.coarse_off[l] / 3 + D.node_of_vert[l][vid[0]]], k);
+                continue;
+            }
             int nd[4];
             double W[4] = {0.0, 0.0, 0.0, 0.0};
             int m = 0;
@@ -588,6 +598,27 @@ __global__ void k_assemble_contacts(Dev<R> D, ContactBuf C) {
                     if (u < m && v < m && ng[u] == ng[v])
                         add_rr(Ab + (size_t)ng[u] * (kBlk * kBlk), ns[u], ns[v], kr, W[u] * W[v]);
         }
+    }
+}
+
+// the summed point-ground stiffness K of each coarse node: K n n^T on its
+// diagonal 3x3 block (one thread per node, the only writer of those entries
+// in this kernel; the contact assembly before it has finished)
+template <class R>
+__global__ void k_assemble_pg_coarse(Dev<R> D) {
+    const int n = D.coarse_off[D.nlev] / 3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double k = D.pg_k[i];
+        if (k == 0.0) continue;
+        int l = 1;
+        while (l + 1 < D.nlev && i >= D.coarse_off[l + 1] / 3) ++l;
+        const int node = i - D.coarse_off[l] / 3;
+        const int s = D.slot_of_node[l][node];
+        double* A = D.asmbc + (size_t)(D.blk_off[l] - D.blk_off[1] + D.grp_of_node[l][node]) * (kBlk * kBlk);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A[(3 * s + r) * kBlk + 3 * s + c] += k * D.gn[r] * D.gn[c];
     }
 }
 
@@ -2030,7 +2061,10 @@ void launch_restart(const Dev<R>& D, const double* x, const ContactBuf& C, cudaS
         KL(k_asm_contrib<R><<<nblk(D.nt), kT, 0, st>>>(D));
         KL(k_asm_sum<R><<<nblk(32LL * D.nitem, 256), 256, 0, st>>>(D));
     }
+    const int ncn = D.coarse_off[D.nlev] / 3;
+    if (ncn > 0) cudaMemsetAsync(D.pg_k, 0, sizeof(double) * ncn, st);
     KL(k_assemble_contacts<R><<<592, kT, 0, st>>>(D, C));
+    if (ncn > 0) KL(k_assemble_pg_coarse<R><<<nblk(ncn), kT, 0, st>>>(D));
     if (D.jac)
         KL(k_jacobi_build<R><<<nblk(D.nv), kT, 0, st>>>(D));
     else
