@@ -64,6 +64,9 @@ def parse():
                     help="requests of the serving stream (Poisson arrivals at 200 timesteps/s over a pool of "
                          "scenes; 0 = skip)")
     ap.add_argument("--pool", type=int, default=200, help="config-3-sized scenes in the serving pool")
+    ap.add_argument("--torus", type=int, default=10,
+                    help="distinct torus-chain scenes of the serving stream (created on first request, "
+                         "evicted least recently used when free device memory runs low)")
     ap.add_argument("--large", type=int, default=0,
                     help="timesteps of the large spiky-ball scene (8 balls, 1.13M vertices, 2.84M tets; 0 = skip)")
     ap.add_argument("--scale", type=int, default=5,
@@ -766,7 +769,7 @@ def main():
     ablation = run_ablation(args, ipc, S, prec) if args.ablation > 0 and world == 1 else None
     sweep = run_stiffness_sweep(args, ipc, S, prec) if args.stiffness_sweep > 0 and world == 1 else None
     large = run_large(args, ipc, S, prec) if args.large > 0 and world == 1 else None
-    stream = run_serve_stream(args, ipc, S) if args.serve_stream > 0 and world == 1 else None
+    stream = run_serve_stream(args, ipc, S, n_torus=args.torus) if args.serve_stream > 0 and world == 1 else None
     scale = run_scale(args, ipc, S, prec, rsize, flush, stream, peak) if args.scale > 0 and world == 1 else None
 
     # end-to-end through the C ABI with host buffers: per step the state goes
