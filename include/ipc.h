@@ -132,10 +132,12 @@ typedef struct ipc_params {
                                 L_rk^2 > 1) is inverted again in FP64 with the
                                 pivot rules (Sec. 4.2). Default 1e-6; 1 sends
                                 every block to FP64. */
-    int grid_pair_capacity;  /* pairs a grid query may hand to the list
-                                kernels per query pass (0: 16 per surface
-                                primitive + 4096). A pass that finds more
-                                runs its FP64 tests inside the query instead:
+    int grid_pair_capacity;  /* entries of the scratch pair list (0: 16 per
+                                surface primitive + 4096): the pairs a grid
+                                query, an FP32 screen of a cached candidate
+                                list, or a CCD verification pass hands on to
+                                be tested in FP64 on full warps. Pairs beyond
+                                it are tested where they were found instead:
                                 same results, slower. */
     int wait_polls;          /* polls of each bounded wait of a CTA on its
                                 bulk copy into shared memory (default 2^22,
