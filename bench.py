@@ -372,22 +372,23 @@ def run_stiffness_sweep(args, ipc, S, prec):
             "rows": out}
 
 
-def run_serve_stream(args, ipc, S, rate=200.0, torus_frac=0.1, n_torus=10, slots=8, margin_gb=40.0, wall_cap_s=240.0):
+def run_serve_stream(args, ipc, S, rate=200.0, torus_frac=0.1, n_torus=10, slots=8, margin_gb=40.0, wall_cap_s=240.0,
+                     creators=4):
     """Serving stream: timestep requests arrive as a Poisson process (`rate`
     per second, seed 3), each for a scene drawn from a pool of `args.pool`
     config-3-sized scenes (500-20k vertices, cubes, balls and rods) and, with
     probability `torus_frac`, from `n_torus` stacks of interlocked torus rings
-    of 100k-300k vertices (10 of them: a hundred would need about 400 GB of
-    device memory, more than the GPU holds, and each first request would pay
-    a ~2 s scene creation). The small scenes are made resident before the
-    stream starts; a torus scene is created on its first request (admission:
-    while free device memory is below `margin_gb`, idle torus scenes are
-    destroyed, least recently used first) and stays resident after. Requests
-    run through ipc_server (continuous batching, `slots` at once); latency is
-    completion minus arrival, scene creation included. After `wall_cap_s`
-    no new request is submitted (the line then reports how many arrived and
-    ran)."""
+    of 100k-300k vertices. The small scenes are made resident before the
+    stream starts. A torus scene is created on its first request by a pool of
+    `creators` host threads (its requests wait for it; the rest of the stream
+    goes on meanwhile). Admission: while free device memory is below
+    `margin_gb`, idle torus scenes are destroyed, least recently used first.
+    Requests run through ipc_server (continuous batching, `slots` at once);
+    latency is completion minus arrival, queueing and scene creation included.
+    After `wall_cap_s` no new request is submitted (the line then reports how
+    many arrived and ran)."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     rng = np.random.default_rng(3)
     t0 = time.perf_counter()
     pool = []
@@ -399,6 +400,8 @@ def run_serve_stream(args, ipc, S, rate=200.0, torus_frac=0.1, n_torus=10, slots
     pool_s = time.perf_counter() - t0
     sizes = np.exp(rng.uniform(np.log(1e5), np.log(3e5), size=n_torus))
     torus = {}            # id -> Scene (resident)
+    creating = {}         # id -> (future, start time)
+    waiting = {}          # id -> arrival times of requests waiting for the scene
     last_use = {}
     busy = {}             # scene key -> live tickets
     created = evicted = 0
@@ -406,13 +409,25 @@ def run_serve_stream(args, ipc, S, rate=200.0, torus_frac=0.1, n_torus=10, slots
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.serve_stream))
     picks = [("t", int(rng.integers(n_torus))) if rng.uniform() < torus_frac else ("s", int(rng.integers(args.pool)))
              for _ in range(args.serve_stream)]
+
+    def make_torus(i):
+        return ipc.Scene(S.torus_stack(int(sizes[i]), seed=1000 + i), precision=ipc.IPC_PREC_FP32,
+                         use_torch_allocator=False)
+
+    ex = ThreadPoolExecutor(max_workers=creators)
     srv = ipc.Server(slots=slots)
     live = {}
     lat, steps_done, torus_steps, create_s = [], 0, 0, 0.0
+    lat_kind = {"s": [], "t": []}
     nxt = 0
     start = time.perf_counter()
     capped = False
-    while nxt < len(picks) or live:
+
+    def submit(scene, arr, key):
+        busy[key] = busy.get(key, 0) + 1
+        live[srv.submit(scene, 1)] = (arr, key)
+
+    while nxt < len(picks) or live or creating:
         now = time.perf_counter() - start
         if now > wall_cap_s and nxt < len(picks):
             capped = True
@@ -420,34 +435,41 @@ def run_serve_stream(args, ipc, S, rate=200.0, torus_frac=0.1, n_torus=10, slots
         while nxt < len(picks) and arrivals[nxt] <= now:
             kind, i = picks[nxt]
             if kind == "s":
-                scene = pool[i]
+                submit(pool[i], arrivals[nxt], (kind, i))
             else:
-                if i not in torus:
-                    tc = time.perf_counter()
-                    while torch.cuda.mem_get_info()[0] < margin_gb * 1e9:
-                        idle = [j for j in torus if busy.get(("t", j), 0) == 0]
-                        if not idle:
-                            break
-                        j = min(idle, key=lambda q: last_use.get(q, 0.0))
-                        torus.pop(j).close()
-                        evicted += 1
-                    torus[i] = ipc.Scene(S.torus_stack(int(sizes[i]), seed=1000 + i), precision=ipc.IPC_PREC_FP32,
-                                         use_torch_allocator=False)
-                    created += 1
-                    create_s += time.perf_counter() - tc
-                    print(f"serving stream: torus scene {i} ({torus[i].nv} vertices) created in "
-                          f"{time.perf_counter() - tc:.1f} s at {now:.1f} s", file=sys.stderr, flush=True)
-                scene = torus[i]
-                last_use[i] = now
                 torus_steps += 1
-            busy[(kind, i)] = busy.get((kind, i), 0) + 1
-            live[srv.submit(scene, 1)] = (arrivals[nxt], (kind, i))
+                last_use[i] = now
+                if i in torus:
+                    submit(torus[i], arrivals[nxt], (kind, i))
+                else:
+                    waiting.setdefault(i, []).append(arrivals[nxt])
+                    if i not in creating:
+                        while torch.cuda.mem_get_info()[0] < margin_gb * 1e9:
+                            idle = [j for j in torus if busy.get(("t", j), 0) == 0]
+                            if not idle:
+                                break
+                            j = min(idle, key=lambda q: last_use.get(q, 0.0))
+                            torus.pop(j).close()
+                            evicted += 1
+                        creating[i] = (ex.submit(make_torus, i), time.perf_counter())
             nxt += 1
+        for i, (fut, tc) in list(creating.items()):
+            if fut.done():
+                torus[i] = fut.result()
+                del creating[i]
+                created += 1
+                create_s += time.perf_counter() - tc
+                print(f"serving stream: torus scene {i} ({torus[i].nv} vertices) created in "
+                      f"{time.perf_counter() - tc:.1f} s at {time.perf_counter() - start:.1f} s", file=sys.stderr,
+                      flush=True)
+                for arr in waiting.pop(i, []):
+                    submit(torus[i], arr, ("t", i))
         done = []
         for tk, (arr, key) in live.items():
             r = srv.poll(tk)
             if r is not None:
                 lat.append(1e3 * (time.perf_counter() - start - arr))
+                lat_kind[key[0]].append(lat[-1])
                 if key[0] == "t":
                     print(f"serving stream: torus {key[1]} step done, {r['iters']} iterations, latency "
                           f"{lat[-1]:.0f} ms", file=sys.stderr, flush=True)
@@ -462,18 +484,28 @@ def run_serve_stream(args, ipc, S, rate=200.0, torus_frac=0.1, n_torus=10, slots
         if not done:
             time.sleep(2e-4)
     wall = time.perf_counter() - start
+    ex.shutdown()
     srv.close()
     for g in pool:
         g.close()
     for g in torus.values():
         g.close()
     lat.sort()
-    return {"requests": len(picks), "capped_at_s": wall_cap_s if capped else None, "rate_per_s": rate, "pool_scenes": args.pool, "torus_scenes": n_torus,
-            "torus_frac": torus_frac, "slots": slots, "pool_setup_s": pool_s,
-            "device_gb_after_pool": (total - free0) / 1e9, "torus_created": created, "torus_evicted": evicted,
-            "torus_create_s": create_s, "torus_requests": torus_steps, "timesteps_per_s": steps_done / wall,
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))] if v else None
+
+    small = len(lat_kind["s"])
+    return {"requests": len(picks), "capped_at_s": wall_cap_s if capped else None, "rate_per_s": rate,
+            "pool_scenes": args.pool, "torus_scenes": n_torus, "torus_frac": torus_frac, "slots": slots,
+            "creator_threads": creators, "pool_setup_s": pool_s, "device_gb_after_pool": (total - free0) / 1e9,
+            "torus_created": created, "torus_evicted": evicted, "torus_create_s_summed": create_s,
+            "torus_requests": torus_steps, "small_requests": small, "timesteps_per_s": steps_done / wall,
             "arrival_span_s": float(arrivals[-1]), "wall_s": wall,
             "latency_ms_p50": lat[len(lat) // 2], "latency_ms_p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "latency_ms_small_p50_p99": [pct(lat_kind["s"], 0.5), pct(lat_kind["s"], 0.99)],
+            "latency_ms_torus_p50_p99": [pct(lat_kind["t"], 0.5), pct(lat_kind["t"], 0.99)],
             "latency": "completion minus arrival, queueing and torus scene creation included"}
 
 
