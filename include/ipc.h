@@ -186,10 +186,17 @@ void ipc_default_params(ipc_params* p);
  * mesh adjacency, supplement Sec. 1.2), allocates device state and copies
  * it up, and picks the block apply's launch configuration by timing (see
  * IPC_Q_APPLY_CTAS).  Fails with IPC_ERR_INTERSECTING if a contact of the initial state
- * has distance <= 0.  `alloc` may be NULL. */
+ * has distance <= 0.  `alloc` may be NULL.  Its device work runs on the
+ * legacy default stream and waits only for that stream, never for the whole
+ * device, so it may run in one thread while other scenes step (and capture
+ * CUDA graphs) on non-blocking streams in others, e.g. under ipc_server. */
 int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params,
                      const ipc_alloc_fns* alloc, ipc_scene** out);
 
+/* Release a scene.  Waits for the scene's own stream and the legacy default
+ * stream only: every call the caller queued for this scene on its own
+ * streams (or submitted to a server) must have completed.  Other scenes may
+ * go on stepping meanwhile. */
 void ipc_scene_destroy(ipc_scene* s);
 
 /* Advance n_steps timesteps (Algorithm 1 each).  `stats` may be NULL.

@@ -568,7 +568,10 @@ int setup_dev(ipc_scene* s) {
     CUDA_TRY(cudaMemset(D.Cb.count, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(D.C.count, 0, sizeof(int)));
     CUDA_TRY(cudaMemset(D.Ct.count, 0, sizeof(int)));
-    CUDA_TRY(cudaDeviceSynchronize());
+    // set-up work runs on the legacy stream and is waited for there, not by
+    // a device-wide synchronisation: other scenes may be stepping, and
+    // capturing CUDA graphs, on non-blocking streams of other threads
+    CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
     // launch configuration of the per-iteration block apply, timed on this
     // scene's block count (the autotuner; its values are overwritten by the
     // first RebuildMAS)
@@ -576,7 +579,7 @@ int setup_dev(ipc_scene* s) {
         D.apply_ctas = p.apply_ctas;
     else
         autotune_apply(D, (cudaStream_t)0);
-    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaStreamSynchronize(cudaStreamLegacy));
     CUDA_TRY(cudaMemset(D.S, 0, sizeof(Scalars)));
     return 0;
 }
@@ -1470,7 +1473,11 @@ int ipc_scene_create(const ipc_scene_desc* desc, const ipc_params* params, const
 
 void ipc_scene_destroy(ipc_scene* s) {
     if (!s) return;
-    cudaDeviceSynchronize();
+    // the scene's own stream and the legacy one; work the caller queued for
+    // the scene on its streams must be complete (no device-wide wait: other
+    // threads may be capturing graphs of other scenes)
+    if (s->own) cudaStreamSynchronize(s->own);
+    cudaStreamSynchronize(cudaStreamLegacy);
     s->arena.release();
     if (s->hv) cudaFreeHost(s->hv);
     delete s;
@@ -1632,7 +1639,7 @@ long long ipc_kernel_launches(void) { return g_kernel_launches.load(); }
 
 int ipc_profile_enable(ipc_scene* s, int enable) {
     if (!checked(s)) return IPC_ERR_INVALID;
-    cudaDeviceSynchronize();
+    for (auto& q : s->prof.pending) cudaEventSynchronize(q.b);
     s->prof.resolve();
     s->prof.on = enable != 0;
     if (enable) {
@@ -1646,7 +1653,7 @@ int ipc_profile_enable(ipc_scene* s, int enable) {
 
 int ipc_profile_read(ipc_scene* s, ipc_profile* out) {
     if (!checked(s) || !out) return IPC_ERR_INVALID;
-    cudaDeviceSynchronize();
+    for (auto& q : s->prof.pending) cudaEventSynchronize(q.b);
     s->prof.resolve();
     for (int i = 0; i < 8; ++i) {
         out->ms[i] = s->prof.ms[i];

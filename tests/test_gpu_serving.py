@@ -115,3 +115,41 @@ def test_numeric_failure_of_one_scene_leaves_the_others_as_alone():
     assert srv.wait(srv.submit(g, 2))["converged"]
     srv.close()
     assert float(np.abs(g.positions() - alone[bad]).max()) / _bbox(sc["x0"]) <= 1e-6
+
+
+def test_scenes_are_created_and_destroyed_while_others_are_served():
+    # scene creation and destruction wait on their own streams only: a host
+    # thread builds and releases scenes while the server steps others (whose
+    # first repeated launch sequences are captured as CUDA graphs meanwhile),
+    # and every request and every creation succeeds
+    import threading
+    import torch
+    from paper_2604_19892_b300 import ipc
+
+    torch.cuda.set_device(0)
+    scs = [S.mixed_scene(nv, seed) for nv, seed in ((3000, 61), (5000, 62), (2000, 63), (4000, 64))]
+    scenes = [ipc.Scene(sc, precision=ipc.IPC_PREC_FP32, use_torch_allocator=False) for sc in scs]
+    errors, made = [], []
+
+    def builder():
+        try:
+            torch.cuda.set_device(0)
+            for seed in range(71, 77):
+                g = ipc.Scene(S.mixed_scene(6000, seed), precision=ipc.IPC_PREC_FP32, use_torch_allocator=False)
+                made.append(g.nv)
+                g.close()
+        except Exception as e:  # reported below, in the test's thread
+            errors.append(e)
+
+    srv = ipc.Server(slots=4)
+    th = threading.Thread(target=builder)
+    th.start()
+    tickets = [srv.submit(g, 4) for g in scenes]
+    res = [srv.wait(t) for t in tickets]
+    th.join()
+    srv.close()
+    assert not errors, errors
+    assert len(made) == 6
+    assert all(r["converged"] for r in res)
+    for g in scenes:
+        g.close()
