@@ -375,3 +375,35 @@ def test_subdomain_fallback_takes_the_verified_body_steps_safely():
     assert st["converged"] and st["min_dist"] > 0.0
     for r in tr:
         assert r["energy_after"] <= r["energy_before"] + o.energy_tolerance(r["energy_before"])
+
+
+def test_forms_are_the_quadratic_forms_of_the_patched_hessian():
+    """Eq. 6: z^T H~ z, z^T H~ p and p^T H~ p, with H~ = H_base plus u u^T over
+    the untruncated differential set (Sec. 4.1.1), equal the bilinear forms of
+    the oracle's Hessian apply (pinned to finite differences) plus the sum of
+    (u . z_c)(u . p_c) over its classified updates, each u placed on its
+    contact's vertices."""
+    sc = S.two_cubes(n=3, jitter=1e-4, seed=4)
+    o = O.Scene(sc)
+    xb, xc = contact_state(sc, 0.9), contact_state(sc, 0.4)
+    rng = np.random.default_rng(11)
+    z, p = rng.normal(size=(2,) + xb.shape)
+    f0 = o.hess_forms(xb, z, p)
+    Hz, Hp = o.hessian_apply(xb, z), o.hessian_apply(xb, p)
+    ref0 = np.array([np.sum(z * Hz), np.sum(z * Hp), np.sum(p * Hp)])
+    np.testing.assert_allclose(f0, ref0, rtol=1e-12, atol=1e-12 * np.abs(ref0).max())
+    f1 = o.hess_forms(xb, z, p, xc)
+    up = o.updates()
+    assert len(up["dS"]) > 0 and np.all(up["dS"] > 0)
+    C = o.contacts(xc)
+    verts = {(int(t), int(a), int(b)): v for t, (a, b), v in zip(C["type"], C["ids"], C["verts"])}
+    add = np.zeros(3)
+    for key, u in zip(up["key"], up["u"]):
+        v = verts[tuple(int(q) for q in key)]
+        nvv = 1 if key[0] == 2 else 4
+        zc = z[v[:nvv]].reshape(-1)
+        pc = p[v[:nvv]].reshape(-1)
+        zu, pu = float(u[:3 * nvv] @ zc), float(u[:3 * nvv] @ pc)
+        add += [zu * zu, zu * pu, pu * pu]
+    assert np.all(np.abs(add) > 0)
+    np.testing.assert_allclose(f1, f0 + add, rtol=1e-10, atol=1e-10 * np.abs(f0).max())
