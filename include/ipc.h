@@ -322,7 +322,7 @@ typedef struct ipc_iter_record {
     int ccd_passes_body;     /* per-body verification passes, -1 = uniform fallback; when
                                 the per-subdomain one fell back and this one did not,
                                 the first energy-check trial was the per-body step */
-    int pad_;
+    int pad_;                /* layout padding, 0 */
 } ipc_iter_record;
 
 /* ---- evaluation entry points (host arrays in and out) -------------------
